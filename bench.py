@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of biased Langevin (rMD) replicas on GB300, through the C ABI.
+
+Workload (default): 64 replicas of a seeded 560-atom synthetic chain (35
+residues; stand-in for the ~550-atom Fip35 domain), unfolded start, T = 300 K,
+gamma = 1/ps, dt = 2 fs, ratchet bias on the native-contact coordinate z with
+k_R = 1e-4 kJ/mol, FP32 forces with int64 fixed-point sums, 10^5 steps in
+total. One bench step = one scps_step_replicas call of 1000 MD steps for every
+replica; K bench steps are timed with CUDA events on the launching stream,
+with an L2 flush (a 512 MB write) between calls outside the events.
+
+Metric: atom-steps/s = sum over replicas of atoms x MD steps / time.
+Also printed: the plain one-replica-per-launch FP32 form on the same GPU
+(speed-up), the roofline of the resident kernel (FP32 ALU), the end-to-end
+rate with host buffers, the FP64 oracle on the host cores, and the GPU clocks.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build).
+Multi-GPU (torchrun): every rank runs its own 64 replicas (distinct replica
+ids); no collective on the data path; value = all ranks' atom-steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+KT_300 = 0.0083144626 * 300.0
+SEED = 2017
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+FLOPS_PAIR_IN = 49        # in-cutoff pair: distance, LJ + Coulomb + shift, two force updates
+FLOPS_PAIR_TEST = 8       # any pair: separation and squared distance
+FLOPS_BOND = 20
+FLOPS_ANGLE = 60
+FLOPS_CONTACT = 30        # C_ij, (C - C0)^2 and its gradient in FP64-equivalent arithmetic
+FLOPS_ATOM_UPDATE = 40    # BAOAB kicks/drifts, Box-Muller
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100, help="timed bench steps (calls)")
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--md-steps-per-call", type=int, default=1000)
+    p.add_argument("--replicas", type=int, default=64)
+    p.add_argument("--residues", type=int, default=35)
+    p.add_argument("--threads", type=int, default=0)
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(args):
+    c = synth.make_chain(args.residues, seed=1)
+    R = args.replicas
+    return c, R
+
+
+def count_pairs(c, frames, cutoff=1.0):
+    """Mean number of non-excluded pairs within the cutoff over sample frames (geometry only)."""
+    n = c.n_atoms
+    ex = np.zeros((n, n), bool)
+    ex[c.exclusions[:, 0], c.exclusions[:, 1]] = True
+    ex |= ex.T
+    iu = np.triu_indices(n, 1)
+    keep = ~ex[iu]
+    counts = []
+    for x in frames:
+        d2 = ((x[:, None, :] - x[None, :, :]) ** 2).sum(-1)[iu][keep]
+        counts.append(int((d2 < cutoff * cutoff).sum()))
+    return float(np.mean(counts)), int(keep.sum())
+
+
+def flops_per_replica_step(c, p_in, p_all):
+    return (FLOPS_PAIR_TEST * p_all + (FLOPS_PAIR_IN - FLOPS_PAIR_TEST) * p_in
+            + FLOPS_BOND * len(c.bonds) + FLOPS_ANGLE * len(c.angles)
+            + FLOPS_CONTACT * len(c.contacts) + FLOPS_ATOM_UPDATE * c.n_atoms)
+
+
+def cpu_baseline(c, R, budget_s=15.0):
+    """FP64 oracle on the host cores, bounded sample of the same workload."""
+    import oracle
+    ff = oracle.ForceField.from_chain(c)
+    bz = oracle.BiasZ(c.contacts, c.x_native, k_R=1e-4)
+    threads = oracle.num_threads()
+    nrep = min(R, max(threads, 1))
+    x0 = np.stack([c.x_unfolded] * nrep)
+    v0 = c.velocities(nrep, KT_300, SEED)
+    z0 = [bz.z(c.x_unfolded)] * nrep
+    t0 = time.perf_counter()
+    oracle.run_baoab(ff, bz, x0, v0, z0, [0] * nrep, np.arange(nrep), SEED, 0.002, 1.0, KT_300, 1)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.run_baoab(ff, bz, x0, v0, z0, [0] * nrep, np.arange(nrep), SEED, 0.002, 1.0, KT_300,
+                     steps)
+    dt = time.perf_counter() - t0
+    return {"value": nrep * c.n_atoms * steps / dt, "unit": "atom-steps/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{nrep} replicas x {steps} steps of the {c.n_atoms}-atom chain "
+                      f"(FP64 C oracle, OpenMP over replicas), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c, R = workload(args)
+    vals = []
+    sample = None
+    for _ in range(max(1, min(args.steps, 3))):
+        cb = cpu_baseline(c, R, budget_s=10.0)
+        vals.append(cb["value"])
+        sample = cb
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": "biased-Langevin atom-steps/s", "value": v,
+            "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": len(vals),
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{R} x {c.n_atoms}-atom chain rMD, dt 2 fs, 300 K",
+                       "md_steps_per_call": args.md_steps_per_call},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": sample["cores"],
+                             "kind": "oracle", "sample": sample["sample"]},
+            "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_1705_02180_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    c, R = workload(args)
+    n = c.n_atoms
+    x0 = np.stack([c.x_unfolded] * R).reshape(-1, 3)
+    v0 = c.velocities(R, KT_300, SEED).reshape(-1, 3)
+    ids = np.arange(R) + rank * R
+    spc = args.md_steps_per_call
+    sysm = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0, v0=v0,
+                      replica_id=ids, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002,
+                      gamma=1.0, kT=KT_300, seed=SEED, save_interval=spc, max_frames=4,
+                      threads=args.threads, steps_per_graph=spc)
+    sysm.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4, r0=0.75)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sysm.step(spc, stream=stream.cuda_stream)
+    rc, _ = sysm.status()
+    if rc != 0:
+        raise RuntimeError(f"warm-up failed: status {rc}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sysm.step(spc, stream=stream.cuda_stream)
+            ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    rc, st = sysm.status()
+    if rc != 0:
+        raise RuntimeError(f"timed run failed: status {rc}")
+    durs = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3  # s per call
+    t_dev = float(durs.sum())
+    if dist:
+        t = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    atom_steps = R * n * spc * args.steps * world
+    value = atom_steps / t_dev
+    paths = sysm.collect_paths(0, min(R, 4))
+    frames = [f for p in paths for f in p["frames"]][:8]
+    p_in, p_all = count_pairs(c, frames)
+    flops_launch = flops_per_replica_step(c, p_in, p_all) * R * spc
+    achieved = flops_launch / float(durs.mean()) / 1e12
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    info = sysm.info()
+
+    result = {"metric": "biased-Langevin atom-steps/s", "value": value, "unit": "atom-steps/s",
+              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64fix+f64z",
+              "data": "synthetic",
+              "config": {"workload": f"{R} replicas x {n}-atom synthetic chain rMD (Fip35-scale), "
+                                     f"dt 2 fs, 300 K, gamma 1/ps, k_R 1e-4",
+                         "replicas_per_gpu": R, "atoms": n, "md_steps_per_call": spc,
+                         "md_steps_total": spc * args.steps, "native_contacts": int(len(c.contacts)),
+                         "l2": "flushed between calls (512 MB write)",
+                         "threads_per_cta": info["threads"], "parallelism": f"replicas x{world}"},
+              "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": None,
+                           "note": "FP32 peak = 152 SMs x 128 lanes x 2 x 2070 MHz; algorithmic "
+                                   f"flops = {FLOPS_PAIR_TEST}/pair test + {FLOPS_PAIR_IN}/in-cutoff "
+                                   f"pair (mean in-cutoff {p_in:.0f} of {p_all} pairs) + bonded, "
+                                   "contacts, update"},
+              "gpu_launches": int(info["graph_nodes_last_call"]) * args.steps,
+              "clocks": clk, "wall_s": t_wall}
+    # plain one-replica-per-launch form on the same GPU (the speed-up denominator)
+    if not args.no_plain and rank == 0:
+        plain_steps = 20
+        ps = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0, v0=v0,
+                        replica_id=ids, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002,
+                        gamma=1.0, kT=KT_300, seed=SEED, exec_form=pkg.EXEC_PLAIN)
+        ps.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4, r0=0.75)
+        with torch.cuda.stream(stream):
+            ps.step(2, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            ps.step(plain_steps, stream=stream.cuda_stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        t_plain = a.elapsed_time(b) * 1e-3
+        plain_rate = R * n * plain_steps / t_plain
+        result["plain_form"] = {"value": plain_rate, "unit": "atom-steps/s",
+                                "md_steps": plain_steps, "speedup": value / world / plain_rate}
+        ps.close()
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        reps_e2e = max(3, min(args.steps, 10))
+        st0 = sysm.get_state()
+        xs, vs = st0["x"].copy(), st0["v"].copy()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps_e2e):
+            sysm.set_state(x=xs, v=vs)
+            sysm.step(spc, stream=stream.cuda_stream)
+            st1 = sysm.get_state()
+            xs, vs = st1["x"], st1["v"]
+        barrier()
+        te = time.perf_counter() - t0
+        h2d = 2 * 16 * R * n
+        d2h = 2 * 16 * R * n + 3 * 8 * R
+        result["e2e"] = {"value": R * n * spc * reps_e2e / te * world, "unit": "atom-steps/s",
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                         "calls": reps_e2e}
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(c, R)
+    sysm.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+if __name__ == "__main__":
+    main()

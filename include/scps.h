@@ -1,0 +1,211 @@
+/*
+ * scps.h - C ABI of the GB300 engine for ratchet-and-pawl biased Langevin
+ * trajectories (rMD), the data-parallel hot path of Self-Consistent Path
+ * Sampling (Orioli, a Beccara, Faccioli, arXiv:1705.02180).
+ *
+ * The library advances many independent replicas of one or more molecular
+ * topologies (or of the two-dimensional double-well model) under
+ *   - the Langevin equation, Eq. (Lang), integrated with BAOAB (underdamped)
+ *     or Euler-Maruyama (overdamped);
+ *   - a force field -grad U (bonds, angles, Lennard-Jones, Coulomb with a
+ *     distance-dependent dielectric, reaction field or plain form; shifted
+ *     force at the cutoff);
+ *   - the ratchet-and-pawl bias of Eq. (FrMD) on the native-contact
+ *     coordinate z(X) of Eq. (zrMD), built from the contact-map entries of
+ *     Eq. (Cij), with z_m the running minimum of z and z_m(0) = z(X(0)).
+ *
+ * Conventions for every entry point:
+ *   - return value: SCPS_OK (0) or a negative SCPS_ERR_* code; nothing throws
+ *     or aborts; scps_last_error() gives a thread-local message for the last
+ *     failure on the calling thread;
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the device the system was created on; buffers passed in
+ *     are owned by the caller and only read or written during the call (or, for
+ *     stream-ordered calls, until the work enqueued on `stream` completes);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream); stream-ordered calls return after enqueueing;
+ *   - units: nm, ps, amu, kJ/mol, elementary charge; forces in kJ mol^-1 nm^-1.
+ */
+#ifndef SCPS_H
+#define SCPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+#define SCPS_OK 0
+#define SCPS_ERR_INVALID_ARG (-1)   /* bad pointer, size, index or option */
+#define SCPS_ERR_CUDA (-2)          /* a CUDA call failed (message has the CUDA error) */
+#define SCPS_ERR_NONFINITE (-3)     /* a replica produced a non-finite force or position */
+#define SCPS_ERR_LIST_OVERFLOW (-4) /* a capacity (tiles, lists, frames) was exceeded */
+#define SCPS_ERR_TIMEOUT (-5)       /* a bounded device wait gave up */
+#define SCPS_ERR_STATE (-6)         /* call not valid in the current state */
+#define SCPS_ERR_UNSUPPORTED (-7)   /* combination of options not implemented */
+
+/* per-replica status bits reported by scps_get_status */
+#define SCPS_REPLICA_OK 0
+#define SCPS_REPLICA_NONFINITE 1    /* non-finite position/velocity: replica frozen */
+#define SCPS_REPLICA_FORCE_RANGE 2  /* a force partial exceeded the fixed-point range */
+
+/* ----------------------------------------------------------------- enums */
+enum { SCPS_MODEL_CHAIN = 0, SCPS_MODEL_TOY2D = 1 };
+enum { SCPS_ELEC_NONE = 0, SCPS_ELEC_DDIEL = 1, SCPS_ELEC_RF = 2, SCPS_ELEC_PLAIN = 3 };
+enum { SCPS_INT_BAOAB = 0, SCPS_INT_EM = 1 };
+/* execution form of scps_step_replicas:
+ *   RESIDENT: every replica stays on chip for the whole call (one CTA or one
+ *     CTA cluster per replica, all replicas in one launch, CUDA graph);
+ *   PLAIN: reference form - one replica per kernel launch per step, FP32 float
+ *     atomics in global memory, no graph. Same physics, same noise. */
+enum { SCPS_EXEC_RESIDENT = 0, SCPS_EXEC_PLAIN = 1 };
+enum { SCPS_BIAS_NONE = 0, SCPS_BIAS_RMD_CONTACTS = 1, SCPS_BIAS_RMD_TOY = 2 };
+enum { SCPS_ZM_FROM_X = 0, SCPS_ZM_VALUE = 1 };
+
+/* ----------------------------------------------------------------- descriptors */
+typedef struct {
+    int32_t n_atoms;
+    const double* mass;     /* host, n_atoms */
+    const double* charge;   /* host, n_atoms */
+    const double* sigma;    /* host, n_atoms; LJ sigma_ij = (sigma_i + sigma_j) / 2 */
+    const double* eps;      /* host, n_atoms; LJ eps_ij = sqrt(eps_i eps_j) */
+    int32_t n_bonds;
+    const int32_t* bonds;   /* host, n_bonds x 2; U = kb/2 (r - b0)^2 */
+    const double* b0;
+    const double* kb;
+    int32_t n_angles;
+    const int32_t* angles;  /* host, n_angles x 3, centre atom in the middle; U = kth/2 (th - th0)^2 */
+    const double* th0;      /* rad */
+    const double* kth;
+    int32_t n_excl;
+    const int32_t* excl;    /* host, n_excl x 2 pairs left out of the non-bonded sum;
+                               every excluded pair must satisfy |i - j| < 32 */
+} scps_topology_desc;
+
+typedef struct {
+    int32_t model;                          /* SCPS_MODEL_* */
+    int32_t n_topologies;                   /* chain model: >= 1; toy: 0 */
+    const scps_topology_desc* topologies;   /* host, n_topologies */
+    int32_t n_replicas;
+    const int32_t* replica_topology;        /* host, n_replicas (chain model) */
+    const int32_t* replica_id;              /* host, n_replicas global ids for the noise counter;
+                                               NULL = 0 .. n_replicas-1 */
+    const double* x0;   /* host, packed: replicas in order, n_atoms(topology) x 3 each (toy: x 2) */
+    const double* v0;   /* host, same layout as x0; NULL = zero (ignored by SCPS_INT_EM) */
+    /* non-bonded */
+    double cutoff;      /* nm */
+    int32_t elec;       /* SCPS_ELEC_* */
+    double k_dd;        /* distance-dependent dielectric eps_r = k_dd r (nm^-1), e.g. 40 */
+    double eps_rf;      /* reaction-field dielectric, e.g. 78.5 */
+    double box;         /* 0: open boundaries (the only value supported by the chain model) */
+    /* integrator */
+    int32_t integrator; /* SCPS_INT_* */
+    double dt, gamma, kT;
+    uint64_t seed;      /* Philox4x32-10 key */
+    /* path output */
+    int32_t save_interval;  /* global steps between saved frames; 0 = no frames */
+    int32_t max_frames;     /* frames kept per replica (the oldest are overwritten) */
+    /* execution */
+    int32_t exec;           /* SCPS_EXEC_* */
+    int32_t cluster_size;   /* CTAs per replica in RESIDENT form: 0 = auto, 1 or 2 */
+    int32_t threads;        /* threads per CTA in RESIDENT form: 0 = auto, else 128..1024 */
+    int32_t steps_per_graph;/* device-loop steps per CUDA-graph node: 0 = auto */
+} scps_system_desc;
+
+typedef struct {
+    int32_t kind;                       /* SCPS_BIAS_* */
+    double k_R;                         /* ratchet constant of Eq. (FrMD) */
+    double r0;                          /* reference distance of Eq. (Cij), nm */
+    const int32_t* n_pairs;             /* host, per topology: native-contact pair count */
+    const int32_t* const* pairs;        /* host, per topology: n_pairs x 2 (i, j) pairs of z(X) */
+    const double* const* x_native;      /* host, per topology: native coordinates n_atoms x 3;
+                                           C0_ij = C_ij(X_N) is computed by the library */
+    int32_t zm_init;                    /* SCPS_ZM_FROM_X: z_m = z(X) of the current state
+                                           (the paper's z_m(0) = z(X(0))); SCPS_ZM_VALUE */
+    double zm_value;
+    double toy_x_ref;                   /* toy model: z = (x - toy_x_ref)^2 */
+} scps_bias_desc;
+
+typedef struct {
+    int32_t n_replicas;
+    int64_t n_atoms_total;              /* sum over replicas */
+    int32_t max_atoms;
+    int32_t cluster_size, threads, steps_per_graph;
+    int32_t kernels_per_step_call;      /* kernel launches one scps_step_replicas call enqueues
+                                           per graph node (resident form) */
+    int64_t graph_nodes_last_call;      /* kernel launches enqueued by the last step call */
+    int64_t pair_checks_per_step;       /* tile-pair slots evaluated in the last step call */
+    size_t device_bytes;                /* device memory held by the system */
+} scps_info;
+
+typedef struct scps_system scps_system;
+
+/* ----------------------------------------------------------------- entry points */
+/* Creates a system on the current CUDA device: copies every descriptor array
+ * (the caller keeps ownership), allocates state, frames and topology tables in
+ * device memory. Velocities default to zero. No bias until scps_set_bias. */
+int scps_create_system(const scps_system_desc* d, scps_system** out);
+
+/* Frees all device and host memory of the system (NULL is ignored). */
+int scps_destroy_system(scps_system* s);
+
+/* Sets the ratchet bias of Eq. (FrMD) on z(X) of Eq. (zrMD) (contact-map form)
+ * or on z = (x - x_ref)^2 (toy). Computes C0_ij = C_ij(X_N) per topology and
+ * resets z_m per replica (SCPS_ZM_FROM_X uses the current positions). Clears
+ * the bias-functional accumulators. Synchronous. */
+int scps_set_bias(scps_system* s, const scps_bias_desc* b);
+
+/* Advances every replica by n_steps steps (rMD: forces, z, ratchet, update,
+ * frame output). Stream-ordered on `stream`; returns after enqueueing. Device
+ * errors of the enqueued work are reported by scps_get_status. */
+int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream);
+
+/* Potential energy, forces and z for n_frames configurations of topology
+ * `topo` (no bias force, no state change). X: device float, n_frames x
+ * n_atoms x 3. U: device double, n_frames (total physical energy). F: device
+ * float, n_frames x n_atoms x 3, may be NULL. z: device double, n_frames, may
+ * be NULL (needs a contact bias). Stream-ordered. */
+int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const float* X,
+                       double* U, float* F, double* z, void* stream);
+
+/* Hessian-vector products H(X_t) V_t of the physical potential for n_frames
+ * frames (device float arrays n_frames x n_atoms x 3). Stream-ordered. */
+int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, const float* V,
+             float* HV, void* stream);
+
+/* Copies saved path frames of replicas [rep0, rep0 + nrep) to host buffers,
+ * oldest first (synchronous). frames: float, per replica max_frames x
+ * n_atoms x 3 packed in replica order (toy: x 2); z, zmin, epot, bias_T:
+ * double, per replica max_frames; n_frames_out: per replica count (<=
+ * max_frames). Any output pointer may be NULL. */
+int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames, double* z,
+                       double* zmin, double* epot, double* bias_T, int64_t* n_frames_out);
+
+/* Checkpoint: copies (to host) or replaces (from host) the full dynamical
+ * state - positions, velocities, z_m, step counters, bias functional T - in the
+ * packed x0 layout (synchronous). Resuming from a saved state reproduces the
+ * uninterrupted run bit for bit. Any pointer may be NULL (left unchanged). */
+int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* step,
+                   double* bias_T);
+int scps_set_state(scps_system* s, const double* x, const double* v, const double* zm,
+                   const int64_t* step, const double* bias_T);
+
+/* Synchronises and returns SCPS_OK or the first error of the enqueued work;
+ * per_replica (host, n_replicas, may be NULL) receives SCPS_REPLICA_* bits. */
+int scps_get_status(scps_system* s, int32_t* per_replica);
+
+int scps_get_info(const scps_system* s, scps_info* info);
+
+/* Philox4x32-10 blocks on the device, for checking the noise stream:
+ * ctr: device uint32 n x 4, key: two uint32 words, out: device uint32 n x 4. */
+int scps_philox4x32_10(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t key1,
+                       uint32_t* out, void* stream);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* scps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCPS_H */

@@ -1,0 +1,754 @@
+// C ABI of the rMD engine (include/scps.h): validation, device tables, state,
+// launch plans and CUDA graphs. All compute runs in the kernels of
+// kern_chain.cu and kern_aux.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/scps.h"
+#include "scps_internal.h"
+
+namespace scps {
+size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max);
+cudaError_t launch_resident(int elec, const TopoDev* topos, const RepDev* reps, const StateDev& st,
+                            const RunParams& P, int nta, int ntp_max, int ncon_max, int threads,
+                            cudaStream_t stream);
+cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
+                        double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
+                        int ncon_max, int threads, cudaStream_t stream);
+cudaError_t launch_toy(const StateDev& st, const RunParams& P, const uint32_t* rep_ids,
+                       cudaStream_t stream);
+cudaError_t launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                          uint32_t* out, cudaStream_t stream);
+cudaError_t plain_run_replica(int elec, const TopoDev& tp, const StateDev& st, int r,
+                              const RepDev& rep, const RunParams& P, float* scratch,
+                              double* dscratch, long long step0, cudaStream_t s);
+cudaError_t launch_native_map(int nc, const int2* pairs, const double* xN, double inv_r0sq,
+                              float2* C0, cudaStream_t s);
+cudaError_t launch_add_steps(long long* step, int n, long long k, cudaStream_t s);
+}  // namespace scps
+
+using namespace scps;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define SCPS_CU(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(SCPS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+constexpr double kCoulombF = 138.935458;  // kJ mol^-1 nm e^-2
+
+struct TopoHost {
+    int n = 0, ncon = 0;
+    std::vector<float> inv_m;
+    TopoDev dev{};
+};
+
+}  // namespace
+
+struct scps_system {
+    int device = 0;
+    int model = SCPS_MODEL_CHAIN;
+    scps_system_desc d{};
+    std::vector<TopoHost> topos;
+    std::vector<int> rep_topo, atom_off;
+    std::vector<long long> frame_off;
+    std::vector<uint32_t> rep_id;
+    std::vector<long long> host_step;
+    long long n_atoms_total = 0, n_frame_atoms = 0;
+    int max_atoms = 0, nta = 0, ntp_max = 0, ncon_max = 0;
+    TopoDev* d_topos = nullptr;
+    RepDev* d_reps = nullptr;
+    uint32_t* d_rep_ids = nullptr;
+    StateDev st{};
+    RunParams base{};
+    std::vector<void*> allocs;
+    cudaStream_t cap_stream = nullptr;
+    std::map<long long, cudaGraphExec_t> graphs;
+    std::vector<cudaGraph_t> graph_defs;
+    float* plain_f = nullptr;
+    double* plain_d = nullptr;
+    int threads = 0, cluster = 1, steps_per_graph = 0;
+    int bias_kind = SCPS_BIAS_NONE;
+    scps_info info{};
+    size_t bytes = 0;
+
+    template <class T>
+    cudaError_t alloc(T** p, size_t n) {
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+        if (e == cudaSuccess) {
+            allocs.push_back(*p);
+            bytes += sizeof(T) * n;
+            e = cudaMemset(*p, 0, sizeof(T) * n);
+        }
+        return e;
+    }
+    template <class T>
+    cudaError_t upload(T** p, const std::vector<T>& h) {
+        cudaError_t e = alloc(p, h.size());
+        if (e == cudaSuccess && !h.empty())
+            e = cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+        return e;
+    }
+};
+
+namespace {
+
+int validate_topology(const scps_topology_desc& t, int idx) {
+    if (t.n_atoms <= 0 || t.n_atoms > kMaxChainAtoms)
+        return fail(SCPS_ERR_INVALID_ARG, "topology %d: n_atoms %d outside [1, %d]", idx, t.n_atoms,
+                    kMaxChainAtoms);
+    if (!t.mass || !t.charge || !t.sigma || !t.eps)
+        return fail(SCPS_ERR_INVALID_ARG, "topology %d: per-atom array is NULL", idx);
+    if (t.n_bonds < 0 || t.n_angles < 0 || t.n_excl < 0)
+        return fail(SCPS_ERR_INVALID_ARG, "topology %d: negative list size", idx);
+    if ((t.n_bonds && (!t.bonds || !t.b0 || !t.kb)) || (t.n_angles && (!t.angles || !t.th0 || !t.kth)) ||
+        (t.n_excl && !t.excl))
+        return fail(SCPS_ERR_INVALID_ARG, "topology %d: list array is NULL", idx);
+    const int n = t.n_atoms;
+    for (int i = 0; i < n; ++i) {
+        if (!(t.mass[i] > 0.0) || !std::isfinite(t.mass[i]))
+            return fail(SCPS_ERR_INVALID_ARG, "topology %d: mass[%d] must be > 0", idx, i);
+        if (!(t.eps[i] >= 0.0) || !(t.sigma[i] >= 0.0) || !std::isfinite(t.charge[i]))
+            return fail(SCPS_ERR_INVALID_ARG, "topology %d: bad LJ/charge parameter at atom %d", idx, i);
+    }
+    for (int b = 0; b < t.n_bonds; ++b) {
+        const int i = t.bonds[2 * b], j = t.bonds[2 * b + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j)
+            return fail(SCPS_ERR_INVALID_ARG, "topology %d: bond %d has bad atoms (%d, %d)", idx, b, i, j);
+    }
+    for (int a = 0; a < t.n_angles; ++a) {
+        const int i = t.angles[3 * a], j = t.angles[3 * a + 1], k = t.angles[3 * a + 2];
+        if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n || i == j || j == k || i == k)
+            return fail(SCPS_ERR_INVALID_ARG, "topology %d: angle %d has bad atoms", idx, a);
+    }
+    for (int e = 0; e < t.n_excl; ++e) {
+        const int i = t.excl[2 * e], j = t.excl[2 * e + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j)
+            return fail(SCPS_ERR_INVALID_ARG, "topology %d: exclusion %d has bad atoms", idx, e);
+        if (std::abs(i - j) >= kExclWindow)
+            return fail(SCPS_ERR_UNSUPPORTED,
+                        "topology %d: excluded pair (%d, %d) is %d apart; the limit is %d", idx, i,
+                        j, std::abs(i - j), kExclWindow - 1);
+    }
+    return SCPS_OK;
+}
+
+int build_topology(scps_system* s, const scps_topology_desc& t, TopoHost& h) {
+    const scps_system_desc& d = s->d;
+    const int n = t.n_atoms;
+    h.n = n;
+    double qscale = 0.0;
+    if (d.elec == SCPS_ELEC_DDIEL) qscale = std::sqrt(2.0 * kCoulombF / d.k_dd);
+    if (d.elec == SCPS_ELEC_RF || d.elec == SCPS_ELEC_PLAIN) qscale = std::sqrt(kCoulombF);
+    const double c1 = std::exp(-d.gamma * d.dt);
+    std::vector<float2> lj(n);
+    std::vector<float> qs(n), inv_m(n), sd(n);
+    std::vector<unsigned long long> excl(n, 0ull);
+    for (int i = 0; i < n; ++i) {
+        lj[i] = make_float2((float)(0.5 * t.sigma[i]), (float)std::sqrt(24.0 * t.eps[i]));
+        qs[i] = (float)(qscale * t.charge[i]);
+        inv_m[i] = (float)(1.0 / t.mass[i]);
+        sd[i] = (float)std::sqrt((1.0 - c1 * c1) * d.kT / t.mass[i]);
+    }
+    for (int e = 0; e < t.n_excl; ++e) {
+        const int i = t.excl[2 * e], j = t.excl[2 * e + 1];
+        excl[i] |= 1ull << (j - i + kExclWindow);
+        excl[j] |= 1ull << (i - j + kExclWindow);
+    }
+    std::vector<int2> bij(t.n_bonds);
+    std::vector<float2> bpar(t.n_bonds);
+    for (int b = 0; b < t.n_bonds; ++b) {
+        bij[b] = make_int2(t.bonds[2 * b], t.bonds[2 * b + 1]);
+        bpar[b] = make_float2((float)t.b0[b], (float)t.kb[b]);
+    }
+    std::vector<int4> aijk(t.n_angles);
+    std::vector<float2> apar(t.n_angles);
+    for (int a = 0; a < t.n_angles; ++a) {
+        aijk[a] = make_int4(t.angles[3 * a], t.angles[3 * a + 1], t.angles[3 * a + 2], 0);
+        apar[a] = make_float2((float)t.th0[a], (float)t.kth[a]);
+    }
+    float2* d_lj;
+    float *d_qs, *d_im, *d_sd;
+    unsigned long long* d_ex;
+    int2* d_bij;
+    float2* d_bpar;
+    int4* d_aijk;
+    float2* d_apar;
+    SCPS_CU(s->upload(&d_lj, lj));
+    SCPS_CU(s->upload(&d_qs, qs));
+    SCPS_CU(s->upload(&d_im, inv_m));
+    SCPS_CU(s->upload(&d_sd, sd));
+    SCPS_CU(s->upload(&d_ex, excl));
+    SCPS_CU(s->upload(&d_bij, bij));
+    SCPS_CU(s->upload(&d_bpar, bpar));
+    SCPS_CU(s->upload(&d_aijk, aijk));
+    SCPS_CU(s->upload(&d_apar, apar));
+    h.inv_m = inv_m;
+    TopoDev& td = h.dev;
+    td.n_atoms = n;
+    td.n_tiles = (n + kTile - 1) / kTile;
+    td.lj = d_lj;
+    td.qs = d_qs;
+    td.inv_m = d_im;
+    td.noise_sd = d_sd;
+    td.excl = d_ex;
+    td.n_bonds = t.n_bonds;
+    td.bond_ij = d_bij;
+    td.bond_par = d_bpar;
+    td.n_angles = t.n_angles;
+    td.ang_ijk = d_aijk;
+    td.ang_par = d_apar;
+    td.n_contacts = 0;
+    td.con_ij = nullptr;
+    td.con_C0 = nullptr;
+    return SCPS_OK;
+}
+
+int atoms_per_replica(const scps_system* s, int r) {
+    return s->model == SCPS_MODEL_TOY2D ? 1 : s->topos[s->rep_topo[r]].n;
+}
+
+int auto_threads(int nta) {
+    if (nta <= 256) return 256;
+    if (nta <= 640) return 512;
+    return 1024;
+}
+
+int sync_topos(scps_system* s) {
+    std::vector<TopoDev> h(s->topos.size());
+    for (size_t t = 0; t < h.size(); ++t) h[t] = s->topos[t].dev;
+    SCPS_CU(cudaMemcpy(s->d_topos, h.data(), sizeof(TopoDev) * h.size(), cudaMemcpyHostToDevice));
+    return SCPS_OK;
+}
+
+void drop_graphs(scps_system* s) {
+    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    for (auto g : s->graph_defs) cudaGraphDestroy(g);
+    s->graph_defs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* scps_last_error(void) { return g_err.c_str(); }
+
+int scps_create_system(const scps_system_desc* d, scps_system** out) {
+    if (!d || !out) return fail(SCPS_ERR_INVALID_ARG, "NULL descriptor or output pointer");
+    *out = nullptr;
+    if (d->model != SCPS_MODEL_CHAIN && d->model != SCPS_MODEL_TOY2D)
+        return fail(SCPS_ERR_INVALID_ARG, "unknown model %d", d->model);
+    if (d->n_replicas <= 0) return fail(SCPS_ERR_INVALID_ARG, "n_replicas must be > 0");
+    if (!d->x0) return fail(SCPS_ERR_INVALID_ARG, "x0 is NULL");
+    if (!(d->dt > 0.0) || !(d->gamma > 0.0) || !(d->kT >= 0.0))
+        return fail(SCPS_ERR_INVALID_ARG, "need dt > 0, gamma > 0, kT >= 0");
+    if (d->save_interval < 0 || (d->save_interval > 0 && d->max_frames <= 0))
+        return fail(SCPS_ERR_INVALID_ARG, "save_interval > 0 needs max_frames > 0");
+    if (d->exec != SCPS_EXEC_RESIDENT && d->exec != SCPS_EXEC_PLAIN)
+        return fail(SCPS_ERR_INVALID_ARG, "unknown exec form %d", d->exec);
+    if (d->cluster_size < 0 || d->cluster_size > 1)
+        return fail(SCPS_ERR_UNSUPPORTED, "cluster_size %d not supported (0 or 1)", d->cluster_size);
+    if (d->threads != 0 && (d->threads < 128 || d->threads > 1024 || d->threads % 32))
+        return fail(SCPS_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [128, 1024]");
+    scps_system* s = new scps_system();
+    s->d = *d;
+    s->d.topologies = nullptr;
+    s->d.replica_topology = nullptr;
+    s->d.replica_id = nullptr;
+    s->d.x0 = nullptr;
+    s->d.v0 = nullptr;
+    s->model = d->model;
+    cudaGetDevice(&s->device);
+    const int R = d->n_replicas;
+    s->rep_id.resize(R);
+    for (int r = 0; r < R; ++r) s->rep_id[r] = d->replica_id ? (uint32_t)d->replica_id[r] : (uint32_t)r;
+    s->host_step.assign(R, 0);
+    auto bail = [&](int rc) {
+        scps_destroy_system(s);
+        return rc;
+    };
+    if (d->model == SCPS_MODEL_CHAIN) {
+        if (d->n_topologies <= 0 || !d->topologies || !d->replica_topology)
+            return bail(fail(SCPS_ERR_INVALID_ARG, "chain model needs topologies and replica_topology"));
+        if (d->box != 0.0)
+            return bail(fail(SCPS_ERR_UNSUPPORTED, "periodic boxes are not supported by the chain model"));
+        if (!(d->cutoff > 0.0)) return bail(fail(SCPS_ERR_INVALID_ARG, "cutoff must be > 0"));
+        if (d->elec < SCPS_ELEC_NONE || d->elec > SCPS_ELEC_PLAIN)
+            return bail(fail(SCPS_ERR_INVALID_ARG, "unknown electrostatics %d", d->elec));
+        if (d->elec == SCPS_ELEC_DDIEL && !(d->k_dd > 0.0))
+            return bail(fail(SCPS_ERR_INVALID_ARG, "k_dd must be > 0"));
+        if (d->integrator != SCPS_INT_BAOAB)
+            return bail(fail(SCPS_ERR_UNSUPPORTED, "the chain model integrates with BAOAB"));
+        s->topos.resize(d->n_topologies);
+        for (int t = 0; t < d->n_topologies; ++t) {
+            int rc = validate_topology(d->topologies[t], t);
+            if (rc) return bail(rc);
+            rc = build_topology(s, d->topologies[t], s->topos[t]);
+            if (rc) return bail(rc);
+            s->max_atoms = std::max(s->max_atoms, s->topos[t].n);
+        }
+        s->rep_topo.resize(R);
+        for (int r = 0; r < R; ++r) {
+            const int t = d->replica_topology[r];
+            if (t < 0 || t >= d->n_topologies)
+                return bail(fail(SCPS_ERR_INVALID_ARG, "replica %d: topology %d out of range", r, t));
+            s->rep_topo[r] = t;
+        }
+    } else {
+        if (d->integrator != SCPS_INT_EM)
+            return bail(fail(SCPS_ERR_UNSUPPORTED, "the toy model integrates with Euler-Maruyama"));
+        s->max_atoms = 1;
+    }
+    // packed addressing
+    s->atom_off.resize(R);
+    s->frame_off.resize(R);
+    long long off = 0, foff = 0;
+    for (int r = 0; r < R; ++r) {
+        const int n = atoms_per_replica(s, r);
+        s->atom_off[r] = (int)off;
+        s->frame_off[r] = foff;
+        off += n;
+        foff += (long long)std::max(d->max_frames, 0) * n;
+    }
+    s->n_atoms_total = off;
+    s->n_frame_atoms = foff;
+    const int mf = std::max(d->max_frames, 1);
+    const int dims = d->model == SCPS_MODEL_TOY2D ? 2 : 3;
+    StateDev& st = s->st;
+    int rc = 0;
+#define ALLOC(p, n)                                          \
+    do {                                                     \
+        cudaError_t e_ = s->alloc(&(p), (size_t)(n));        \
+        if (e_ != cudaSuccess)                               \
+            return bail(fail(SCPS_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e_))); \
+    } while (0)
+    ALLOC(st.zm, R);
+    ALLOC(st.z, R);
+    ALLOC(st.step, R);
+    ALLOC(st.T, R);
+    ALLOC(st.status, R);
+    ALLOC(st.n_saved, R);
+    ALLOC(st.fz, (size_t)R * mf);
+    ALLOC(st.fzm, (size_t)R * mf);
+    ALLOC(st.fe, (size_t)R * mf);
+    ALLOC(st.fT, (size_t)R * mf);
+    ALLOC(st.frames, (size_t)std::max(foff, 1ll) * dims);
+    ALLOC(s->d_rep_ids, R);
+    if (d->model == SCPS_MODEL_CHAIN) {
+        ALLOC(st.x, off);
+        ALLOC(st.v, off);
+        ALLOC(s->d_topos, s->topos.size());
+        ALLOC(s->d_reps, R);
+        ALLOC(s->plain_f, (size_t)6 * s->max_atoms + 16384 + 64);
+        ALLOC(s->plain_d, 8);
+    } else {
+        ALLOC(st.xy, R);
+    }
+#undef ALLOC
+    {
+        std::vector<double> inf(R, std::numeric_limits<double>::infinity());
+        cudaMemcpy(st.zm, inf.data(), sizeof(double) * R, cudaMemcpyHostToDevice);
+        cudaMemcpy(s->d_rep_ids, s->rep_id.data(), sizeof(uint32_t) * R, cudaMemcpyHostToDevice);
+    }
+    if (d->model == SCPS_MODEL_CHAIN) {
+        std::vector<RepDev> reps(R);
+        for (int r = 0; r < R; ++r)
+            reps[r] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], 0};
+        if (cudaMemcpy(s->d_reps, reps.data(), sizeof(RepDev) * R, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(SCPS_ERR_CUDA, "upload of the replica table failed"));
+        rc = sync_topos(s);
+        if (rc) return bail(rc);
+        s->nta = ((s->max_atoms + kTile - 1) / kTile) * kTile;
+        const int nt = s->nta / kTile;
+        s->ntp_max = nt * (nt + 1) / 2;
+        s->threads = d->threads ? d->threads : auto_threads(s->nta);
+        s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
+    }
+    rc = scps_set_state(s, d->x0, d->v0, nullptr, nullptr, nullptr);
+    if (rc) return bail(rc);
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(SCPS_ERR_CUDA, "cudaStreamCreate failed"));
+    // run parameters shared by every launch
+    RunParams& P = s->base;
+    P.n_replicas = R;
+    P.dt = (float)d->dt;
+    P.half_dt = (float)(0.5 * d->dt);
+    P.c1 = (float)std::exp(-d->gamma * d->dt);
+    P.gamma = d->gamma;
+    P.key0 = (uint32_t)(d->seed & 0xffffffffull);
+    P.key1 = (uint32_t)(d->seed >> 32);
+    P.save_interval = d->save_interval;
+    P.max_frames = mf;
+    P.bias = 0;
+    P.k_R = 0.0;
+    P.toy_dt_over_gamma = d->dt / d->gamma;
+    P.toy_sd = std::sqrt(2.0 * d->kT * d->dt / d->gamma);
+    P.toy_x_ref = 1.0;
+    const double rcut = d->cutoff > 0.0 ? d->cutoff : 1.0;
+    P.pc.rc = (float)rcut;
+    P.pc.rc2 = (float)(rcut * rcut);
+    P.pc.inv_rc = (float)(1.0 / rcut);
+    P.pc.inv_rc2 = (float)(1.0 / (rcut * rcut));
+    P.pc.inv_rc3 = (float)(1.0 / (rcut * rcut * rcut));
+    const double krf = (d->eps_rf - 1.0) / ((2.0 * d->eps_rf + 1.0) * rcut * rcut * rcut);
+    P.pc.krf = (float)krf;
+    P.pc.crf = (float)(1.0 / rcut + krf * rcut * rcut);
+    s->cluster = 1;
+    *out = s;
+    return SCPS_OK;
+}
+
+int scps_destroy_system(scps_system* s) {
+    if (!s) return SCPS_OK;
+    drop_graphs(s);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (void* p : s->allocs) cudaFree(p);
+    delete s;
+    return SCPS_OK;
+}
+
+int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
+    if (!s || !b) return fail(SCPS_ERR_INVALID_ARG, "NULL system or bias");
+    RunParams& P = s->base;
+    if (b->kind == SCPS_BIAS_NONE) {
+        P.bias = 0;
+    } else if (b->kind == SCPS_BIAS_RMD_TOY) {
+        if (s->model != SCPS_MODEL_TOY2D) return fail(SCPS_ERR_INVALID_ARG, "toy bias on a chain system");
+        P.bias = 2;
+        P.toy_x_ref = b->toy_x_ref;
+    } else if (b->kind == SCPS_BIAS_RMD_CONTACTS) {
+        if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_INVALID_ARG, "contact bias needs the chain model");
+        if (!(b->r0 > 0.0)) return fail(SCPS_ERR_INVALID_ARG, "r0 must be > 0");
+        if (!b->n_pairs || !b->pairs || !b->x_native)
+            return fail(SCPS_ERR_INVALID_ARG, "contact bias needs n_pairs, pairs and x_native");
+        const double inv_r0sq = 1.0 / (b->r0 * b->r0);
+        int ncon_max = 0;
+        for (size_t t = 0; t < s->topos.size(); ++t) {
+            const int nc = b->n_pairs[t], n = s->topos[t].n;
+            if (nc < 0) return fail(SCPS_ERR_INVALID_ARG, "topology %zu: negative pair count", t);
+            if (nc > 0 && (!b->pairs[t] || !b->x_native[t]))
+                return fail(SCPS_ERR_INVALID_ARG, "topology %zu: NULL pairs or x_native", t);
+            std::vector<int2> pairs(nc);
+            for (int c = 0; c < nc; ++c) {
+                const int i = b->pairs[t][2 * c], j = b->pairs[t][2 * c + 1];
+                if (i < 0 || j < 0 || i >= n || j >= n || i == j)
+                    return fail(SCPS_ERR_INVALID_ARG, "topology %zu: contact %d has bad atoms", t, c);
+                pairs[c] = make_int2(i, j);
+            }
+            std::vector<double> xn(nc > 0 ? (size_t)3 * n : 0);
+            if (nc > 0) std::memcpy(xn.data(), b->x_native[t], sizeof(double) * 3 * n);
+            int2* d_pairs;
+            float2* d_c0;
+            double* d_xn;
+            SCPS_CU(s->upload(&d_pairs, pairs));
+            SCPS_CU(s->alloc(&d_c0, nc));
+            SCPS_CU(s->upload(&d_xn, xn));
+            SCPS_CU(launch_native_map(nc, d_pairs, d_xn, inv_r0sq, d_c0, 0));
+            SCPS_CU(cudaDeviceSynchronize());
+            s->topos[t].dev.n_contacts = nc;
+            s->topos[t].dev.con_ij = d_pairs;
+            s->topos[t].dev.con_C0 = d_c0;
+            s->topos[t].ncon = nc;
+            ncon_max = std::max(ncon_max, nc);
+        }
+        const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, ncon_max);
+        if (smem > 227 * 1024)
+            return fail(SCPS_ERR_UNSUPPORTED, "shared memory %zu B exceeds the per-CTA limit", smem);
+        if (s->d.exec == SCPS_EXEC_PLAIN && ncon_max > 16384)
+            return fail(SCPS_ERR_UNSUPPORTED, "plain form supports up to 16384 contacts");
+        s->ncon_max = ncon_max;
+        int rc = sync_topos(s);
+        if (rc) return rc;
+        P.bias = 1;
+        P.inv_r0sq = (float)inv_r0sq;
+        const float hi = (float)inv_r0sq;
+        P.inv_r0sq_ff = ff{hi, (float)(inv_r0sq - (double)hi)};
+    } else {
+        return fail(SCPS_ERR_INVALID_ARG, "unknown bias kind %d", b->kind);
+    }
+    P.k_R = b->k_R;
+    s->bias_kind = b->kind;
+    const int R = s->d.n_replicas;
+    std::vector<double> zm(R, b->zm_init == SCPS_ZM_VALUE ? b->zm_value
+                                                          : std::numeric_limits<double>::infinity());
+    std::vector<double> zero(R, 0.0);
+    SCPS_CU(cudaMemcpy(s->st.zm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+    SCPS_CU(cudaMemcpy(s->st.T, zero.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+    drop_graphs(s);
+    return SCPS_OK;
+}
+
+int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    if (n_steps < 0) return fail(SCPS_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (n_steps == 0) return SCPS_OK;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int R = s->d.n_replicas;
+    for (int r = 0; r < R; ++r)
+        if (s->host_step[r] + n_steps > (long long)UINT32_MAX)
+            return fail(SCPS_ERR_INVALID_ARG, "step counter would pass 2^32 (noise counter word)");
+    RunParams P = s->base;
+    long long launches = 0;
+    if (s->model == SCPS_MODEL_TOY2D) {
+        P.n_steps = n_steps;
+        SCPS_CU(launch_toy(s->st, P, s->d_rep_ids, cs));
+        launches = 1;
+    } else if (s->d.exec == SCPS_EXEC_PLAIN) {
+        P.n_steps = n_steps;
+        std::vector<RepDev> reps(R);
+        for (int r = 0; r < R; ++r) {
+            const RepDev rep{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], 0};
+            SCPS_CU(plain_run_replica(s->d.elec, s->topos[s->rep_topo[r]].dev, s->st, r, rep, P,
+                                      s->plain_f, s->plain_d, s->host_step[r], cs));
+        }
+        SCPS_CU(launch_add_steps(s->st.step, R, n_steps, cs));
+        launches = -1;  // many; not tracked
+    } else {
+        const long long chunk = s->steps_per_graph;
+        const long long full = n_steps / chunk, rem = n_steps % chunk;
+        if (full > 0) {
+            auto it = s->graphs.find(chunk);
+            if (it == s->graphs.end()) {
+                RunParams Pc = P;
+                Pc.n_steps = chunk;
+                cudaGraph_t g;
+                SCPS_CU(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t le = launch_resident(s->d.elec, s->d_topos, s->d_reps, s->st, Pc, s->nta,
+                                                 s->ntp_max, s->ncon_max, s->threads, s->cap_stream);
+                cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+                if (le != cudaSuccess || ce != cudaSuccess)
+                    return fail(SCPS_ERR_CUDA, "graph capture failed: %s",
+                                cudaGetErrorString(le != cudaSuccess ? le : ce));
+                cudaGraphExec_t ge;
+                SCPS_CU(cudaGraphInstantiate(&ge, g, 0));
+                s->graph_defs.push_back(g);
+                it = s->graphs.emplace(chunk, ge).first;
+            }
+            for (long long k = 0; k < full; ++k) SCPS_CU(cudaGraphLaunch(it->second, cs));
+        }
+        if (rem > 0) {
+            P.n_steps = rem;
+            SCPS_CU(launch_resident(s->d.elec, s->d_topos, s->d_reps, s->st, P, s->nta, s->ntp_max,
+                                    s->ncon_max, s->threads, cs));
+        }
+        launches = full + (rem > 0);
+    }
+    for (int r = 0; r < R; ++r) s->host_step[r] += n_steps;
+    s->info.graph_nodes_last_call = launches;
+    return SCPS_OK;
+}
+
+int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const float* X, double* U,
+                       float* F, double* z, void* stream) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
+    if (topo < 0 || topo >= (int)s->topos.size()) return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
+    if (n_frames < 0 || n_frames > 2147483647ll) return fail(SCPS_ERR_INVALID_ARG, "bad n_frames");
+    if (n_frames == 0) return SCPS_OK;
+    if (!X || !U) return fail(SCPS_ERR_INVALID_ARG, "X and U are required");
+    if (z && s->base.bias != 1) return fail(SCPS_ERR_STATE, "z needs a contact bias (scps_set_bias)");
+    const TopoHost& th = s->topos[topo];
+    const int nta = ((th.n + kTile - 1) / kTile) * kTile;
+    const int nt = nta / kTile;
+    RunParams P = s->base;
+    if (!z) P.bias = 0;
+    SCPS_CU(launch_eval(s->d.elec, s->d_topos + topo, P, X, U, F, z, n_frames, nta, nt * (nt + 1) / 2,
+                        th.ncon, auto_threads(nta), (cudaStream_t)stream));
+    return SCPS_OK;
+}
+
+int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, const float* V,
+             float* HV, void* stream) {
+    (void)s; (void)topo; (void)n_frames; (void)X; (void)V; (void)HV; (void)stream;
+    return fail(SCPS_ERR_UNSUPPORTED, "Hessian-vector products are not built yet");
+}
+
+int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames, double* z,
+                       double* zmin, double* epot, double* bias_T, int64_t* n_frames_out) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    const int R = s->d.n_replicas;
+    if (rep0 < 0 || nrep < 0 || rep0 + nrep > R) return fail(SCPS_ERR_INVALID_ARG, "replica range");
+    SCPS_CU(cudaDeviceSynchronize());
+    const int mf = std::max(s->d.max_frames, 1);
+    const int dims = s->model == SCPS_MODEL_TOY2D ? 2 : 3;
+    std::vector<long long> ns(R);
+    SCPS_CU(cudaMemcpy(ns.data(), s->st.n_saved, sizeof(long long) * R, cudaMemcpyDeviceToHost));
+    std::vector<double> buf((size_t)nrep * mf);
+    double* dst[4] = {z, zmin, epot, bias_T};
+    double* src[4] = {s->st.fz, s->st.fzm, s->st.fe, s->st.fT};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        SCPS_CU(cudaMemcpy(buf.data(), src[q] + (size_t)rep0 * mf, sizeof(double) * nrep * mf,
+                           cudaMemcpyDeviceToHost));
+        for (int k = 0; k < nrep; ++k) {
+            const long long n_have = std::min<long long>(ns[rep0 + k], mf);
+            const long long first = ns[rep0 + k] > mf ? ns[rep0 + k] % mf : 0;
+            for (long long f = 0; f < n_have; ++f)
+                dst[q][(size_t)k * mf + f] = buf[(size_t)k * mf + (first + f) % mf];
+        }
+    }
+    if (frames && s->d.save_interval > 0) {
+        size_t out_off = 0;
+        for (int k = 0; k < nrep; ++k) {
+            const int r = rep0 + k;
+            const int n = atoms_per_replica(s, r);
+            const size_t per = (size_t)n * dims;
+            std::vector<float> fb((size_t)mf * per);
+            const size_t src_off = s->model == SCPS_MODEL_TOY2D ? (size_t)r * mf * 2
+                                                                : (size_t)s->frame_off[r] * 3;
+            SCPS_CU(cudaMemcpy(fb.data(), s->st.frames + src_off, sizeof(float) * fb.size(),
+                               cudaMemcpyDeviceToHost));
+            const long long n_have = std::min<long long>(ns[r], mf);
+            const long long first = ns[r] > mf ? ns[r] % mf : 0;
+            for (long long f = 0; f < n_have; ++f)
+                std::memcpy(frames + out_off + f * per, fb.data() + ((first + f) % mf) * per,
+                            sizeof(float) * per);
+            out_off += (size_t)mf * per;
+        }
+    }
+    if (n_frames_out)
+        for (int k = 0; k < nrep; ++k) n_frames_out[k] = std::min<long long>(ns[rep0 + k], mf);
+    return SCPS_OK;
+}
+
+int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* step, double* bias_T) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    SCPS_CU(cudaDeviceSynchronize());
+    const int R = s->d.n_replicas;
+    if (s->model == SCPS_MODEL_TOY2D) {
+        if (x) SCPS_CU(cudaMemcpy(x, s->st.xy, sizeof(double2) * R, cudaMemcpyDeviceToHost));
+        if (v) std::memset(v, 0, sizeof(double) * 2 * R);
+    } else {
+        std::vector<float4> h(s->n_atoms_total);
+        if (x) {
+            SCPS_CU(cudaMemcpy(h.data(), s->st.x, sizeof(float4) * h.size(), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < h.size(); ++i) {
+                x[3 * i] = h[i].x;
+                x[3 * i + 1] = h[i].y;
+                x[3 * i + 2] = h[i].z;
+            }
+        }
+        if (v) {
+            SCPS_CU(cudaMemcpy(h.data(), s->st.v, sizeof(float4) * h.size(), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < h.size(); ++i) {
+                v[3 * i] = h[i].x;
+                v[3 * i + 1] = h[i].y;
+                v[3 * i + 2] = h[i].z;
+            }
+        }
+    }
+    if (zm) SCPS_CU(cudaMemcpy(zm, s->st.zm, sizeof(double) * R, cudaMemcpyDeviceToHost));
+    if (step) SCPS_CU(cudaMemcpy(step, s->st.step, sizeof(long long) * R, cudaMemcpyDeviceToHost));
+    if (bias_T) SCPS_CU(cudaMemcpy(bias_T, s->st.T, sizeof(double) * R, cudaMemcpyDeviceToHost));
+    return SCPS_OK;
+}
+
+int scps_set_state(scps_system* s, const double* x, const double* v, const double* zm,
+                   const int64_t* step, const double* bias_T) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    SCPS_CU(cudaDeviceSynchronize());
+    const int R = s->d.n_replicas;
+    if (s->model == SCPS_MODEL_TOY2D) {
+        if (x) {
+            for (int r = 0; r < 2 * R; ++r)
+                if (!std::isfinite(x[r])) return fail(SCPS_ERR_NONFINITE, "non-finite position");
+            SCPS_CU(cudaMemcpy(s->st.xy, x, sizeof(double2) * R, cudaMemcpyHostToDevice));
+        }
+    } else {
+        std::vector<float4> h(s->n_atoms_total);
+        if (x) {
+            for (size_t i = 0; i < h.size(); ++i) {
+                for (int k = 0; k < 3; ++k)
+                    if (!std::isfinite(x[3 * i + k]))
+                        return fail(SCPS_ERR_NONFINITE, "non-finite position at packed atom %zu", i);
+                h[i] = make_float4((float)x[3 * i], (float)x[3 * i + 1], (float)x[3 * i + 2], 0.f);
+            }
+            SCPS_CU(cudaMemcpy(s->st.x, h.data(), sizeof(float4) * h.size(), cudaMemcpyHostToDevice));
+        }
+        if (v) {
+            for (size_t i = 0; i < h.size(); ++i) {
+                for (int k = 0; k < 3; ++k)
+                    if (!std::isfinite(v[3 * i + k]))
+                        return fail(SCPS_ERR_NONFINITE, "non-finite velocity at packed atom %zu", i);
+                h[i] = make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.f);
+            }
+            SCPS_CU(cudaMemcpy(s->st.v, h.data(), sizeof(float4) * h.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    if (zm) SCPS_CU(cudaMemcpy(s->st.zm, zm, sizeof(double) * R, cudaMemcpyHostToDevice));
+    if (step) {
+        for (int r = 0; r < R; ++r) {
+            if (step[r] < 0 || step[r] > (int64_t)UINT32_MAX) return fail(SCPS_ERR_INVALID_ARG, "step out of range");
+            s->host_step[r] = step[r];
+        }
+        SCPS_CU(cudaMemcpy(s->st.step, step, sizeof(long long) * R, cudaMemcpyHostToDevice));
+    }
+    if (bias_T) SCPS_CU(cudaMemcpy(s->st.T, bias_T, sizeof(double) * R, cudaMemcpyHostToDevice));
+    if (x || v) {
+        std::vector<int> zero(R, 0);
+        SCPS_CU(cudaMemcpy(s->st.status, zero.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
+    }
+    return SCPS_OK;
+}
+
+int scps_get_status(scps_system* s, int32_t* per_replica) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(SCPS_ERR_CUDA, "device error: %s", cudaGetErrorString(e));
+    const int R = s->d.n_replicas;
+    std::vector<int> st(R);
+    SCPS_CU(cudaMemcpy(st.data(), s->st.status, sizeof(int) * R, cudaMemcpyDeviceToHost));
+    int rc = SCPS_OK;
+    for (int r = 0; r < R; ++r) {
+        if (per_replica) per_replica[r] = st[r];
+        if (st[r] != SCPS_REPLICA_OK) rc = SCPS_ERR_NONFINITE;
+    }
+    if (rc) fail(rc, "a replica produced non-finite or out-of-range values and was frozen");
+    return rc;
+}
+
+int scps_get_info(const scps_system* s, scps_info* info) {
+    if (!s || !info) return fail(SCPS_ERR_INVALID_ARG, "NULL argument");
+    *info = s->info;
+    info->n_replicas = s->d.n_replicas;
+    info->n_atoms_total = s->n_atoms_total;
+    info->max_atoms = s->max_atoms;
+    info->cluster_size = s->cluster;
+    info->threads = s->threads;
+    info->steps_per_graph = s->steps_per_graph;
+    info->kernels_per_step_call = 1;
+    info->device_bytes = s->bytes;
+    return SCPS_OK;
+}
+
+int scps_philox4x32_10(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,
+                       void* stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(SCPS_ERR_INVALID_ARG, "bad arguments");
+    SCPS_CU(launch_philox(n, ctr, key0, key1, out, (cudaStream_t)stream));
+    return SCPS_OK;
+}
+
+}  // extern "C"

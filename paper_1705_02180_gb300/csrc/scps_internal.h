@@ -1,0 +1,79 @@
+// Internal data layout of the rMD engine (device tables and launch plans).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "scps_device.cuh"
+
+namespace scps {
+
+constexpr int kTile = 32;            // atoms per tile (one warp lane per atom)
+constexpr int kMaxChainAtoms = 2048; // resident-form limit per replica (shared memory)
+constexpr int kExclWindow = 32;      // excluded pairs must satisfy |i - j| < 32
+
+// Per-topology tables in device memory (shared by all replicas of a topology).
+struct TopoDev {
+    int n_atoms, n_tiles;
+    const float2* lj;          // (sigma/2, sqrt(24 eps))
+    const float* qs;           // scaled charge (see pair_s)
+    const float* inv_m;        // 1/m
+    const float* noise_sd;     // sqrt((1 - c1^2) kT / m), c1 = exp(-gamma dt)
+    const unsigned long long* excl;  // bit (j - i + 32) set when pair (i, j) is excluded
+    int n_bonds;
+    const int2* bond_ij;
+    const float2* bond_par;    // (b0, kb)
+    int n_angles;
+    const int4* ang_ijk;       // (i, centre j, k, -)
+    const float2* ang_par;     // (th0, kth)
+    int n_contacts;
+    const int2* con_ij;        // native-contact pairs of z(X)
+    const float2* con_C0;      // C0 as float-float (hi, lo)
+};
+
+// Per-replica addressing.
+struct RepDev {
+    int topo;
+    int atom_off;     // offset into the packed per-atom state arrays
+    long long frame_off;  // offset (in atoms) of the replica's frame ring buffer
+    uint32_t rep_id;  // global replica id (noise counter word)
+    int pad;
+};
+
+// Replica state and outputs (device pointers).
+struct StateDev {
+    float4* x;        // packed positions (x, y, z, -)
+    float4* v;        // packed velocities
+    double* zm;       // running minimum of z
+    double* z;        // z of the current configuration
+    long long* step;  // global step counter
+    double* T;        // bias functional accumulator
+    int* status;      // SCPS_REPLICA_* bits
+    // path output (ring buffers of max_frames per replica)
+    float* frames;    // frame_off * 3 floats per replica start
+    double* fz;
+    double* fzm;
+    double* fe;
+    double* fT;
+    long long* n_saved;
+    // toy model state
+    double2* xy;
+};
+
+struct RunParams {
+    int n_replicas;
+    float dt, half_dt, c1;        // c1 = exp(-gamma dt)
+    double k_R;
+    int bias;                     // 0 none, 1 contacts, 2 toy
+    float inv_r0sq;               // 1 / r0^2 (FP32)
+    ff inv_r0sq_ff;               // 1 / r0^2 (float-float)
+    uint32_t key0, key1;
+    int save_interval, max_frames;
+    long long n_steps;            // steps in this launch
+    PairConst pc;
+    // toy model
+    double toy_dt_over_gamma, toy_sd, toy_x_ref;
+    double gamma;
+};
+
+}  // namespace scps
