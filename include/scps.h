@@ -202,6 +202,25 @@ int scps_get_info(const scps_system* s, scps_info* info);
 int scps_philox4x32_10(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t key1,
                        uint32_t* out, void* stream);
 
+/* Allocation-free variant of scps_energy_forces for one configuration (the
+ * paper has no counterpart; it serves callers that cannot allocate device
+ * memory when they need forces: code running inside a CUDA stream capture,
+ * where cudaMalloc is not allowed; frameworks that have reserved the device
+ * memory for their own pool; latency-critical loops that must not allocate).
+ * X: device float n_atoms x 3 of topology `topo`; U: device double (1 value);
+ * F: device float n_atoms x 3, may be NULL. Physical energy and forces only.
+ * It calls no cudaMalloc/cudaFree: the plain-form kernels accumulate into a
+ * static device array of this library (sized for at most 8192 atoms, held by
+ * every GPU that loads the library until the process exits); larger
+ * topologies return SCPS_ERR_UNSUPPORTED. Each call clears the part it uses
+ * first. All calls share that array, so calls that overlap on the GPU (on
+ * different streams, or from several threads) race and corrupt each other's
+ * results; serialise them. The first call on a device looks up the array's
+ * device address (once per device, with that device current); make that first
+ * call before any stream capture. Stream-ordered on `stream`. */
+int scps_energy_forces_noalloc(scps_system* s, int32_t topo, const float* X, double* U, float* F,
+                               void* stream);
+
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* scps_last_error(void);
 

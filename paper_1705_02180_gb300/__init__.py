@@ -63,7 +63,7 @@ class Info(C.Structure):
 EXPORTS = ["scps_create_system", "scps_destroy_system", "scps_set_bias", "scps_step_replicas",
            "scps_energy_forces", "scps_hvp", "scps_collect_paths", "scps_get_state",
            "scps_set_state", "scps_get_status", "scps_get_info", "scps_philox4x32_10",
-           "scps_last_error"]
+           "scps_energy_forces_noalloc", "scps_last_error"]
 
 _lib = None
 
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "scps_get_state": [_P, _P, _P, _P, _P, _P], "scps_set_state": [_P, _P, _P, _P, _P, _P],
         "scps_get_status": [_P, _P], "scps_get_info": [_P, _P],
         "scps_philox4x32_10": [i64, _P, u32, u32, _P, _P],
+        "scps_energy_forces_noalloc": [_P, i32, _P, _P, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -288,6 +289,11 @@ class System:
         """X: CUDA float32 (frames, n, 3); U: CUDA float64 (frames,); F, z optional."""
         check(load().scps_energy_forces(self.h, int(topo), int(X.shape[0]), _dptr(X), _dptr(U),
                                         _dptr(F), _dptr(z), _stream(stream)))
+
+    def energy_forces_noalloc(self, topo, X, U, F=None, stream=None):
+        """One configuration without device allocation: X CUDA float32 (n, 3), U CUDA float64 (1,)."""
+        check(load().scps_energy_forces_noalloc(self.h, int(topo), _dptr(X), _dptr(U), _dptr(F),
+                                                _stream(stream)))
 
     def hvp(self, topo, X, V, HV, stream=None):
         check(load().scps_hvp(self.h, int(topo), int(X.shape[0]), _dptr(X), _dptr(V), _dptr(HV),

@@ -752,3 +752,18 @@ int scps_philox4x32_10(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t k
 }
 
 }  // extern "C"
+
+// Accessors for the allocation-free entry point (noalloc.cu).
+namespace scps {
+int internal_topology(const scps_system* s, int topo, TopoDev* out, int* elec, RunParams* P) {
+    if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
+    if (topo < 0 || topo >= (int)s->topos.size())
+        return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
+    *out = s->topos[topo].dev;
+    *elec = s->d.elec;
+    *P = s->base;
+    return SCPS_OK;
+}
+
+int internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace scps
