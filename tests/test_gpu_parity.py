@@ -182,7 +182,9 @@ def test_one_step_positions_bias_released(pkg):
     # here the bias factor is -k_R (z(X1) - z(X0)), a small difference of two large z
     # values; FP32 positions (GPU) vs FP64 positions (oracle) move it by ~1e-3 relative
     assert np.allclose(got["T"], ref["T"], rtol=5e-3, atol=1e-12)
-    assert np.allclose(got["zm"], ref["zm"], rtol=1e-9)
+    # where z fell, z_m = z(X1) with X1 in FP32 (GPU) vs FP64 (oracle): the positions differ
+    # by ~1e-7 nm, so z_m agrees to ~1e-8 relative (the 1e-9 bound is for identical positions)
+    assert np.allclose(got["zm"], ref["zm"], rtol=1e-7)
 
 
 def test_short_run_tracks_oracle(pkg):
