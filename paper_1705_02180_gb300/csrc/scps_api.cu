@@ -15,9 +15,9 @@
 
 namespace scps {
 size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max);
-cudaError_t launch_resident(int elec, const TopoDev* topos, const RepDev* reps, const StateDev& st,
-                            const RunParams& P, int nta, int ntp_max, int ncon_max, int threads,
-                            cudaStream_t stream);
+cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const RepDev* reps,
+                            const StateDev& st, const RunParams& P, int nta, int ntp_max,
+                            int ncon_max, int threads, cudaStream_t stream);
 cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
                         double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
                         int ncon_max, int threads, cudaStream_t stream);
@@ -269,8 +269,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         return fail(SCPS_ERR_INVALID_ARG, "save_interval > 0 needs max_frames > 0");
     if (d->exec != SCPS_EXEC_RESIDENT && d->exec != SCPS_EXEC_PLAIN)
         return fail(SCPS_ERR_INVALID_ARG, "unknown exec form %d", d->exec);
-    if (d->cluster_size < 0 || d->cluster_size > 1)
-        return fail(SCPS_ERR_UNSUPPORTED, "cluster_size %d not supported (0 or 1)", d->cluster_size);
+    if (d->cluster_size < 0 || d->cluster_size > 2)
+        return fail(SCPS_ERR_UNSUPPORTED, "cluster_size %d not supported (0, 1 or 2)", d->cluster_size);
     if (d->threads != 0 && (d->threads < 128 || d->threads > 1024 || d->threads % 32))
         return fail(SCPS_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [128, 1024]");
     scps_system* s = new scps_system();
@@ -384,7 +384,12 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         s->nta = ((s->max_atoms + kTile - 1) / kTile) * kTile;
         const int nt = s->nta / kTile;
         s->ntp_max = nt * (nt + 1) / 2;
-        s->threads = d->threads ? d->threads : auto_threads(s->nta);
+        int n_sm = 0;
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
+        // a 2-CTA cluster per replica when the replicas alone leave SMs idle
+        s->cluster = d->cluster_size ? d->cluster_size : (2 * R <= n_sm ? 2 : 1);
+        const bool one_cta_per_sm = (long long)R * s->cluster <= n_sm;
+        s->threads = d->threads ? d->threads : (one_cta_per_sm ? 1024 : auto_threads(s->nta));
         s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
     }
     rc = scps_set_state(s, d->x0, d->v0, nullptr, nullptr, nullptr);
@@ -416,7 +421,6 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     const double krf = (d->eps_rf - 1.0) / ((2.0 * d->eps_rf + 1.0) * rcut * rcut * rcut);
     P.pc.krf = (float)krf;
     P.pc.crf = (float)(1.0 / rcut + krf * rcut * rcut);
-    s->cluster = 1;
     *out = s;
     return SCPS_OK;
 }
@@ -536,8 +540,9 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
                 Pc.n_steps = chunk;
                 cudaGraph_t g;
                 SCPS_CU(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t le = launch_resident(s->d.elec, s->d_topos, s->d_reps, s->st, Pc, s->nta,
-                                                 s->ntp_max, s->ncon_max, s->threads, s->cap_stream);
+                cudaError_t le = launch_resident(s->d.elec, s->cluster, s->d_topos, s->d_reps, s->st,
+                                                 Pc, s->nta, s->ntp_max, s->ncon_max, s->threads,
+                                                 s->cap_stream);
                 cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
                 if (le != cudaSuccess || ce != cudaSuccess)
                     return fail(SCPS_ERR_CUDA, "graph capture failed: %s",
@@ -551,8 +556,8 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
         }
         if (rem > 0) {
             P.n_steps = rem;
-            SCPS_CU(launch_resident(s->d.elec, s->d_topos, s->d_reps, s->st, P, s->nta, s->ntp_max,
-                                    s->ncon_max, s->threads, cs));
+            SCPS_CU(launch_resident(s->d.elec, s->cluster, s->d_topos, s->d_reps, s->st, P, s->nta,
+                                    s->ntp_max, s->ncon_max, s->threads, cs));
         }
         launches = full + (rem > 0);
     }

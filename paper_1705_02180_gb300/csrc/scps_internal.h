@@ -12,6 +12,10 @@ constexpr int kTile = 32;            // atoms per tile (one warp lane per atom)
 constexpr int kMaxChainAtoms = 2048; // resident-form limit per replica (shared memory)
 constexpr int kExclWindow = 32;      // excluded pairs must satisfy |i - j| < 32
 
+// replica status bits (the values of SCPS_REPLICA_* in scps.h)
+#define SCPS_FLAG_NONFINITE 1
+#define SCPS_FLAG_FORCE_RANGE 2
+
 // Per-topology tables in device memory (shared by all replicas of a topology).
 struct TopoDev {
     int n_atoms, n_tiles;

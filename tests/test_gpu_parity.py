@@ -378,3 +378,37 @@ def test_set_state_rejects_nan(pkg):
     with pytest.raises(pkg.ScpsError):
         s.set_state(x=bad)
     s.close()
+
+
+# ------------------------------------------------------------------ 2-CTA clusters
+def test_cluster_pair_matches_single_cta_and_oracle(pkg):
+    c = chain(35)
+    R = 3
+    x0 = f32(np.stack([c.x_unfolded] * R))
+    v0 = f32(c.velocities(R, KT, 14))
+    out = {}
+    for cl in (1, 2):
+        runs = []
+        for rep in range(2):
+            s = make_system(pkg, [c], [0] * R, x0, v0, cluster_size=cl, save_interval=10,
+                            max_frames=4)
+            s.set_contact_bias([c.contacts], [c.x_native], k_R=0.01, zm_init=pkg.ZM_VALUE,
+                               zm_value=0.0)
+            assert s.info()["cluster_size"] == cl
+            s.step(1)
+            one = s.get_state()
+            s.step(39)
+            runs.append((one, s.get_state(), s.collect_paths()))
+            s.close()
+        a, b = runs
+        for k in ("x", "v", "zm", "T"):
+            assert np.array_equal(a[1][k], b[1][k]), (cl, k)  # run-to-run bit-exact
+        out[cl] = a
+    ff = oracle.ForceField.from_chain(c)
+    bz = oracle.BiasZ(c.contacts, c.x_native, k_R=0.01)
+    ref = oracle.run_baoab(ff, bz, x0, v0, [0.0] * R, [0] * R, np.arange(R), 11, DT, 1.0, KT, 1)
+    for cl in (1, 2):
+        assert np.abs(out[cl][0]["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-6, cl
+    # force sums are fixed point, so the split over two CTAs changes only the z grouping
+    assert np.abs(out[1][1]["x"] - out[2][1]["x"]).max() < 1e-4
+    assert np.allclose(out[1][2][0]["z"], out[2][2][0]["z"], rtol=1e-6)
