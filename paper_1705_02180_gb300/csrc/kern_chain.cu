@@ -13,6 +13,10 @@
 // and writes a frame every save_interval steps. Every CTA of a cluster
 // integrates all atoms of the replica with the same total force, so their
 // copies of the state stay identical without being exchanged.
+//
+// Work inside a CTA is pulled from a queue by warps (half tile pairs first,
+// then chunks of 32 native contacts, bonds and angles), so no warp idles at
+// the barrier that follows while another still holds several work items.
 #include <cooperative_groups.h>
 
 #include "scps_internal.h"
@@ -24,6 +28,7 @@ namespace scps {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per lane)
 
 struct Shared {
     float4* xq;         // (x, y, z, qs)
@@ -42,19 +47,18 @@ struct Shared {
 
 struct Scalars {
     int tp_count;
-    int status;       // replica status (identical in every CTA of a cluster)
+    int work_next;
+    int status;         // replica status (identical in every CTA of a cluster)
     int bias_on;
-    int flag[2];      // force-range bits raised during the evaluation of a given parity
+    int flag[2];        // force-range bits raised during the evaluation of a given parity
     long long n_saved;
     double zm, z, factor, epot, T;
-    ff zpart[2];      // this CTA's share of z, by parity
-    double epart[2];  // this CTA's share of the potential energy, by parity
-    float red_f[32];
-    ff red_ff[32];
-    double red_d[32];
+    long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity (read by the peer)
+    long long red_e[2][32];  // per-warp shares of the potential energy (units of 2^-20), by parity
+    float red_t[32];    // per-warp shares of sum |F_bias|^2 / m
 };
 
-__device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int ncon_max) {
+__device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max) {
     Shared s;
     char* p = (char*)base;
     s.nta = nta;
@@ -87,59 +91,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-__device__ __forceinline__ ff warp_sum_ff(ff v) {
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ff w;
-        w.hi = __shfl_down_sync(kFull, v.hi, o);
-        w.lo = __shfl_down_sync(kFull, v.lo, o);
-        v = ff_add(v, w);
-    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     return v;
-}
-
-// Block reductions in a fixed order (lane tree, then warps in index order):
-// the result is bit-identical from run to run. Result valid on thread 0.
-__device__ ff block_sum_ff(ff v, Scalars& sc) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_ff(v);
-    if (lane == 0) sc.red_ff[w] = v;
-    __syncthreads();
-    ff t = {0.0f, 0.0f};
-    if (w == 0) {
-        t = lane < nw ? sc.red_ff[lane] : ff{0.0f, 0.0f};
-        t = warp_sum_ff(t);
-    }
-    __syncthreads();
-    return t;
-}
-
-__device__ double block_sum_d(double v, Scalars& sc) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_d(v);
-    if (lane == 0) sc.red_d[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (w == 0) {
-        t = lane < nw ? sc.red_d[lane] : 0.0;
-        t = warp_sum_d(t);
-    }
-    __syncthreads();
-    return t;
-}
-
-__device__ float block_sum_f(float v, Scalars& sc) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_f(v);
-    if (lane == 0) sc.red_f[w] = v;
-    __syncthreads();
-    float t = 0.0f;
-    if (w == 0) {
-        t = lane < nw ? sc.red_f[lane] : 0.0f;
-        t = warp_sum_f(t);
-    }
-    __syncthreads();
-    return t;
 }
 
 // Fixed-point value of a force partial; a non-finite partial or one above
@@ -159,30 +114,34 @@ __device__ __forceinline__ void add_fix(const Shared& sm, long long* F, int i, f
     atomicAdd((unsigned long long*)&F[2 * nta + i], (unsigned long long)f2fix_checked(fz, sm.flag));
 }
 
-// One 32 x 32 tile pair on one warp. Lane l owns atom i = 32 I + l and, in
-// turn, atom j = 32 J + ((l + t) & 31) at iteration t; the j-force
-// accumulators rotate one lane per iteration so that lane l ends with slot l.
+// Half of a 32 x 32 tile pair (j slots 16h .. 16h+15) on one warp. Lane l
+// owns atom i = 32 I + l; within each 16-lane half-warp, lane l takes j slot
+// 16h + ((l + t) & 15) at iteration t and the j-force accumulators rotate one
+// lane per iteration, so lane l ends with slot l & 15; the two half-warps'
+// shares of each j are then added with one exchange.
 template <int ELEC, bool ENERGY>
-__device__ __forceinline__ float tile_pair(const Shared& sm, long long* F, const TopoDev& tp,
-                                           const PairConst& pc, int I, int J, int lane) {
+__device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const TopoDev& tp,
+                                           const PairConst& pc, int I, int J, int h, int lane) {
     const int i = I * kTile + lane;
     const float4 xi = sm.xq[i];
     const float2 li = sm.lj[i];
     const bool near = (J - I) <= 1;
     const unsigned long long em = (near && i < tp.n_atoms) ? tp.excl[i] : 0ull;
+    const int g16 = lane & 16, l16 = lane & 15;
+    const int jb = J * kTile + 16 * h;
     float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
-    const int jb = J * kTile;
 #pragma unroll 4
-    for (int t = 0; t < kTile; ++t) {
-        const int sl = (lane + t) & (kTile - 1);
-        const float4 xj = sm.xq[jb + sl];
-        const float2 lj = sm.lj[jb + sl];
+    for (int t = 0; t < 16; ++t) {
+        const int sl = (l16 + t) & 15;
+        const int j = jb + sl;
+        const float4 xj = sm.xq[j];
+        const float2 lj = sm.lj[j];
         const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         bool ok = r2 < pc.rc2;
-        if (I == J) ok = ok && (sl > lane);
+        if (I == J) ok = ok && (j > i);
         if (near) {
-            const int dj = jb + sl - i + kExclWindow;
+            const int dj = j - i + kExclWindow;
             if (dj >= 0 && dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
         }
         float e = 0.f;
@@ -195,59 +154,71 @@ __device__ __forceinline__ float tile_pair(const Shared& sm, long long* F, const
         fjy = fmaf(-s, dy, fjy);
         fjz = fmaf(-s, dz, fjz);
         if (ENERGY) eacc += ok ? e : 0.0f;
-        const int src = (lane + 1) & (kTile - 1);
+        const int src = g16 | ((l16 + 1) & 15);
         fjx = __shfl_sync(kFull, fjx, src);
         fjy = __shfl_sync(kFull, fjy, src);
         fjz = __shfl_sync(kFull, fjz, src);
     }
+    fjx += __shfl_xor_sync(kFull, fjx, 16);
+    fjy += __shfl_xor_sync(kFull, fjy, 16);
+    fjz += __shfl_xor_sync(kFull, fjz, 16);
     add_fix(sm, F, i, fix, fiy, fiz);
-    add_fix(sm, F, jb + lane, fjx, fjy, fjz);
+    if (lane < 16) add_fix(sm, F, jb + lane, fjx, fjy, fjz);
     return eacc;
 }
 
-// Bonds and angles with index = rank (mod nranks), strided over the CTA.
 template <bool ENERGY>
-__device__ double bonded(const Shared& sm, long long* F, const TopoDev& tp, int rank, int nranks) {
-    double e = 0.0;
-    const int stride = blockDim.x * nranks, first = threadIdx.x * nranks + rank;
-    for (int b = first; b < tp.n_bonds; b += stride) {
-        const int2 ij = tp.bond_ij[b];
-        const float2 par = tp.bond_par[b];
-        const float4 a = sm.xq[ij.x], c = sm.xq[ij.y];
-        const float dx = c.x - a.x, dy = c.y - a.y, dz = c.z - a.z;
-        const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        const float dr = r - par.x;
-        const float f = par.y * dr / r;
-        add_fix(sm, F, ij.x, f * dx, f * dy, f * dz);
-        add_fix(sm, F, ij.y, -f * dx, -f * dy, -f * dz);
-        if (ENERGY) e += 0.5 * (double)par.y * (double)dr * (double)dr;
-    }
-    for (int q = first; q < tp.n_angles; q += stride) {
-        const int4 ijk = tp.ang_ijk[q];
-        const float2 par = tp.ang_par[q];
-        const float4 a = sm.xq[ijk.x], b = sm.xq[ijk.y], c = sm.xq[ijk.z];
-        const float ux = a.x - b.x, uy = a.y - b.y, uz = a.z - b.z;
-        const float wx = c.x - b.x, wy = c.y - b.y, wz = c.z - b.z;
-        const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
-        const float sn = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
-        const float cs = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
-        const float ru2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-        const float rw2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-        const float th = atan2f(sn, cs);
-        const float dth = th - par.x;
-        // F_i = g (cs u / |u|^2 - w) / sn, F_k = g (cs w / |w|^2 - u) / sn, g = -k dth
-        const float g = -par.y * dth / sn;
-        const float au = cs / ru2, aw = cs / rw2;
-        const float fix = g * fmaf(au, ux, -wx), fiy = g * fmaf(au, uy, -wy),
-                    fiz = g * fmaf(au, uz, -wz);
-        const float fkx = g * fmaf(aw, wx, -ux), fky = g * fmaf(aw, wy, -uy),
-                    fkz = g * fmaf(aw, wz, -uz);
-        add_fix(sm, F, ijk.x, fix, fiy, fiz);
-        add_fix(sm, F, ijk.z, fkx, fky, fkz);
-        add_fix(sm, F, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
-        if (ENERGY) e += 0.5 * (double)par.y * (double)dth * (double)dth;
-    }
-    return e;
+__device__ __forceinline__ float bond_term(const Shared& sm, long long* F, const TopoDev& tp,
+                                            int b) {
+    const int2 ij = tp.bond_ij[b];
+    const float2 par = tp.bond_par[b];
+    const float4 a = sm.xq[ij.x], c = sm.xq[ij.y];
+    const float dx = c.x - a.x, dy = c.y - a.y, dz = c.z - a.z;
+    const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float dr = r - par.x;
+    const float f = par.y * dr / r;
+    add_fix(sm, F, ij.x, f * dx, f * dy, f * dz);
+    add_fix(sm, F, ij.y, -f * dx, -f * dy, -f * dz);
+    return ENERGY ? 0.5f * par.y * dr * dr : 0.0f;
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ float angle_term(const Shared& sm, long long* F, const TopoDev& tp,
+                                             int q) {
+    const int4 ijk = tp.ang_ijk[q];
+    const float2 par = tp.ang_par[q];
+    const float4 a = sm.xq[ijk.x], b = sm.xq[ijk.y], c = sm.xq[ijk.z];
+    const float ux = a.x - b.x, uy = a.y - b.y, uz = a.z - b.z;
+    const float wx = c.x - b.x, wy = c.y - b.y, wz = c.z - b.z;
+    const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+    const float sn = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
+    const float cs = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
+    const float ru2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float rw2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+    const float dth = atan2f(sn, cs) - par.x;
+    // F_i = g (cs u / |u|^2 - w) / sn, F_k = g (cs w / |w|^2 - u) / sn, g = -k dth
+    const float g = -par.y * dth / sn;
+    const float au = cs / ru2, aw = cs / rw2;
+    const float fix = g * fmaf(au, ux, -wx), fiy = g * fmaf(au, uy, -wy), fiz = g * fmaf(au, uz, -wz);
+    const float fkx = g * fmaf(aw, wx, -ux), fky = g * fmaf(aw, wy, -uy), fkz = g * fmaf(aw, wz, -uz);
+    add_fix(sm, F, ijk.x, fix, fiy, fiz);
+    add_fix(sm, F, ijk.z, fkx, fky, fkz);
+    add_fix(sm, F, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
+    return ENERGY ? 0.5f * par.y * dth * dth : 0.0f;
+}
+
+// One native contact: (C - C0)^2 in float-float for z, C - C0 kept for the gradient.
+__device__ __forceinline__ long long contact_term(const Shared& sm, const TopoDev& tp,
+                                           const RunParams& P, int c) {
+    const int2 ij = tp.con_ij[c];
+    const float4 a = sm.xq[ij.x], b = sm.xq[ij.y];
+    const ff r2 = ff_r2(ff_diff(b.x, a.x), ff_diff(b.y, a.y), ff_diff(b.z, a.z));
+    const ff u = ff_mul(r2, P.inv_r0sq_ff);
+    const ff C = contact_C_ff(u);
+    const float2 c0 = tp.con_C0[c];
+    const ff d = ff_add(C, ff{-c0.x, -c0.y});
+    sm.cdelta[c] = d.hi + d.lo;
+    return ff2fix40(ff_sqr(d));
 }
 
 // Cluster helpers: CL == 1 degenerates to a plain CTA.
@@ -260,10 +231,9 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 template <int CL, class T>
-__device__ __forceinline__ T* peer_ptr(T* p) {
-    if (CL == 1) return nullptr;
-    cg::cluster_group c = cg::this_cluster();
-    return c.map_shared_rank(p, c.block_rank() ^ 1u);
+__device__ __forceinline__ T* rank_ptr(T* p, int rank) {
+    if (CL == 1) return p;
+    return cg::this_cluster().map_shared_rank(p, (unsigned)rank);
 }
 
 template <int CL>
@@ -272,24 +242,12 @@ __device__ __forceinline__ int cta_rank() {
     return (int)cg::this_cluster().block_rank();
 }
 
-// Force evaluation of the configuration in shared memory for the step of
-// parity b: this CTA's share of pairs, bonds/angles and contacts go to Fp[b];
-// partial z and energy are exchanged within the cluster; every CTA applies
-// the same ratchet decision; the bias gradient (when engaged) goes to Fb.
-// Must be called by all threads of all CTAs of the cluster.
-template <int ELEC, bool ENERGY, int CL>
-__device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
-                         bool do_ratchet) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int n = tp.n_atoms, nt = tp.n_tiles, ntp = nt * (nt + 1) / 2;
-    const int rank = cta_rank<CL>();
-    long long* F = sm.Fp[b];
-    sm.flag = &sc.flag[b];
-    // 1. tile bounding boxes (valid atoms only)
-    for (int t = warp; t < nt; t += nw) {
-        int a = t * kTile + lane;
-        if (a >= n) a = t * kTile;
-        const float4 p = sm.xq[a];
+// Bounding boxes of all tiles (whole CTA; valid atoms only).
+__device__ void tile_boxes(const Shared& sm, int n, int nt) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x >> 5; t < nt; t += nw) {
+        const int a = t * kTile + lane;
+        const float4 p = sm.xq[a < n ? a : t * kTile];
         float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -305,9 +263,23 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             sm.bhi[t] = make_float4(hx, hy, hz, 0.f);
         }
     }
-    if (tid == 0) sc.tp_count = 0;
-    __syncthreads();
-    // 2. this CTA's tile pairs (index = rank mod CL) whose boxes come within the cutoff
+}
+
+// Force evaluation of the configuration in shared memory (tile boxes already
+// current) for the evaluated step of parity b: this CTA's share of the work
+// goes to Fp[b]; per-warp shares of z and energy are combined in a fixed
+// order by every CTA of the cluster, which then takes the same ratchet
+// decision; the bias gradient (when engaged) goes to Fb. On entry tp_count and
+// work_next are zero. Ends with a barrier of the whole cluster.
+template <int ELEC, bool ENERGY, int CL>
+__device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
+                         bool do_ratchet) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nt = tp.n_tiles, ntp = nt * (nt + 1) / 2;
+    const int rank = cta_rank<CL>();
+    long long* F = sm.Fp[b];
+    sm.flag = &sc.flag[b];
+    // 1. this CTA's tile pairs (index = rank mod CL) whose boxes come within the cutoff
     for (int p = tid * CL + rank; p < ntp; p += blockDim.x * CL) {
         const uint32_t w = sm.tpl[p];
         const int I = (int)(w >> 16), J = (int)(w & 0xffff);
@@ -318,56 +290,66 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2) sm.tpa[atomicAdd(&sc.tp_count, 1)] = w;
     }
     __syncthreads();
-    // 3. non-bonded tile pairs, one per warp at a time
-    double e = 0.0;
-    const int ntpa = sc.tp_count;
-    for (int k = warp; k < ntpa; k += nw) {
-        const uint32_t w = sm.tpa[k];
-        const float ep = tile_pair<ELEC, ENERGY>(sm, F, tp, P.pc, (int)(w >> 16), (int)(w & 0xffff), lane);
-        if (ENERGY) e += (double)ep;
-    }
-    // 4. bonded terms
-    e += bonded<ENERGY>(sm, F, tp, rank, CL);
-    // 5. native contacts: z in float-float, C - C0 kept for the gradient pass
-    ff zacc = {0.0f, 0.0f};
-    if (P.bias == 1) {
-        for (int c = tid * CL + rank; c < tp.n_contacts; c += blockDim.x * CL) {
-            const int2 ij = tp.con_ij[c];
-            const float4 a = sm.xq[ij.x], bb = sm.xq[ij.y];
-            const ff r2 = ff_r2(ff_diff(bb.x, a.x), ff_diff(bb.y, a.y), ff_diff(bb.z, a.z));
-            const ff u = ff_mul(r2, P.inv_r0sq_ff);
-            const ff C = contact_C_ff(u);
-            const float2 c0 = tp.con_C0[c];
-            const ff d = ff_add(C, ff{-c0.x, -c0.y});
-            zacc = ff_add(zacc, ff_sqr(d));
-            sm.cdelta[c] = d.hi + d.lo;
+    // 2. work queue: half tile pairs, then contact, bond and angle chunks of this CTA
+    const int n_half = 2 * sc.tp_count;
+    const int ncl = P.bias == 1 ? (tp.n_contacts - rank + CL - 1) / CL : 0;
+    const int nbl = (tp.n_bonds - rank + CL - 1) / CL, nal = (tp.n_angles - rank + CL - 1) / CL;
+    const int e_con = n_half + (ncl + kChunk - 1) / kChunk;
+    const int e_bond = e_con + (nbl + kChunk - 1) / kChunk;
+    const int e_all = e_bond + (nal + kChunk - 1) / kChunk;
+    long long e = 0, zacc = 0;  // fixed point: sums independent of the work order
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&sc.work_next, 1);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= e_all) break;
+        if (k < n_half) {
+            const uint32_t w = sm.tpa[k >> 1];
+            const float ep = half_tile<ELEC, ENERGY>(sm, F, tp, P.pc, (int)(w >> 16),
+                                                     (int)(w & 0xffff), k & 1, lane);
+            if (ENERGY) e += f2fix(ep);
+        } else if (k < e_con) {
+            const int loc = (k - n_half) * kChunk + lane;
+            if (loc < ncl) zacc += contact_term(sm, tp, P, loc * CL + rank);
+        } else if (k < e_bond) {
+            const int loc = (k - e_con) * kChunk + lane;
+            if (loc < nbl) {
+                const float eb = bond_term<ENERGY>(sm, F, tp, loc * CL + rank);
+                if (ENERGY) e += f2fix(eb);
+            }
+        } else {
+            const int loc = (k - e_bond) * kChunk + lane;
+            if (loc < nal) {
+                const float ea = angle_term<ENERGY>(sm, F, tp, loc * CL + rank);
+                if (ENERGY) e += f2fix(ea);
+            }
         }
     }
-    const ff zsum = block_sum_ff(zacc, sc);
-    double esum = 0.0;
-    if (ENERGY) esum = block_sum_d(e, sc);
-    if (tid == 0) {
-        sc.zpart[b] = zsum;
-        sc.epart[b] = esum;
+    zacc = warp_sum_ll(zacc);
+    if (ENERGY) e = warp_sum_ll(e);
+    if (lane == 0) {
+        sc.red_z[b][warp] = zacc;
+        sc.red_e[b][warp] = e;
     }
-    // 6. exchange within the cluster; every CTA takes the same ratchet decision
+    // 3. exchange within the cluster; every CTA adds the shares in the same order
     cluster_barrier<CL>();
     if (tid == 0) {
-        ff zt = sc.zpart[b];
-        double et = sc.epart[b];
-        int fl = sc.flag[b];
-        if (CL == 2) {
-            const ff zp = *peer_ptr<CL>(&sc.zpart[b]);
-            const double ep = *peer_ptr<CL>(&sc.epart[b]);
-            fl |= *peer_ptr<CL>(&sc.flag[b]);
-            zt = rank == 0 ? ff_add(zt, zp) : ff_add(zp, zt);  // rank-0 share first
-            et = rank == 0 ? et + ep : ep + et;
+        long long zt = 0, et = 0;
+        int fl = 0;
+        for (int q = 0; q < CL; ++q) {
+            const long long* rz = rank_ptr<CL>(&sc.red_z[b][0], q);
+            const long long* re = rank_ptr<CL>(&sc.red_e[b][0], q);
+            for (int w = 0; w < nw; ++w) {
+                zt += rz[w];
+                if (ENERGY) et += re[w];
+            }
+            fl |= *rank_ptr<CL>(&sc.flag[b], q);
         }
-        if (ENERGY) sc.epot = et;
+        if (ENERGY) sc.epot = (double)et * 9.5367431640625e-07;  // 2^-20
         if (fl) sc.status |= SCPS_FLAG_FORCE_RANGE;
         double factor = 0.0;
         if (P.bias == 1) {
-            const double z = ff_to_double(zt);
+            const double z = (double)zt * 9.094947017729282e-13;  // 2^-40
             sc.z = z;
             if (do_ratchet) {  // Eq. (FrMD) with theta(0) = 1
                 if (z < sc.zm)
@@ -380,7 +362,7 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         sc.bias_on = factor != 0.0;
     }
     __syncthreads();
-    // 7. bias force factor * grad z (only when the ratchet is engaged)
+    // 4. bias force factor * grad z (only when the ratchet is engaged)
     if (sc.bias_on) {
         for (int i = tid; i < 3 * sm.nta; i += blockDim.x) sm.Fb[i] = 0;
         __syncthreads();
@@ -399,7 +381,7 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     }
 }
 
-// Sum of this CTA's and the peer's fixed-point partials for component k of atom i.
+// Sum of this CTA's and the peer's fixed-point partials at index idx.
 template <int CL>
 __device__ __forceinline__ float sum_fix(const long long* own, const long long* peer, int idx) {
     long long v = own[idx];
@@ -412,16 +394,16 @@ __device__ __forceinline__ float sum_fix(const long long* own, const long long* 
 template <int ELEC, int CL>
 __global__ void __launch_bounds__(1024, 1)
 k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, StateDev st,
-           RunParams P, int nta, int ntp_max, int ncon_max) {
+           RunParams P, int nta, int ntp_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const int r = blockIdx.x / CL;
     const int rank = cta_rank<CL>();
     const RepDev rep = reps[r];
     const TopoDev tp = topos[rep.topo];
-    Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
+    Shared sm = carve(smem_raw, nta, ntp_max);
     const int n = tp.n_atoms, nt = tp.n_tiles;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nta3 = 3 * nta;
 
     for (int i = tid; i < nta; i += blockDim.x) {
@@ -459,113 +441,145 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         sc.flag[0] = 0;
         sc.flag[1] = 0;
         sc.bias_on = 0;
+        sc.tp_count = 0;
+        sc.work_next = 0;
     }
     long long step = st.step[r];
+    __syncthreads();
+    tile_boxes(sm, n, nt);
     cluster_barrier<CL>();  // every CTA of the cluster is initialised before any remote access
-    const long long* pFp[2] = {peer_ptr<CL>(sm.Fp[0]), peer_ptr<CL>(sm.Fp[1])};
-    const long long* pFb = peer_ptr<CL>(sm.Fb);
-    if (sc.status == 0) evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true);
-
+    const int peer = rank ^ 1;
+    const long long* pFp[2] = {CL == 2 ? rank_ptr<CL>(sm.Fp[0], peer) : nullptr,
+                               CL == 2 ? rank_ptr<CL>(sm.Fp[1], peer) : nullptr};
+    const long long* pFb = CL == 2 ? rank_ptr<CL>(sm.Fb, peer) : nullptr;
     const float hdt = P.half_dt;
-    for (long long s = 0; s < P.n_steps; ++s) {
-        if (sc.status != 0) break;  // frozen replica (identical in every CTA of the cluster)
-        const int b = (int)(step & 1), nb = b ^ 1;
-        const long long* own = sm.Fp[b];
-        const bool bias = sc.bias_on;
-        // B A O A (every CTA integrates every atom)
-        for (int i = tid; i < n; i += blockDim.x) {
-            const float im = tp.inv_m[i];
-            float fx = sum_fix<CL>(own, pFp[b], i), fy = sum_fix<CL>(own, pFp[b], nta + i),
-                  fz = sum_fix<CL>(own, pFp[b], 2 * nta + i);
-            if (bias) {
-                fx += sum_fix<CL>(sm.Fb, pFb, i);
-                fy += sum_fix<CL>(sm.Fb, pFb, nta + i);
-                fz += sum_fix<CL>(sm.Fb, pFb, 2 * nta + i);
-            }
-            float4 v = sm.v[i];
-            float4 x = sm.xq[i];
-            v.x = fmaf(hdt * im, fx, v.x);
-            v.y = fmaf(hdt * im, fy, v.y);
-            v.z = fmaf(hdt * im, fz, v.z);
-            x.x = fmaf(hdt, v.x, x.x);
-            x.y = fmaf(hdt, v.y, x.y);
-            x.z = fmaf(hdt, v.z, x.z);
-            const uint4 rb = philox4x32_10(make_uint4((uint32_t)i, rep.rep_id, (uint32_t)step, 0u),
-                                           P.key0, P.key1);
-            const float4 xi = normals4_f32(rb);
-            const float sd = tp.noise_sd[i];
-            v.x = fmaf(P.c1, v.x, sd * xi.x);
-            v.y = fmaf(P.c1, v.y, sd * xi.y);
-            v.z = fmaf(P.c1, v.z, sd * xi.z);
-            x.x = fmaf(hdt, v.x, x.x);
-            x.y = fmaf(hdt, v.y, x.y);
-            x.z = fmaf(hdt, v.z, x.z);
-            if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
-                  isfinite(v.y) && isfinite(v.z)))
-                atomicOr(&sc.status, SCPS_FLAG_NONFINITE);
-            sm.v[i] = v;
-            sm.xq[i] = x;
-        }
-        // this CTA's partials of the next evaluation start from zero
-        for (int i = tid; i < nta3; i += blockDim.x) sm.Fp[nb][i] = 0;
-        if (tid == 0) sc.flag[nb] = 0;
-        __syncthreads();
-        if (sc.status != 0) break;  // non-finite state: identical decision in every CTA
-        ++step;
-        const bool save = P.save_interval > 0 && (step % P.save_interval) == 0;
-        if (save)
-            evaluate<ELEC, true, CL>(sm, sc, tp, P, nb, true);
-        else
-            evaluate<ELEC, false, CL>(sm, sc, tp, P, nb, true);
-        // B, and the bias functional sum_i |F_bias,i|^2 / (m_i gamma) dt
-        const long long slot = sc.n_saved % P.max_frames;
-        const bool bias2 = sc.bias_on;
-        const long long* own2 = sm.Fp[nb];
-        float tb = 0.f;
-        for (int i = tid; i < n; i += blockDim.x) {
-            const float im = tp.inv_m[i];
-            float fx = sum_fix<CL>(own2, pFp[nb], i), fy = sum_fix<CL>(own2, pFp[nb], nta + i),
-                  fz = sum_fix<CL>(own2, pFp[nb], 2 * nta + i);
-            if (bias2) {
-                const float bx = sum_fix<CL>(sm.Fb, pFb, i), by = sum_fix<CL>(sm.Fb, pFb, nta + i),
-                            bz = sum_fix<CL>(sm.Fb, pFb, 2 * nta + i);
-                tb += (bx * bx + by * by + bz * bz) * im;
-                fx += bx;
-                fy += by;
-                fz += bz;
-            }
-            float4 v = sm.v[i];
-            v.x = fmaf(hdt * im, fx, v.x);
-            v.y = fmaf(hdt * im, fy, v.y);
-            v.z = fmaf(hdt * im, fz, v.z);
-            sm.v[i] = v;
-            if (save && rank == 0) {
-                float* fr = st.frames + 3 * (rep.frame_off + slot * n + i);
-                const float4 x = sm.xq[i];
-                fr[0] = x.x;
-                fr[1] = x.y;
-                fr[2] = x.z;
-            }
-        }
-        if (bias2) {
-            const float tsum = block_sum_f(tb, sc);
-            if (tid == 0) sc.T += (double)P.dt / P.gamma * (double)tsum;
-        }
-        if (save) {
-            __syncthreads();  // every thread has used sc.n_saved for this frame
-            if (tid == 0) {
-                if (rank == 0) {
-                    const long long fi = (long long)r * P.max_frames + slot;
-                    st.fz[fi] = sc.z;
-                    st.fzm[fi] = sc.zm;
-                    st.fe[fi] = sc.epot;
-                    st.fT[fi] = sc.T;
+    if (sc.status == 0 && P.n_steps > 0) {
+        evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true);
+        for (long long s = 0; s <= P.n_steps; ++s) {
+            // B of the step just evaluated (s > 0), then A of the next one (s < n_steps)
+            const bool do_b = s > 0, do_a = s < P.n_steps;
+            const int b = (int)(step & 1), nb = b ^ 1;
+            const bool bias = sc.bias_on;
+            const bool save = do_b && P.save_interval > 0 && (step % P.save_interval) == 0;
+            const long long slot = sc.n_saved % P.max_frames;
+            const long long* own = sm.Fp[b];
+            float tb = 0.f;
+            for (int base = 0; base < nta; base += blockDim.x) {
+                const int i = base + tid;
+                float4 x = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+                bool valid = i < n;
+                if (valid) {
+                    const float im = tp.inv_m[i];
+                    float fx = sum_fix<CL>(own, pFp[b], i), fy = sum_fix<CL>(own, pFp[b], nta + i),
+                          fz = sum_fix<CL>(own, pFp[b], 2 * nta + i);
+                    if (bias) {
+                        const float bx = sum_fix<CL>(sm.Fb, pFb, i), by = sum_fix<CL>(sm.Fb, pFb, nta + i),
+                                    bz = sum_fix<CL>(sm.Fb, pFb, 2 * nta + i);
+                        if (do_b) tb += (bx * bx + by * by + bz * bz) * im;
+                        fx += bx;
+                        fy += by;
+                        fz += bz;
+                    }
+                    float4 v = sm.v[i];
+                    x = sm.xq[i];
+                    if (do_b) {  // B: closes the evaluated step
+                        v.x = fmaf(hdt * im, fx, v.x);
+                        v.y = fmaf(hdt * im, fy, v.y);
+                        v.z = fmaf(hdt * im, fz, v.z);
+                        if (save && rank == 0) {
+                            float* fr = st.frames + 3 * (rep.frame_off + slot * n + i);
+                            fr[0] = x.x;
+                            fr[1] = x.y;
+                            fr[2] = x.z;
+                        }
+                    }
+                    if (do_a) {  // B A O A of the next step
+                        v.x = fmaf(hdt * im, fx, v.x);
+                        v.y = fmaf(hdt * im, fy, v.y);
+                        v.z = fmaf(hdt * im, fz, v.z);
+                        x.x = fmaf(hdt, v.x, x.x);
+                        x.y = fmaf(hdt, v.y, x.y);
+                        x.z = fmaf(hdt, v.z, x.z);
+                        const uint4 rb = philox4x32_10(
+                            make_uint4((uint32_t)i, rep.rep_id, (uint32_t)step, 0u), P.key0, P.key1);
+                        const float4 xi = normals4_f32(rb);
+                        const float sd = tp.noise_sd[i];
+                        v.x = fmaf(P.c1, v.x, sd * xi.x);
+                        v.y = fmaf(P.c1, v.y, sd * xi.y);
+                        v.z = fmaf(P.c1, v.z, sd * xi.z);
+                        x.x = fmaf(hdt, v.x, x.x);
+                        x.y = fmaf(hdt, v.y, x.y);
+                        x.z = fmaf(hdt, v.z, x.z);
+                        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
+                              isfinite(v.y) && isfinite(v.z)))
+                            atomicOr(&sc.status, SCPS_FLAG_NONFINITE);
+                        sm.xq[i] = x;
+                    }
+                    sm.v[i] = v;
                 }
-                sc.n_saved += 1;
+                if (do_a) {  // bounding box of this warp's tile at the new positions
+                    float lx = x.x, ly = x.y, lz = x.z;
+                    float hx = valid ? x.x : -3.0e38f, hy = valid ? x.y : -3.0e38f,
+                          hz = valid ? x.z : -3.0e38f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
+                        ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+                        lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
+                        hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+                        hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
+                        hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+                    }
+                    const int t = (base >> 5) + warp;
+                    if (lane == 0 && t < nt) {
+                        sm.blo[t] = make_float4(lx, ly, lz, 0.f);
+                        sm.bhi[t] = make_float4(hx, hy, hz, 0.f);
+                    }
+                }
             }
+            // this CTA's partials of the next evaluation start from zero
+            if (do_a)
+                for (int i = tid; i < nta3; i += blockDim.x) sm.Fp[nb][i] = 0;
+            if (bias && do_b) {
+                tb = warp_sum_f(tb);
+                if (lane == 0) sc.red_t[warp] = tb;
+            }
+            if (tid == 0) {
+                sc.flag[nb] = 0;
+                sc.tp_count = 0;
+                sc.work_next = 0;
+            }
+            __syncthreads();
+            if (tid == 0 && do_b) {
+                if (bias) {
+                    float tsum = 0.f;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += sc.red_t[w];
+                    sc.T += (double)P.dt / P.gamma * (double)tsum;
+                }
+                if (save) {
+                    if (rank == 0) {
+                        const long long fi = (long long)r * P.max_frames + slot;
+                        st.fz[fi] = sc.z;
+                        st.fzm[fi] = sc.zm;
+                        st.fe[fi] = sc.epot;
+                        st.fT[fi] = sc.T;
+                    }
+                    sc.n_saved += 1;
+                }
+            }
+            // leave after the last B, or when the new state is non-finite (identical in
+            // every CTA of the cluster: same inputs, same arithmetic)
+            if (!do_a || sc.status != 0) break;
+            ++step;
+            const bool save_next = P.save_interval > 0 && (step % P.save_interval) == 0;
+            if (save_next)
+                evaluate<ELEC, true, CL>(sm, sc, tp, P, nb, true);
+            else
+                evaluate<ELEC, false, CL>(sm, sc, tp, P, nb, true);
+            if (sc.status != 0) break;  // force out of range: frozen before the update
         }
-        __syncthreads();
     }
+    __syncthreads();
     // write back the state (rank 0; every CTA holds the same copy)
     if (rank == 0) {
         for (int i = tid; i < n; i += blockDim.x) {
@@ -590,11 +604,11 @@ template <int ELEC>
 __global__ void __launch_bounds__(1024, 1)
 k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
               double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta,
-              int ntp_max, int ncon_max) {
+              int ntp_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const TopoDev tp = *topo_ptr;
-    Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
+    Shared sm = carve(smem_raw, nta, ntp_max);
     const int n = tp.n_atoms, nt = tp.n_tiles;
     const long long f = blockIdx.x;
     const float* xf = X + f * n * 3;
@@ -622,7 +636,11 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
         sc.z = 0.0;
         sc.status = 0;
         sc.flag[0] = 0;
+        sc.tp_count = 0;
+        sc.work_next = 0;
     }
+    __syncthreads();
+    tile_boxes(sm, n, nt);
     __syncthreads();
     evaluate<ELEC, true, 1>(sm, sc, tp, P, 0, false);
     if (F) {
@@ -667,7 +685,7 @@ static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta, ntp_max, ncon_max);
+    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta, ntp_max);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -701,7 +719,7 @@ static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_eval_frames<ELEC><<<(unsigned)n_frames, threads, smem, stream>>>(topo, P, X, U, F, Z, nta,
-                                                                       ntp_max, ncon_max);
+                                                                       ntp_max);
     return cudaGetLastError();
 }
 

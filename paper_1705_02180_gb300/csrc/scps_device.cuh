@@ -146,6 +146,20 @@ __device__ __forceinline__ ff ff_div(ff x, ff y) {
 
 __device__ __forceinline__ double ff_to_double(ff x) { return (double)x.hi + (double)x.lo; }
 
+// round(x * 2^40) of a float-float x with 0 <= x.hi <= 1 (a native-contact
+// term (C - C0)^2): the z sum is accumulated as int64 multiples of 2^-40, so it
+// does not depend on the order in which warps add their terms.
+__device__ __forceinline__ long long ff2fix40(ff x) {
+    const float magic = 12582912.0f;                     // 1.5 * 2^23
+    const float a = x.hi * 1048576.0f;                   // x.hi * 2^20, |a| <= 2^20
+    const float t = __fadd_rn(a, magic);
+    const int q1 = __float_as_int(t) - 0x4B400000;       // round(a)
+    const float rem = __fsub_rn(a, __fsub_rn(t, magic)); // exact, |rem| <= 1/2
+    const float b = __fmaf_rn(x.lo, 1099511627776.0f, rem * 1048576.0f);  // (rem + lo 2^20) 2^20
+    const int q2 = __float_as_int(__fadd_rn(b, magic)) - 0x4B400000;
+    return ((long long)q1 << 20) + (long long)q2;
+}
+
 __device__ __forceinline__ ff ff_from_double(double d) {
     const float hi = __double2float_rn(d);
     return {hi, __double2float_rn(d - (double)hi)};
