@@ -2,21 +2,19 @@
 //
 // One thread-block cluster of CL CTAs (CL = 1 or 2) owns one replica for a
 // whole launch of n_steps steps. Positions, velocities and int64 fixed-point
-// force partials live in shared memory; the CTAs of a cluster split the force
-// work and read each other's partials through distributed shared memory.
-// Every step evaluates
-//   bonded terms + non-bonded pairs (32 x 32 tile pairs, skipped when their
-//   bounding boxes are farther apart than the cutoff)            -grad U
+// force partials live in shared memory; the CTAs of a cluster pull force work
+// from one queue (a counter in the shared memory of CTA 0) and read each
+// other's partials through distributed shared memory. Every step evaluates
+//   bonded terms + non-bonded pairs (32 x 16 half tile pairs, skipped when
+//   their bounding boxes are farther apart than the cutoff)       -grad U
 //   z(X) of Eq. (zrMD) from C_ij of Eq. (Cij) in float-float     collective coordinate
 //   ratchet of Eq. (FrMD) in FP64 (z < z_m: z_m = z, no bias)   bias force
 //   BAOAB update with Philox4x32-10 noise (Eq. Lang)
 // and writes a frame every save_interval steps. Every CTA of a cluster
 // integrates all atoms of the replica with the same total force, so their
-// copies of the state stay identical without being exchanged.
-//
-// Work inside a CTA is pulled from a queue by warps (half tile pairs first,
-// then chunks of 32 native contacts, bonds and angles), so no warp idles at
-// the barrier that follows while another still holds several work items.
+// copies of the state stay identical without being exchanged. All sums that
+// several warps contribute to are fixed point, so results do not depend on
+// which warp or CTA took which work item.
 #include <cooperative_groups.h>
 
 #include "scps_internal.h"
@@ -33,65 +31,61 @@ constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per 
 struct Shared {
     float4* xq;         // (x, y, z, qs)
     float4* v;          // velocities
+    float4* fb;         // bias force per atom (computed by the atom's thread)
     float2* lj;         // (sigma/2, sqrt(24 eps))
     long long* Fp[2];   // 3 x nta force partials of this CTA, by parity of the evaluated step
-    long long* Fb;      // 3 x nta bias-force partial of this CTA
-    float4* blo;        // tile bounding boxes
+    float4* blo;        // tile bounding boxes, then half-tile boxes (2 per tile)
     float4* bhi;
     uint32_t* tpl;      // all tile pairs (I << 16 | J), I <= J
-    uint32_t* tpa;      // active tile pairs of this CTA
-    float* cdelta;      // C - C0 per native contact (FP32 copy of the float-float value)
+    uint32_t* items;    // active half-tile pairs: I | J << 11 | h << 22
+    float* hcoef[2];    // per native contact: (C - C0) dC/du, by parity of the evaluated step
     int* flag;          // force-range flag of the current evaluation
-    int nta;
+    int nta, nt;
 };
 
 struct Scalars {
-    int tp_count;
-    int work_next;
+    int n_items;
+    int work_next[2];   // work counters by parity (the cluster uses the one of CTA 0)
     int status;         // replica status (identical in every CTA of a cluster)
     int bias_on;
     int flag[2];        // force-range bits raised during the evaluation of a given parity
+    int scan[33];
     long long n_saved;
     double zm, z, factor, epot, T;
-    long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity (read by the peer)
-    long long red_e[2][32];  // per-warp shares of the potential energy (units of 2^-20), by parity
-    float red_t[32];    // per-warp shares of sum |F_bias|^2 / m
+    long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity
+    long long red_e[2][32];  // per-warp shares of the potential energy (units of 2^-20)
+    float red_t[32];         // per-warp shares of sum |F_bias|^2 / m
 };
 
-__device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max) {
+__device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int ncon_max) {
     Shared s;
     char* p = (char*)base;
     s.nta = nta;
+    s.nt = nta / kTile;
     s.xq = (float4*)p; p += sizeof(float4) * nta;
     s.v = (float4*)p; p += sizeof(float4) * nta;
+    s.fb = (float4*)p; p += sizeof(float4) * nta;
+    s.blo = (float4*)p; p += sizeof(float4) * 3 * s.nt;
+    s.bhi = (float4*)p; p += sizeof(float4) * 3 * s.nt;
     s.Fp[0] = (long long*)p; p += sizeof(long long) * 3 * nta;
     s.Fp[1] = (long long*)p; p += sizeof(long long) * 3 * nta;
-    s.Fb = (long long*)p; p += sizeof(long long) * 3 * nta;
     s.lj = (float2*)p; p += sizeof(float2) * nta;
-    const int nt = nta / kTile;
-    s.blo = (float4*)p; p += sizeof(float4) * nt;
-    s.bhi = (float4*)p; p += sizeof(float4) * nt;
     const int ntp4 = (ntp_max + 3) & ~3;
     s.tpl = (uint32_t*)p; p += sizeof(uint32_t) * ntp4;
-    s.tpa = (uint32_t*)p; p += sizeof(uint32_t) * ntp4;
-    s.cdelta = (float*)p;
+    s.items = (uint32_t*)p; p += sizeof(uint32_t) * 2 * ntp4;
+    s.hcoef[0] = (float*)p; p += sizeof(float) * ncon_max;
+    s.hcoef[1] = (float*)p;
     s.flag = nullptr;
     return s;
 }
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     return v;
@@ -118,15 +112,15 @@ __device__ __forceinline__ void add_fix(const Shared& sm, long long* F, int i, f
 // owns atom i = 32 I + l; within each 16-lane half-warp, lane l takes j slot
 // 16h + ((l + t) & 15) at iteration t and the j-force accumulators rotate one
 // lane per iteration, so lane l ends with slot l & 15; the two half-warps'
-// shares of each j are then added with one exchange.
-template <int ELEC, bool ENERGY>
+// shares of each j are then added with one exchange. NEAR tile pairs
+// (J - I <= 1) test exclusions and, on the diagonal, keep j > i only.
+template <int ELEC, bool ENERGY, bool NEAR>
 __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const TopoDev& tp,
                                            const PairConst& pc, int I, int J, int h, int lane) {
     const int i = I * kTile + lane;
     const float4 xi = sm.xq[i];
     const float2 li = sm.lj[i];
-    const bool near = (J - I) <= 1;
-    const unsigned long long em = (near && i < tp.n_atoms) ? tp.excl[i] : 0ull;
+    const unsigned long long em = (NEAR && i < tp.n_atoms) ? tp.excl[i] : 0ull;
     const int g16 = lane & 16, l16 = lane & 15;
     const int jb = J * kTile + 16 * h;
     float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
@@ -139,10 +133,10 @@ __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const
         const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         bool ok = r2 < pc.rc2;
-        if (I == J) ok = ok && (j > i);
-        if (near) {
-            const int dj = j - i + kExclWindow;
-            if (dj >= 0 && dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
+        if (NEAR) {
+            const int dj = j - i + kExclWindow;  // in [1, 95]: j - i in (-32, 64)
+            ok = ok && (I != J || j > i);
+            if (dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
         }
         float e = 0.f;
         float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
@@ -169,7 +163,7 @@ __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const
 
 template <bool ENERGY>
 __device__ __forceinline__ float bond_term(const Shared& sm, long long* F, const TopoDev& tp,
-                                            int b) {
+                                           int b) {
     const int2 ij = tp.bond_ij[b];
     const float2 par = tp.bond_par[b];
     const float4 a = sm.xq[ij.x], c = sm.xq[ij.y];
@@ -184,7 +178,7 @@ __device__ __forceinline__ float bond_term(const Shared& sm, long long* F, const
 
 template <bool ENERGY>
 __device__ __forceinline__ float angle_term(const Shared& sm, long long* F, const TopoDev& tp,
-                                             int q) {
+                                            int q) {
     const int4 ijk = tp.ang_ijk[q];
     const float2 par = tp.ang_par[q];
     const float4 a = sm.xq[ijk.x], b = sm.xq[ijk.y], c = sm.xq[ijk.z];
@@ -205,20 +199,6 @@ __device__ __forceinline__ float angle_term(const Shared& sm, long long* F, cons
     add_fix(sm, F, ijk.z, fkx, fky, fkz);
     add_fix(sm, F, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
     return ENERGY ? 0.5f * par.y * dth * dth : 0.0f;
-}
-
-// One native contact: (C - C0)^2 in float-float for z, C - C0 kept for the gradient.
-__device__ __forceinline__ long long contact_term(const Shared& sm, const TopoDev& tp,
-                                           const RunParams& P, int c) {
-    const int2 ij = tp.con_ij[c];
-    const float4 a = sm.xq[ij.x], b = sm.xq[ij.y];
-    const ff r2 = ff_r2(ff_diff(b.x, a.x), ff_diff(b.y, a.y), ff_diff(b.z, a.z));
-    const ff u = ff_mul(r2, P.inv_r0sq_ff);
-    const ff C = contact_C_ff(u);
-    const float2 c0 = tp.con_C0[c];
-    const ff d = ff_add(C, ff{-c0.x, -c0.y});
-    sm.cdelta[c] = d.hi + d.lo;
-    return ff2fix40(ff_sqr(d));
 }
 
 // Cluster helpers: CL == 1 degenerates to a plain CTA.
@@ -242,35 +222,128 @@ __device__ __forceinline__ int cta_rank() {
     return (int)cg::this_cluster().block_rank();
 }
 
-// Bounding boxes of all tiles (whole CTA; valid atoms only).
-__device__ void tile_boxes(const Shared& sm, int n, int nt) {
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int t = threadIdx.x >> 5; t < nt; t += nw) {
-        const int a = t * kTile + lane;
-        const float4 p = sm.xq[a < n ? a : t * kTile];
-        float lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
+// One native contact: (C - C0)^2 in float-float, returned as a 2^-40 fixed-point
+// value; (C - C0) dC/du is stored for the bias gradient in every CTA of the cluster.
+template <int CL>
+__device__ __forceinline__ long long contact_term(float* own_hcoef, float* peer_hcoef,
+                                                  const Shared& sm, const TopoDev& tp,
+                                                  const RunParams& P, int c) {
+    const int2 ij = tp.con_ij[c];
+    const float4 a = sm.xq[ij.x], b = sm.xq[ij.y];
+    const ff r2 = ff_r2(ff_diff(b.x, a.x), ff_diff(b.y, a.y), ff_diff(b.z, a.z));
+    const ff u = ff_mul(r2, P.inv_r0sq_ff);
+    const ff C = contact_C_ff(u);
+    const float2 c0 = tp.con_C0[c];
+    const ff d = ff_add(C, ff{-c0.x, -c0.y});
+    const float h = (d.hi + d.lo) * contact_dC_du(u.hi);
+    own_hcoef[c] = h;
+    if (CL == 2) peer_hcoef[c] = h;
+    return ff2fix40(ff_sqr(d));
+}
+
+// Box of 32 positions of one warp (invalid lanes hold +inf/-inf sentinels):
+// lane 0 writes the tile box, lanes 0 and 16 the two half-tile boxes.
+__device__ __forceinline__ void warp_boxes(const Shared& sm, int t, float4 lo, float4 hi,
+                                           int lane) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
-            ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
-            lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
-            hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
-            hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
-            hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
-        }
-        if (lane == 0) {
-            sm.blo[t] = make_float4(lx, ly, lz, 0.f);
-            sm.bhi[t] = make_float4(hx, hy, hz, 0.f);
-        }
+    for (int o = 8; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
+    }
+    if (t < sm.nt && (lane & 15) == 0) {
+        sm.blo[sm.nt + 2 * t + (lane >> 4)] = lo;
+        sm.bhi[sm.nt + 2 * t + (lane >> 4)] = hi;
+    }
+    lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, 16));
+    lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, 16));
+    lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, 16));
+    hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, 16));
+    hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, 16));
+    hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, 16));
+    if (t < sm.nt && lane == 0) {
+        sm.blo[t] = lo;
+        sm.bhi[t] = hi;
     }
 }
 
-// Force evaluation of the configuration in shared memory (tile boxes already
-// current) for the evaluated step of parity b: this CTA's share of the work
-// goes to Fp[b]; per-warp shares of z and energy are combined in a fixed
-// order by every CTA of the cluster, which then takes the same ratchet
-// decision; the bias gradient (when engaged) goes to Fb. On entry tp_count and
-// work_next are zero. Ends with a barrier of the whole cluster.
+// Tile and half-tile boxes of the positions in shared memory (whole CTA).
+__device__ void all_boxes(const Shared& sm, int n) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < sm.nta; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+        float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
+        if (i < n) {  // i may run past the nta-entry arrays: no load then
+            lo = sm.xq[i];
+            hi = lo;
+        }
+        warp_boxes(sm, (base >> 5) + (threadIdx.x >> 5), lo, hi, lane);
+    }
+}
+
+__device__ __forceinline__ float box_gap2(float4 al, float4 ah, float4 bl, float4 bh) {
+    const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
+    const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
+    const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
+    return fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+}
+
+// Active half-tile pairs in a fixed order (identical in every CTA of a cluster).
+__device__ void build_items(const Shared& sm, Scalars& sc, int ntp, float rc2) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    int carry = 0;
+    for (int base = 0; base < ntp; base += blockDim.x) {
+        const int p = base + tid;
+        unsigned m = 0;
+        uint32_t w = 0;
+        if (p < ntp) {
+            w = sm.tpl[p];
+            const int I = (int)(w >> 16), J = (int)(w & 0xffff);
+            const float4 al = sm.blo[I], ah = sm.bhi[I];
+            if (box_gap2(al, ah, sm.blo[sm.nt + 2 * J], sm.bhi[sm.nt + 2 * J]) < rc2) m |= 1u;
+            if (box_gap2(al, ah, sm.blo[sm.nt + 2 * J + 1], sm.bhi[sm.nt + 2 * J + 1]) < rc2) m |= 2u;
+        }
+        const int cnt = __popc(m);
+        int x = cnt;  // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sc.scan[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = lane < nw ? sc.scan[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, t, o);
+                if (lane >= o) t += y;
+            }
+            sc.scan[lane] = t;
+        }
+        __syncthreads();
+        int pos = carry + (warp > 0 ? sc.scan[warp - 1] : 0) + x - cnt;
+        if (m) {
+            const uint32_t I = w >> 16, J = w & 0xffff;
+            if (m & 1u) sm.items[pos++] = I | (J << 11);
+            if (m & 2u) sm.items[pos] = I | (J << 11) | (1u << 22);
+        }
+        carry += sc.scan[nw - 1];
+        __syncthreads();
+    }
+    if (tid == 0) sc.n_items = carry;
+    __syncthreads();
+}
+
+// Force evaluation of the configuration in shared memory (boxes current) for
+// the evaluated step of parity b. Work items come from the queue of the
+// cluster; this CTA's share goes to Fp[b]; the ratchet decision is taken by
+// every CTA from the same fixed-point sums; with the bias engaged, every CTA
+// fills fb for all atoms. On return the CTA is synchronised.
 template <int ELEC, bool ENERGY, int CL>
 __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
                          bool do_ratchet) {
@@ -279,48 +352,44 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     const int rank = cta_rank<CL>();
     long long* F = sm.Fp[b];
     sm.flag = &sc.flag[b];
-    // 1. this CTA's tile pairs (index = rank mod CL) whose boxes come within the cutoff
-    for (int p = tid * CL + rank; p < ntp; p += blockDim.x * CL) {
-        const uint32_t w = sm.tpl[p];
-        const int I = (int)(w >> 16), J = (int)(w & 0xffff);
-        const float4 al = sm.blo[I], ah = sm.bhi[I], bl = sm.blo[J], bh = sm.bhi[J];
-        const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
-        const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
-        const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
-        if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2) sm.tpa[atomicAdd(&sc.tp_count, 1)] = w;
-    }
-    __syncthreads();
-    // 2. work queue: half tile pairs, then contact, bond and angle chunks of this CTA
-    const int n_half = 2 * sc.tp_count;
-    const int ncl = P.bias == 1 ? (tp.n_contacts - rank + CL - 1) / CL : 0;
-    const int nbl = (tp.n_bonds - rank + CL - 1) / CL, nal = (tp.n_angles - rank + CL - 1) / CL;
-    const int e_con = n_half + (ncl + kChunk - 1) / kChunk;
-    const int e_bond = e_con + (nbl + kChunk - 1) / kChunk;
-    const int e_all = e_bond + (nal + kChunk - 1) / kChunk;
+    build_items(sm, sc, ntp, P.pc.rc2);
+    // work queue: half tile pairs, then contact, bond and angle chunks
+    const int n_half = sc.n_items;
+    const int ncon = P.bias == 1 ? tp.n_contacts : 0;
+    const int e_con = n_half + (ncon + kChunk - 1) / kChunk;
+    const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
+    const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
+    int* counter = rank_ptr<CL>(&sc.work_next[b], 0);
+    float* own_hcoef = sm.hcoef[b];
+    float* peer_hcoef = CL == 2 ? rank_ptr<CL>(sm.hcoef[b], rank ^ 1) : nullptr;
     long long e = 0, zacc = 0;  // fixed point: sums independent of the work order
     for (;;) {
         int k = 0;
-        if (lane == 0) k = atomicAdd(&sc.work_next, 1);
+        if (lane == 0) k = atomicAdd(counter, 1);
         k = __shfl_sync(kFull, k, 0);
         if (k >= e_all) break;
         if (k < n_half) {
-            const uint32_t w = sm.tpa[k >> 1];
-            const float ep = half_tile<ELEC, ENERGY>(sm, F, tp, P.pc, (int)(w >> 16),
-                                                     (int)(w & 0xffff), k & 1, lane);
+            const uint32_t w = sm.items[k];
+            const int I = (int)(w & 0x7ff), J = (int)((w >> 11) & 0x7ff), h = (int)(w >> 22);
+            float ep;
+            if (J - I <= 1)
+                ep = half_tile<ELEC, ENERGY, true>(sm, F, tp, P.pc, I, J, h, lane);
+            else
+                ep = half_tile<ELEC, ENERGY, false>(sm, F, tp, P.pc, I, J, h, lane);
             if (ENERGY) e += f2fix(ep);
         } else if (k < e_con) {
-            const int loc = (k - n_half) * kChunk + lane;
-            if (loc < ncl) zacc += contact_term(sm, tp, P, loc * CL + rank);
+            const int c = (k - n_half) * kChunk + lane;
+            if (c < ncon) zacc += contact_term<CL>(own_hcoef, peer_hcoef, sm, tp, P, c);
         } else if (k < e_bond) {
-            const int loc = (k - e_con) * kChunk + lane;
-            if (loc < nbl) {
-                const float eb = bond_term<ENERGY>(sm, F, tp, loc * CL + rank);
+            const int q = (k - e_con) * kChunk + lane;
+            if (q < tp.n_bonds) {
+                const float eb = bond_term<ENERGY>(sm, F, tp, q);
                 if (ENERGY) e += f2fix(eb);
             }
         } else {
-            const int loc = (k - e_bond) * kChunk + lane;
-            if (loc < nal) {
-                const float ea = angle_term<ENERGY>(sm, F, tp, loc * CL + rank);
+            const int q = (k - e_bond) * kChunk + lane;
+            if (q < tp.n_angles) {
+                const float ea = angle_term<ENERGY>(sm, F, tp, q);
                 if (ENERGY) e += f2fix(ea);
             }
         }
@@ -331,53 +400,58 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         sc.red_z[b][warp] = zacc;
         sc.red_e[b][warp] = e;
     }
-    // 3. exchange within the cluster; every CTA adds the shares in the same order
     cluster_barrier<CL>();
-    if (tid == 0) {
+    // shares of z, energy and flags from every CTA of the cluster (integer sums)
+    if (warp == 0) {
         long long zt = 0, et = 0;
         int fl = 0;
         for (int q = 0; q < CL; ++q) {
-            const long long* rz = rank_ptr<CL>(&sc.red_z[b][0], q);
-            const long long* re = rank_ptr<CL>(&sc.red_e[b][0], q);
-            for (int w = 0; w < nw; ++w) {
-                zt += rz[w];
-                if (ENERGY) et += re[w];
+            if (lane < nw) {
+                zt += rank_ptr<CL>(&sc.red_z[b][0], q)[lane];
+                if (ENERGY) et += rank_ptr<CL>(&sc.red_e[b][0], q)[lane];
             }
-            fl |= *rank_ptr<CL>(&sc.flag[b], q);
+            if (lane == 0) fl |= *rank_ptr<CL>(&sc.flag[b], q);
         }
-        if (ENERGY) sc.epot = (double)et * 9.5367431640625e-07;  // 2^-20
-        if (fl) sc.status |= SCPS_FLAG_FORCE_RANGE;
-        double factor = 0.0;
-        if (P.bias == 1) {
-            const double z = (double)zt * 9.094947017729282e-13;  // 2^-40
-            sc.z = z;
-            if (do_ratchet) {  // Eq. (FrMD) with theta(0) = 1
-                if (z < sc.zm)
-                    sc.zm = z;
-                else
-                    factor = -P.k_R * (z - sc.zm);
+        zt = warp_sum_ll(zt);
+        if (ENERGY) et = warp_sum_ll(et);
+        if (lane == 0) {
+            if (ENERGY) sc.epot = (double)et * 9.5367431640625e-07;  // 2^-20
+            if (fl) sc.status |= SCPS_FLAG_FORCE_RANGE;
+            double factor = 0.0;
+            if (P.bias == 1) {
+                const double z = (double)zt * 9.094947017729282e-13;  // 2^-40
+                sc.z = z;
+                if (do_ratchet) {  // Eq. (FrMD) with theta(0) = 1
+                    if (z < sc.zm)
+                        sc.zm = z;
+                    else
+                        factor = -P.k_R * (z - sc.zm);
+                }
             }
+            sc.factor = factor;
+            sc.bias_on = factor != 0.0;
+            sc.work_next[b] = 0;  // every pull of this evaluation is done
         }
-        sc.factor = factor;
-        sc.bias_on = factor != 0.0;
     }
     __syncthreads();
-    // 4. bias force factor * grad z (only when the ratchet is engaged)
+    // bias force factor * grad z per atom, summed over the atom's contacts in a fixed
+    // order: grad_i (C - C0)^2 = -4 (C - C0) C'(u) (x_p - x_i) / r0^2 for partner p
     if (sc.bias_on) {
-        for (int i = tid; i < 3 * sm.nta; i += blockDim.x) sm.Fb[i] = 0;
-        __syncthreads();
-        const float fac = (float)sc.factor;
-        const float k = fac * 4.0f * P.inv_r0sq;  // d/dx_j (C - C0)^2 = 2 d C'(u) 2 r / r0^2
-        for (int c = tid * CL + rank; c < tp.n_contacts; c += blockDim.x * CL) {
-            const int2 ij = tp.con_ij[c];
-            const float4 a = sm.xq[ij.x], bb = sm.xq[ij.y];
-            const float dx = bb.x - a.x, dy = bb.y - a.y, dz = bb.z - a.z;
-            const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq;
-            const float g = k * sm.cdelta[c] * contact_dC_du(u);
-            add_fix(sm, sm.Fb, ij.y, g * dx, g * dy, g * dz);
-            add_fix(sm, sm.Fb, ij.x, -g * dx, -g * dy, -g * dz);
+        const float k = -(float)sc.factor * 4.0f * P.inv_r0sq;
+        for (int i = tid; i < tp.n_atoms; i += blockDim.x) {
+            const float4 xi = sm.xq[i];
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            for (int q = tp.con_off[i]; q < tp.con_off[i + 1]; ++q) {
+                const int2 cp = tp.con_nbr[q];
+                const float4 xp = sm.xq[cp.y];
+                const float hc = own_hcoef[cp.x];
+                fx = fmaf(hc, xp.x - xi.x, fx);
+                fy = fmaf(hc, xp.y - xi.y, fy);
+                fz = fmaf(hc, xp.z - xi.z, fz);
+            }
+            sm.fb[i] = make_float4(k * fx, k * fy, k * fz, 0.f);
         }
-        cluster_barrier<CL>();
+        __syncthreads();
     }
 }
 
@@ -389,19 +463,31 @@ __device__ __forceinline__ float sum_fix(const long long* own, const long long* 
     return fix2f(v);
 }
 
+__device__ void tile_pair_table(const Shared& sm, int nt) {
+    for (int p = threadIdx.x; p < nt * (nt + 1) / 2; p += blockDim.x) {  // row major, I <= J
+        int I = 0, row = nt, q = p;
+        while (q >= row) {
+            q -= row;
+            ++I;
+            --row;
+        }
+        sm.tpl[p] = ((uint32_t)I << 16) | (uint32_t)(I + q);
+    }
+}
+
 }  // namespace
 
 template <int ELEC, int CL>
 __global__ void __launch_bounds__(1024, 1)
 k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, StateDev st,
-           RunParams P, int nta, int ntp_max) {
+           RunParams P, int nta, int ntp_max, int ncon_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const int r = blockIdx.x / CL;
     const int rank = cta_rank<CL>();
     const RepDev rep = reps[r];
     const TopoDev tp = topos[rep.topo];
-    Shared sm = carve(smem_raw, nta, ntp_max);
+    Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
     const int n = tp.n_atoms, nt = tp.n_tiles;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nta3 = 3 * nta;
@@ -417,21 +503,13 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             sm.lj[i] = make_float2(0.f, 0.f);
             sm.v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        sm.fb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int i = tid; i < nta3; i += blockDim.x) {
         sm.Fp[0][i] = 0;
         sm.Fp[1][i] = 0;
-        sm.Fb[i] = 0;
     }
-    for (int p = tid; p < nt * (nt + 1) / 2; p += blockDim.x) {  // tile-pair table, row major
-        int I = 0, row = nt, q = p;
-        while (q >= row) {
-            q -= row;
-            ++I;
-            --row;
-        }
-        sm.tpl[p] = ((uint32_t)I << 16) | (uint32_t)(I + q);
-    }
+    tile_pair_table(sm, nt);
     if (tid == 0) {
         sc.zm = st.zm[r];
         sc.z = st.z[r];
@@ -441,17 +519,16 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         sc.flag[0] = 0;
         sc.flag[1] = 0;
         sc.bias_on = 0;
-        sc.tp_count = 0;
-        sc.work_next = 0;
+        sc.work_next[0] = 0;
+        sc.work_next[1] = 0;
     }
     long long step = st.step[r];
     __syncthreads();
-    tile_boxes(sm, n, nt);
+    all_boxes(sm, n);
     cluster_barrier<CL>();  // every CTA of the cluster is initialised before any remote access
     const int peer = rank ^ 1;
     const long long* pFp[2] = {CL == 2 ? rank_ptr<CL>(sm.Fp[0], peer) : nullptr,
                                CL == 2 ? rank_ptr<CL>(sm.Fp[1], peer) : nullptr};
-    const long long* pFb = CL == 2 ? rank_ptr<CL>(sm.Fb, peer) : nullptr;
     const float hdt = P.half_dt;
     if (sc.status == 0 && P.n_steps > 0) {
         evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true);
@@ -466,19 +543,18 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             float tb = 0.f;
             for (int base = 0; base < nta; base += blockDim.x) {
                 const int i = base + tid;
-                float4 x = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-                bool valid = i < n;
+                const bool valid = i < n;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (valid) {
                     const float im = tp.inv_m[i];
                     float fx = sum_fix<CL>(own, pFp[b], i), fy = sum_fix<CL>(own, pFp[b], nta + i),
                           fz = sum_fix<CL>(own, pFp[b], 2 * nta + i);
                     if (bias) {
-                        const float bx = sum_fix<CL>(sm.Fb, pFb, i), by = sum_fix<CL>(sm.Fb, pFb, nta + i),
-                                    bz = sum_fix<CL>(sm.Fb, pFb, 2 * nta + i);
-                        if (do_b) tb += (bx * bx + by * by + bz * bz) * im;
-                        fx += bx;
-                        fy += by;
-                        fz += bz;
+                        const float4 f = sm.fb[i];
+                        if (do_b) tb += (f.x * f.x + f.y * f.y + f.z * f.z) * im;
+                        fx += f.x;
+                        fy += f.y;
+                        fz += f.z;
                     }
                     float4 v = sm.v[i];
                     x = sm.xq[i];
@@ -517,24 +593,10 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                     }
                     sm.v[i] = v;
                 }
-                if (do_a) {  // bounding box of this warp's tile at the new positions
-                    float lx = x.x, ly = x.y, lz = x.z;
-                    float hx = valid ? x.x : -3.0e38f, hy = valid ? x.y : -3.0e38f,
-                          hz = valid ? x.z : -3.0e38f;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
-                        ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
-                        lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
-                        hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
-                        hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
-                        hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
-                    }
-                    const int t = (base >> 5) + warp;
-                    if (lane == 0 && t < nt) {
-                        sm.blo[t] = make_float4(lx, ly, lz, 0.f);
-                        sm.bhi[t] = make_float4(hx, hy, hz, 0.f);
-                    }
+                if (do_a) {  // boxes of this warp's tile at the new positions
+                    const float4 lo = valid ? x : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+                    const float4 hi = valid ? x : make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
+                    warp_boxes(sm, (base >> 5) + warp, lo, hi, lane);
                 }
             }
             // this CTA's partials of the next evaluation start from zero
@@ -544,11 +606,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                 tb = warp_sum_f(tb);
                 if (lane == 0) sc.red_t[warp] = tb;
             }
-            if (tid == 0) {
-                sc.flag[nb] = 0;
-                sc.tp_count = 0;
-                sc.work_next = 0;
-            }
+            if (tid == 0) sc.flag[nb] = 0;
             __syncthreads();
             if (tid == 0 && do_b) {
                 if (bias) {
@@ -604,11 +662,11 @@ template <int ELEC>
 __global__ void __launch_bounds__(1024, 1)
 k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
               double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta,
-              int ntp_max) {
+              int ntp_max, int ncon_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const TopoDev tp = *topo_ptr;
-    Shared sm = carve(smem_raw, nta, ntp_max);
+    Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
     const int n = tp.n_atoms, nt = tp.n_tiles;
     const long long f = blockIdx.x;
     const float* xf = X + f * n * 3;
@@ -622,25 +680,16 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
         }
     }
     for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) sm.Fp[0][i] = 0;
-    for (int p = threadIdx.x; p < nt * (nt + 1) / 2; p += blockDim.x) {
-        int I = 0, row = nt, q = p;
-        while (q >= row) {
-            q -= row;
-            ++I;
-            --row;
-        }
-        sm.tpl[p] = ((uint32_t)I << 16) | (uint32_t)(I + q);
-    }
+    tile_pair_table(sm, nt);
     if (threadIdx.x == 0) {
         sc.zm = 0.0;
         sc.z = 0.0;
         sc.status = 0;
         sc.flag[0] = 0;
-        sc.tp_count = 0;
-        sc.work_next = 0;
+        sc.work_next[0] = 0;
     }
     __syncthreads();
-    tile_boxes(sm, n, nt);
+    all_boxes(sm, n);
     __syncthreads();
     evaluate<ELEC, true, 1>(sm, sc, tp, P, 0, false);
     if (F) {
@@ -661,8 +710,8 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
 size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max) {
     const int nt = nta / kTile;
     const size_t ntp4 = (size_t)((ntp_max + 3) & ~3);
-    return sizeof(float4) * nta * 2 + sizeof(long long) * 9 * nta + sizeof(float2) * nta +
-           sizeof(float4) * 2 * nt + sizeof(uint32_t) * 2 * ntp4 + sizeof(float) * ncon_max;
+    return sizeof(float4) * nta * 3 + sizeof(float4) * 6 * nt + sizeof(long long) * 6 * nta +
+           sizeof(float2) * nta + sizeof(uint32_t) * 3 * ntp4 + sizeof(float) * 2 * ncon_max;
 }
 
 template <int ELEC, int CL>
@@ -685,7 +734,7 @@ static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta, ntp_max);
+    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta, ntp_max, ncon_max);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -719,7 +768,7 @@ static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_eval_frames<ELEC><<<(unsigned)n_frames, threads, smem, stream>>>(topo, P, X, U, F, Z, nta,
-                                                                       ntp_max);
+                                                                       ntp_max, ncon_max);
     return cudaGetLastError();
 }
 

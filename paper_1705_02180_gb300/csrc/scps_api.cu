@@ -464,17 +464,36 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
             }
             std::vector<double> xn(nc > 0 ? (size_t)3 * n : 0);
             if (nc > 0) std::memcpy(xn.data(), b->x_native[t], sizeof(double) * 3 * n);
+            // per-atom adjacency of the contact list: (contact index, partner atom)
+            std::vector<int> off(n + 1, 0);
+            for (int c = 0; c < nc; ++c) {
+                off[pairs[c].x + 1]++;
+                off[pairs[c].y + 1]++;
+            }
+            for (int i = 0; i < n; ++i) off[i + 1] += off[i];
+            std::vector<int> fill(off.begin(), off.end() - 1);
+            std::vector<int2> nbr((size_t)2 * nc);
+            for (int c = 0; c < nc; ++c) {
+                nbr[fill[pairs[c].x]++] = make_int2(c, pairs[c].y);
+                nbr[fill[pairs[c].y]++] = make_int2(c, pairs[c].x);
+            }
             int2* d_pairs;
             float2* d_c0;
             double* d_xn;
+            int* d_off;
+            int2* d_nbr;
             SCPS_CU(s->upload(&d_pairs, pairs));
             SCPS_CU(s->alloc(&d_c0, nc));
             SCPS_CU(s->upload(&d_xn, xn));
+            SCPS_CU(s->upload(&d_off, off));
+            SCPS_CU(s->upload(&d_nbr, nbr));
             SCPS_CU(launch_native_map(nc, d_pairs, d_xn, inv_r0sq, d_c0, 0));
             SCPS_CU(cudaDeviceSynchronize());
             s->topos[t].dev.n_contacts = nc;
             s->topos[t].dev.con_ij = d_pairs;
             s->topos[t].dev.con_C0 = d_c0;
+            s->topos[t].dev.con_off = d_off;
+            s->topos[t].dev.con_nbr = d_nbr;
             s->topos[t].ncon = nc;
             ncon_max = std::max(ncon_max, nc);
         }

@@ -33,6 +33,8 @@ struct TopoDev {
     int n_contacts;
     const int2* con_ij;        // native-contact pairs of z(X)
     const float2* con_C0;      // C0 as float-float (hi, lo)
+    const int* con_off;        // n_atoms + 1 offsets into con_nbr
+    const int2* con_nbr;       // per atom: (contact index, partner atom)
 };
 
 // Per-replica addressing.
