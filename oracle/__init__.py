@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "scps_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "scps_oracle_hvp.c")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
@@ -31,10 +32,11 @@ KB = 0.0083144626        # kJ mol^-1 K^-1
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, -O2, OpenMP over replicas)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(s) for s in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -83,6 +85,8 @@ def lib():
                                      C.c_int, P, P, P, P, P]
         _lib.orc_run_toy.restype = C.c_int
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_hvp.argtypes = [P, P, P, P, P]
+        _lib.orc_hvp.restype = C.c_int
     return _lib
 
 
@@ -150,6 +154,15 @@ class ForceField:
 
     def energy(self, x):
         return float(self.forces(x)[1].sum())
+
+    def hvp(self, x, v):
+        """(grad U, H v) at x along v, by forward-mode differentiation (dual numbers)."""
+        x = _f64(x)
+        v = _f64(v)
+        g = np.zeros((self.n, 3))
+        hv = np.zeros((self.n, 3))
+        lib().orc_hvp(C.byref(self.s), _p(x), _p(v), _p(g), _p(hv))
+        return g, hv
 
 
 def contact_C(r, r0=0.75):
