@@ -1,0 +1,303 @@
+// Hessian-vector products H(X_t) V_t of the physical potential, one CTA per
+// frame. Used by the double backward of the energy (the gradient of
+// sum_t |grad U(X_t)|^2 is sum_t 2 H(X_t) grad U(X_t); the Onsager-Machlup
+// action of Eq. (SOM) contains (grad U)^2).
+//
+// For a pair term phi(r) with d = x_j - x_i and w = v_j - v_i:
+//   (Hv)_j = phi'' (d.w) d / r^2 + (phi'/r) (w - (d.w) d / r^2),  (Hv)_i = -(Hv)_j,
+// with the shifted-force phi' (the shift is linear in r, so phi'' is unchanged).
+// For an angle term k/2 (theta - theta0)^2:
+//   H v = k (grad theta . v) grad theta + k (theta - theta0) D_v(grad theta),
+// D_v being the directional derivative along v, written out by hand below.
+// Sums are int64 fixed point (order-free, so results are bit-reproducible).
+#include "scps_internal.h"
+
+namespace scps {
+
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+struct HvpShared {
+    float4* xq;      // (x, y, z, qs)
+    float4* vq;      // direction v
+    float2* lj;
+    long long* H;    // 3 x nta fixed point
+    float4* blo;
+    float4* bhi;
+    uint32_t* tp;    // active tile pairs
+    int nta;
+};
+
+__device__ __forceinline__ void hadd(const HvpShared& sm, int i, float x, float y, float z) {
+    atomicAdd((unsigned long long*)&sm.H[i], (unsigned long long)f2fix(x));
+    atomicAdd((unsigned long long*)&sm.H[sm.nta + i], (unsigned long long)f2fix(y));
+    atomicAdd((unsigned long long*)&sm.H[2 * sm.nta + i], (unsigned long long)f2fix(z));
+}
+
+// phi'(r)/r of the shifted-force pair potential and phi''(r).
+template <int ELEC>
+__device__ __forceinline__ void pair_derivs(float r2, float sig, float eps24, float qq,
+                                            const PairConst& pc, float& p1, float& pp) {
+    const float inv_r = rsqrtf(r2);
+    const float inv_r2 = inv_r * inv_r;
+    const float sig2 = sig * sig;
+    const float s2 = sig2 * inv_r2;
+    const float s6 = s2 * s2 * s2;
+    const float s12 = s6 * s6;
+    p1 = -eps24 * fmaf(2.0f, s12, -s6) * inv_r2;     // LJ phi'/r
+    pp = eps24 * fmaf(26.0f, s12, -7.0f * s6) * inv_r2;  // LJ phi''
+    const float c2 = sig2 * pc.inv_rc2;
+    const float c6 = c2 * c2 * c2;
+    const float a_ljc = eps24 * c6 * fmaf(2.0f, c6, -1.0f);
+    float cc = 0.0f;
+    if (ELEC == ELEC_DDIEL) {        // phi = (qq/2) / r^2
+        p1 -= qq * inv_r2 * inv_r2;
+        pp += 3.0f * qq * inv_r2 * inv_r2;
+        cc = qq * pc.inv_rc3;
+    } else if (ELEC == ELEC_RF) {    // phi = qq (1/r + krf r^2 - crf)
+        p1 += qq * fmaf(-inv_r2, inv_r, 2.0f * pc.krf);
+        pp += qq * fmaf(2.0f * inv_r2, inv_r, 2.0f * pc.krf);
+        cc = qq * fmaf(pc.inv_rc2, 1.0f, -2.0f * pc.krf * pc.rc);
+    } else if (ELEC == ELEC_PLAIN) { // phi = qq / r
+        p1 -= qq * inv_r2 * inv_r;
+        pp += 2.0f * qq * inv_r2 * inv_r;
+        cc = qq * pc.inv_rc2;
+    }
+    p1 = fmaf(fmaf(a_ljc, pc.inv_rc, cc), inv_r, p1);  // phi_sf' = phi' - phi'(rc)
+}
+
+template <int ELEC>
+__device__ void hvp_tile(const HvpShared& sm, const TopoDev& tp, const PairConst& pc, int I,
+                         int J, int lane) {
+    const int i = I * kTile + lane;
+    const float4 xi = sm.xq[i];
+    const float4 vi = sm.vq[i];
+    const float2 li = sm.lj[i];
+    const bool near = (J - I) <= 1;
+    const unsigned long long em = (near && i < tp.n_atoms) ? tp.excl[i] : 0ull;
+    float hix = 0.f, hiy = 0.f, hiz = 0.f, hjx = 0.f, hjy = 0.f, hjz = 0.f;
+    const int jb = J * kTile;
+    for (int t = 0; t < kTile; ++t) {
+        const int sl = (lane + t) & (kTile - 1);
+        const int j = jb + sl;
+        const float4 xj = sm.xq[j];
+        const float4 vj = sm.vq[j];
+        const float2 lj = sm.lj[j];
+        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool ok = r2 < pc.rc2;
+        if (I == J) ok = ok && (j > i);
+        if (near) {
+            const int dj = j - i + kExclWindow;
+            if (dj >= 0 && dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
+        }
+        float p1, pp;
+        pair_derivs<ELEC>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, p1, pp);
+        const float wx = vj.x - vi.x, wy = vj.y - vi.y, wz = vj.z - vi.z;
+        const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+        const float c1 = (pp - p1) * dw / r2;
+        float ax = fmaf(c1, dx, p1 * wx), ay = fmaf(c1, dy, p1 * wy), az = fmaf(c1, dz, p1 * wz);
+        ax = ok ? ax : 0.f;
+        ay = ok ? ay : 0.f;
+        az = ok ? az : 0.f;
+        hix -= ax;
+        hiy -= ay;
+        hiz -= az;
+        hjx += ax;
+        hjy += ay;
+        hjz += az;
+        const int src = (lane + 1) & (kTile - 1);
+        hjx = __shfl_sync(kFullMask, hjx, src);
+        hjy = __shfl_sync(kFullMask, hjy, src);
+        hjz = __shfl_sync(kFullMask, hjz, src);
+    }
+    hadd(sm, i, hix, hiy, hiz);
+    hadd(sm, jb + lane, hjx, hjy, hjz);
+}
+
+__device__ void hvp_bond(const HvpShared& sm, const TopoDev& tp, int b) {
+    const int2 ij = tp.bond_ij[b];
+    const float2 par = tp.bond_par[b];
+    const float4 a = sm.xq[ij.x], c = sm.xq[ij.y];
+    const float4 va = sm.vq[ij.x], vc = sm.vq[ij.y];
+    const float dx = c.x - a.x, dy = c.y - a.y, dz = c.z - a.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float r = sqrtf(r2);
+    const float p1 = par.y * (r - par.x) / r;  // phi'/r
+    const float wx = vc.x - va.x, wy = vc.y - va.y, wz = vc.z - va.z;
+    const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+    const float c1 = (par.y - p1) * dw / r2;
+    const float ax = fmaf(c1, dx, p1 * wx), ay = fmaf(c1, dy, p1 * wy), az = fmaf(c1, dz, p1 * wz);
+    hadd(sm, ij.y, ax, ay, az);
+    hadd(sm, ij.x, -ax, -ay, -az);
+}
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 lin(float a, float3 x, float b, float3 y) {
+    return f3(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z));
+}
+
+__device__ void hvp_angle(const HvpShared& sm, const TopoDev& tp, int q) {
+    const int4 ijk = tp.ang_ijk[q];
+    const float2 par = tp.ang_par[q];
+    const float4 A = sm.xq[ijk.x], B = sm.xq[ijk.y], Cc = sm.xq[ijk.z];
+    const float4 VA = sm.vq[ijk.x], VB = sm.vq[ijk.y], VC = sm.vq[ijk.z];
+    const float3 u = f3(A.x - B.x, A.y - B.y, A.z - B.z), w = f3(Cc.x - B.x, Cc.y - B.y, Cc.z - B.z);
+    const float3 du = f3(VA.x - VB.x, VA.y - VB.y, VA.z - VB.z);
+    const float3 dw = f3(VC.x - VB.x, VC.y - VB.y, VC.z - VB.z);
+    const float3 c = cross3(u, w);
+    const float sn = sqrtf(dot3(c, c));
+    const float cs = dot3(u, w);
+    const float ru2 = dot3(u, u), rw2 = dot3(w, w);
+    const float dth = atan2f(sn, cs) - par.x;
+    // grad theta: G_i = (cs u / |u|^2 - w) / sn, G_k = (cs w / |w|^2 - u) / sn, G_j = -(G_i + G_k)
+    const float isn = 1.0f / sn;
+    const float3 Gi = lin(cs / ru2 * isn, u, -isn, w);
+    const float3 Gk = lin(cs / rw2 * isn, w, -isn, u);
+    // directional derivatives along v
+    const float dcs = dot3(du, w) + dot3(u, dw);
+    const float3 dc = f3(cross3(du, w).x + cross3(u, dw).x, cross3(du, w).y + cross3(u, dw).y,
+                         cross3(du, w).z + cross3(u, dw).z);
+    const float dsn = dot3(c, dc) * isn;
+    const float dru2 = 2.0f * dot3(u, du), drw2 = 2.0f * dot3(w, dw);
+    const float ai = (dcs / ru2 - cs * dru2 / (ru2 * ru2)) * isn;
+    const float ak = (dcs / rw2 - cs * drw2 / (rw2 * rw2)) * isn;
+    const float3 dGi = f3(ai * u.x + (cs / ru2) * isn * du.x - isn * dw.x - Gi.x * dsn * isn,
+                          ai * u.y + (cs / ru2) * isn * du.y - isn * dw.y - Gi.y * dsn * isn,
+                          ai * u.z + (cs / ru2) * isn * du.z - isn * dw.z - Gi.z * dsn * isn);
+    const float3 dGk = f3(ak * w.x + (cs / rw2) * isn * dw.x - isn * du.x - Gk.x * dsn * isn,
+                          ak * w.y + (cs / rw2) * isn * dw.y - isn * du.y - Gk.y * dsn * isn,
+                          ak * w.z + (cs / rw2) * isn * dw.z - isn * du.z - Gk.z * dsn * isn);
+    // grad theta . v with G_j = -(G_i + G_k): G_i.(v_i - v_j) + G_k.(v_k - v_j)
+    const float gv = dot3(Gi, du) + dot3(Gk, dw);
+    const float k = par.y;
+    const float3 hi = lin(k * gv, Gi, k * dth, dGi);
+    const float3 hk = lin(k * gv, Gk, k * dth, dGk);
+    // the centre gets -(H v)_i - (H v)_k since G_j = -(G_i + G_k) and D_v G_j = -(D_v G_i + D_v G_k)
+    hadd(sm, ijk.x, hi.x, hi.y, hi.z);
+    hadd(sm, ijk.z, hk.x, hk.y, hk.z);
+    hadd(sm, ijk.y, -(hi.x + hk.x), -(hi.y + hk.y), -(hi.z + hk.z));
+}
+
+}  // namespace
+
+template <int ELEC>
+__global__ void __launch_bounds__(512)
+k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
+             const float* __restrict__ V, float* __restrict__ HV, int nta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int tp_count;
+    const TopoDev tp = *topo_ptr;
+    const int n = tp.n_atoms, nt = tp.n_tiles, ntp = nt * (nt + 1) / 2;
+    HvpShared sm;
+    char* p = (char*)smem_raw;
+    sm.nta = nta;
+    sm.xq = (float4*)p; p += sizeof(float4) * nta;
+    sm.vq = (float4*)p; p += sizeof(float4) * nta;
+    sm.blo = (float4*)p; p += sizeof(float4) * (nta / kTile);
+    sm.bhi = (float4*)p; p += sizeof(float4) * (nta / kTile);
+    sm.H = (long long*)p; p += sizeof(long long) * 3 * nta;
+    sm.lj = (float2*)p; p += sizeof(float2) * nta;
+    sm.tp = (uint32_t*)p;
+    const long long f = blockIdx.x;
+    const float* xf = X + f * n * 3;
+    const float* vf = V + f * n * 3;
+    for (int i = threadIdx.x; i < nta; i += blockDim.x) {
+        if (i < n) {
+            sm.xq[i] = make_float4(xf[3 * i], xf[3 * i + 1], xf[3 * i + 2], tp.qs[i]);
+            sm.vq[i] = make_float4(vf[3 * i], vf[3 * i + 1], vf[3 * i + 2], 0.f);
+            sm.lj[i] = tp.lj[i];
+        } else {
+            sm.xq[i] = make_float4(1.0e5f * (float)(i + 1), 0.f, 0.f, 0.f);
+            sm.vq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sm.lj[i] = make_float2(0.f, 0.f);
+        }
+    }
+    for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) sm.H[i] = 0;
+    if (threadIdx.x == 0) tp_count = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = warp; t < nt; t += nw) {  // tile boxes (valid atoms only)
+        const int a = t * kTile + lane;
+        const float4 q = sm.xq[a < n ? a : t * kTile];
+        float lx = q.x, ly = q.y, lz = q.z, hx = q.x, hy = q.y, hz = q.z;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(kFullMask, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(kFullMask, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(kFullMask, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(kFullMask, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(kFullMask, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(kFullMask, hz, o));
+        }
+        if (lane == 0) {
+            sm.blo[t] = make_float4(lx, ly, lz, 0.f);
+            sm.bhi[t] = make_float4(hx, hy, hz, 0.f);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < ntp; q += blockDim.x) {
+        int I = 0, row = nt, r = q;
+        while (r >= row) {
+            r -= row;
+            ++I;
+            --row;
+        }
+        const int J = I + r;
+        const float4 al = sm.blo[I], ah = sm.bhi[I], bl = sm.blo[J], bh = sm.bhi[J];
+        const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
+        const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
+        const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
+        if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2)
+            sm.tp[atomicAdd(&tp_count, 1)] = ((uint32_t)I << 16) | (uint32_t)J;
+    }
+    __syncthreads();
+    for (int k = warp; k < tp_count; k += nw) {
+        const uint32_t w = sm.tp[k];
+        hvp_tile<ELEC>(sm, tp, P.pc, (int)(w >> 16), (int)(w & 0xffff), lane);
+    }
+    for (int b = threadIdx.x; b < tp.n_bonds; b += blockDim.x) hvp_bond(sm, tp, b);
+    for (int q = threadIdx.x; q < tp.n_angles; q += blockDim.x) hvp_angle(sm, tp, q);
+    __syncthreads();
+    float* out = HV + f * n * 3;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        out[3 * i] = fix2f(sm.H[i]);
+        out[3 * i + 1] = fix2f(sm.H[nta + i]);
+        out[3 * i + 2] = fix2f(sm.H[2 * nta + i]);
+    }
+}
+
+size_t hvp_smem_bytes(int nta) {
+    const int nt = nta / kTile;
+    return sizeof(float4) * 2 * nta + sizeof(float4) * 2 * nt + sizeof(long long) * 3 * nta +
+           sizeof(float2) * nta + sizeof(uint32_t) * (size_t)(nt * (nt + 1) / 2 + 4);
+}
+
+template <int ELEC>
+static cudaError_t launch_hvp_t(const TopoDev* topo, const RunParams& P, const float* X,
+                                const float* V, float* HV, long long n_frames, int nta,
+                                cudaStream_t s) {
+    const size_t smem = hvp_smem_bytes(nta);
+    cudaError_t e = cudaFuncSetAttribute(k_hvp_frames<ELEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_hvp_frames<ELEC><<<(unsigned)n_frames, 512, smem, s>>>(topo, P, X, V, HV, nta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hvp(int elec, const TopoDev* topo, const RunParams& P, const float* X,
+                       const float* V, float* HV, long long n_frames, int nta, cudaStream_t s) {
+    switch (elec) {
+        case ELEC_DDIEL: return launch_hvp_t<ELEC_DDIEL>(topo, P, X, V, HV, n_frames, nta, s);
+        case ELEC_RF: return launch_hvp_t<ELEC_RF>(topo, P, X, V, HV, n_frames, nta, s);
+        case ELEC_PLAIN: return launch_hvp_t<ELEC_PLAIN>(topo, P, X, V, HV, n_frames, nta, s);
+        default: return launch_hvp_t<ELEC_NONE>(topo, P, X, V, HV, n_frames, nta, s);
+    }
+}
+
+}  // namespace scps

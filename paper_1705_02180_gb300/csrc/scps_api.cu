@@ -31,6 +31,8 @@ cudaError_t plain_run_replica(int elec, const TopoDev& tp, const StateDev& st, i
 cudaError_t launch_native_map(int nc, const int2* pairs, const double* xN, double inv_r0sq,
                               float2* C0, cudaStream_t s);
 cudaError_t launch_add_steps(long long* step, int n, long long k, cudaStream_t s);
+cudaError_t launch_hvp(int elec, const TopoDev* topo, const RunParams& P, const float* X,
+                       const float* V, float* HV, long long n_frames, int nta, cudaStream_t s);
 }  // namespace scps
 
 using namespace scps;
@@ -606,8 +608,16 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
 
 int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, const float* V,
              float* HV, void* stream) {
-    (void)s; (void)topo; (void)n_frames; (void)X; (void)V; (void)HV; (void)stream;
-    return fail(SCPS_ERR_UNSUPPORTED, "Hessian-vector products are not built yet");
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
+    if (topo < 0 || topo >= (int)s->topos.size()) return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
+    if (n_frames < 0 || n_frames > 2147483647ll) return fail(SCPS_ERR_INVALID_ARG, "bad n_frames");
+    if (n_frames == 0) return SCPS_OK;
+    if (!X || !V || !HV) return fail(SCPS_ERR_INVALID_ARG, "X, V and HV are required");
+    const int nta = ((s->topos[topo].n + kTile - 1) / kTile) * kTile;
+    SCPS_CU(launch_hvp(s->d.elec, s->d_topos + topo, s->base, X, V, HV, n_frames, nta,
+                       (cudaStream_t)stream));
+    return SCPS_OK;
 }
 
 int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames, double* z,
