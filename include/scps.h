@@ -98,7 +98,11 @@ typedef struct {
     int32_t elec;       /* SCPS_ELEC_* */
     double k_dd;        /* distance-dependent dielectric eps_r = k_dd r (nm^-1), e.g. 40 */
     double eps_rf;      /* reaction-field dielectric, e.g. 78.5 */
-    double box;         /* 0: open boundaries (the only value supported by the chain model) */
+    double box;         /* 0: open boundaries; > 0: cubic periodic box of this edge (nm), with
+                           minimum-image bonded terms and contacts, cell-sorted tiles and tile
+                           neighbour lists (one topology; its bonded atoms, the "chain", come
+                           first; the remaining atoms are solvent sites). Reaction field is the
+                           intended electrostatics. Needs box > 2 (cutoff + skin). */
     /* integrator */
     int32_t integrator; /* SCPS_INT_* */
     double dt, gamma, kT;
@@ -111,6 +115,10 @@ typedef struct {
     int32_t cluster_size;   /* CTAs per replica in RESIDENT form: 0 = auto, 1 or 2 */
     int32_t threads;        /* threads per CTA in RESIDENT form: 0 = auto, else 128..1024 */
     int32_t steps_per_graph;/* device-loop steps per CUDA-graph node: 0 = auto */
+    /* periodic box only */
+    double skin;            /* neighbour-list buffer (nm), 0 = 0.15; a list is rebuilt when an
+                               atom has moved skin/2 since the last rebuild */
+    int32_t rebuild_every;  /* scheduled list rebuild interval (steps), 0 = 20 */
 } scps_system_desc;
 
 typedef struct {

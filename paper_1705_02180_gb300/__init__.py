@@ -43,7 +43,8 @@ class SystemDesc(C.Structure):
                 ("integrator", C.c_int32), ("dt", C.c_double), ("gamma", C.c_double),
                 ("kT", C.c_double), ("seed", C.c_uint64), ("save_interval", C.c_int32),
                 ("max_frames", C.c_int32), ("exec", C.c_int32), ("cluster_size", C.c_int32),
-                ("threads", C.c_int32), ("steps_per_graph", C.c_int32)]
+                ("threads", C.c_int32), ("steps_per_graph", C.c_int32), ("skin", C.c_double),
+                ("rebuild_every", C.c_int32)]
 
 
 class BiasDesc(C.Structure):
@@ -151,7 +152,7 @@ class System:
                  replica_id=None, cutoff=1.0, elec=ELEC_DDIEL, k_dd=40.0, eps_rf=78.5,
                  integrator=INT_BAOAB, dt=0.002, gamma=1.0, kT=2.494, seed=0, save_interval=0,
                  max_frames=0, exec_form=EXEC_RESIDENT, threads=0, steps_per_graph=0,
-                 cluster_size=0):
+                 cluster_size=0, box=0.0, skin=0.0, rebuild_every=0):
         lib = load()
         self._keep = []
         tops = (TopologyDesc * max(len(topologies), 1))()
@@ -186,9 +187,9 @@ class System:
         self.max_frames = max_frames
         self.save_interval = save_interval
         d = SystemDesc(model, len(topologies), C.cast(tops, _P), n_rep, _ptr(rt), _ptr(rid),
-                       _ptr(x0), _ptr(v0), cutoff, elec, k_dd, eps_rf, 0.0, integrator, dt, gamma,
+                       _ptr(x0), _ptr(v0), cutoff, elec, k_dd, eps_rf, box, integrator, dt, gamma,
                        kT, seed, save_interval, max_frames, exec_form, cluster_size, threads,
-                       steps_per_graph)
+                       steps_per_graph, skin, rebuild_every)
         h = C.c_void_p()
         check(lib.scps_create_system(C.byref(d), C.byref(h)))
         self.h = h

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libscps.so")
-SOURCES = ["scps_api.cu", "kern_chain.cu", "kern_aux.cu", "kern_hvp.cu", "noalloc.cu"]
+SOURCES = ["scps_api.cu", "kern_chain.cu", "kern_aux.cu", "kern_hvp.cu", "kern_box.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,696 @@
+// Solvated periodic box: rMD replicas of one chain in LJ + Coulomb solvent
+// (reaction field), cubic box, cell-sorted tiles and tile neighbour lists.
+//
+// Per step (kernels in stream order):
+//   [rebuild, when due]  wrap, sort atoms by (Morton cell, atom id) into tiles
+//                        of 32, tile boxes, per i-tile list of j tiles within
+//                        r_c + skin with the periodic shift of each j tile
+//   pairs                one warp per i tile; each lane owns one atom and adds
+//                        up its own force over the listed j tiles (both
+//                        directions of every pair: no atomics, a fixed order)
+//   chain                one CTA per replica: bonds, angles, z(X) of Eq.
+//                        (zrMD), the ratchet of Eq. (FrMD), the bias force
+//   integrate            BAOAB half steps with Philox noise keyed by atom id
+// A rebuild is due every `rebuild_every` steps, or earlier when an atom has
+// moved more than skin/2 since the last one, so every pair inside the cutoff
+// is always in the list. The rebuild order depends only on positions and ids.
+#include "scps_internal.h"
+
+namespace scps {
+
+namespace {
+
+constexpr unsigned kFullB = 0xffffffffu;
+constexpr int kKeyBits = 12;            // Morton key of up to 16^3 cells
+constexpr int kNumKeys = 1 << kKeyBits;
+
+__device__ __forceinline__ int morton3(int x, int y, int z) {
+    int k = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        k |= (((x >> b) & 1) << (3 * b)) | (((y >> b) & 1) << (3 * b + 1)) | (((z >> b) & 1) << (3 * b + 2));
+    return k;
+}
+
+__device__ __forceinline__ float wrapc(float x, float L, float invL) {
+    return x - L * floorf(x * invL);
+}
+
+__device__ __forceinline__ float min_img(float d, float L, float invL) {
+    return d - L * rintf(d * invL);
+}
+
+}  // namespace
+
+// Rebuild step 1 (one CTA per replica): decide, wrap, sort by (cell key, atom id).
+__global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __restrict__ topo,
+                                                    StateDev st, int r0, int auto_ok) {
+    __shared__ int cnt[kNumKeys];
+    __shared__ int decide;
+    const int r = blockIdx.x + r0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) {
+        const float d2 = __uint_as_float(B.maxd2[r]);
+        decide = st.status[r] == 0 &&
+                 (B.need[r] || (auto_ok && (B.since[r] >= B.rebuild_every || d2 >= B.skin2_quarter)));
+    }
+    __syncthreads();
+    if (!decide) return;
+    const TopoDev tp = *topo;
+    float4* pos = B.pos + (size_t)r * B.np;
+    float4* vel = B.vel + (size_t)r * B.np;
+    int* id = B.id + (size_t)r * B.np;
+    int* key = B.key + (size_t)r * B.np;
+    int* slot_of = B.slot_of + (size_t)r * B.n_atoms;
+    float4* pos2 = B.pos2 + (size_t)r * B.np;
+    float4* vel2 = B.vel2 + (size_t)r * B.np;
+    for (int k = tid; k < kNumKeys; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    const float cs = (float)B.nc * B.invL;
+    for (int s = tid; s < B.np; s += blockDim.x) {
+        const int a = id[s];
+        if (a < 0) continue;
+        float4 p = pos[s];
+        p.x = wrapc(p.x, B.L, B.invL);
+        p.y = wrapc(p.y, B.L, B.invL);
+        p.z = wrapc(p.z, B.L, B.invL);
+        pos[s] = p;
+        const int qx = min((int)(p.x * cs), B.nc - 1), qy = min((int)(p.y * cs), B.nc - 1),
+                  qz = min((int)(p.z * cs), B.nc - 1);
+        const int k = morton3(qx, qy, qz);
+        key[s] = k;
+        atomicAdd(&cnt[k], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the key counts (4 keys per thread, 1024 threads)
+    {
+        int loc[4], sum = 0;
+        const int base = tid * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            loc[q] = (base + q < kNumKeys) ? cnt[base + q] : 0;
+            sum += loc[q];
+        }
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFullB, x, o);
+            if (lane >= o) x += y;
+        }
+        __shared__ int wtot[32];
+        if (lane == 31) wtot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = lane < nw ? wtot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFullB, t, o);
+                if (lane >= o) t += y;
+            }
+            wtot[lane] = t;
+        }
+        __syncthreads();
+        int run = (warp > 0 ? wtot[warp - 1] : 0) + x - sum;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (base + q < kNumKeys) {
+                cnt[base + q] = run;  // becomes the running cursor of key base+q
+                run += loc[q];
+            }
+    }
+    __syncthreads();
+    // scatter in atom-id order, one warp at a time: ties (same key) keep id order
+    for (int c0 = 0; c0 < B.n_atoms; c0 += blockDim.x) {
+        const int a = c0 + tid;
+        const bool valid = a < B.n_atoms;
+        const int s = valid ? slot_of[a] : 0;
+        const int k = valid ? key[s] : -1 - lane;
+        for (int w = 0; w < nw; ++w) {
+            if (warp == w) {
+                const unsigned peers = __match_any_sync(kFullB, k);
+                const int rank = __popc(peers & ((1u << lane) - 1u));
+                int dst = 0;
+                if (valid) dst = cnt[k] + rank;
+                __syncwarp();
+                if (valid && rank == 0) cnt[k] += __popc(peers);
+                if (valid) {
+                    pos2[dst] = pos[s];
+                    vel2[dst] = vel[s];
+                    slot_of[a] = dst;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // copy back in tile order; padding slots are far away, without charge or LJ
+    for (int s = tid; s < B.np; s += blockDim.x) {
+        if (s < B.n_atoms) {
+            pos[s] = pos2[s];
+            vel[s] = vel2[s];
+            B.pos_ref[(size_t)r * B.np + s] = pos2[s];
+        } else {
+            pos[s] = make_float4(1.0e5f * (float)(s + 1), 0.f, 0.f, 0.f);
+            vel[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            id[s] = -1;
+        }
+    }
+    __syncthreads();
+    for (int a = tid; a < B.n_atoms; a += blockDim.x) {
+        const int s = slot_of[a];
+        id[s] = a;
+        B.par[(size_t)r * B.np + s] = tp.lj[a];
+    }
+    for (int s = B.n_atoms + tid; s < B.np; s += blockDim.x) B.par[(size_t)r * B.np + s] = make_float2(0.f, 0.f);
+    if (tid == 0) {
+        B.need[r] = 1;  // the tile and list kernels of this step run
+        B.since[r] = 0;
+        B.maxd2[r] = 0u;
+    }
+}
+
+// Rebuild step 2: tile boxes (one warp per tile).
+__global__ void k_box_tiles(BoxDev B, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= B.nt) return;
+    const int lane = threadIdx.x & 31;
+    const int s = t * 32 + lane;
+    const float4 p = B.pos[(size_t)r * B.np + s];
+    const bool valid = B.id[(size_t)r * B.np + s] >= 0;
+    float lx = valid ? p.x : 3.0e38f, ly = valid ? p.y : 3.0e38f, lz = valid ? p.z : 3.0e38f;
+    float hx = valid ? p.x : -3.0e38f, hy = valid ? p.y : -3.0e38f, hz = valid ? p.z : -3.0e38f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(kFullB, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(kFullB, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(kFullB, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(kFullB, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(kFullB, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(kFullB, hz, o));
+    }
+    if (lane == 0) {
+        B.tlo[(size_t)r * B.nt + t] = make_float4(lx, ly, lz, 0.f);
+        B.thi[(size_t)r * B.nt + t] = make_float4(hx, hy, hz, 0.f);
+    }
+}
+
+// Rebuild step 3: neighbour tiles of every tile (one warp per i tile), in j order.
+__global__ void k_box_list(BoxDev B, StateDev st, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= B.nt) return;
+    const int lane = threadIdx.x & 31;
+    const float4 al = B.tlo[(size_t)r * B.nt + t], ah = B.thi[(size_t)r * B.nt + t];
+    const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
+    uint32_t* out = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
+    int count = 0;
+    bool overflow = false;
+    for (int j0 = 0; j0 < B.nt; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        uint32_t code = 0;
+        if (j < B.nt) {
+            const float4 bl = B.tlo[(size_t)r * B.nt + j], bh = B.thi[(size_t)r * B.nt + j];
+            if (bl.x <= bh.x) {  // tile holds atoms
+                // lower bound of any periodic-image distance between the two boxes:
+                // |minimum-image centre distance| - half widths, per dimension
+                const float gx = fmaxf(0.f, fabsf(min_img(0.5f * (bl.x + bh.x) - cx, B.L, B.invL)) -
+                                                0.5f * ((bh.x - bl.x) + (ah.x - al.x)));
+                const float gy = fmaxf(0.f, fabsf(min_img(0.5f * (bl.y + bh.y) - cy, B.L, B.invL)) -
+                                                0.5f * ((bh.y - bl.y) + (ah.y - al.y)));
+                const float gz = fmaxf(0.f, fabsf(min_img(0.5f * (bl.z + bh.z) - cz, B.L, B.invL)) -
+                                                0.5f * ((bh.z - bl.z) + (ah.z - al.z)));
+                hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
+                code = (uint32_t)j;
+            }
+        }
+        const unsigned m = __ballot_sync(kFullB, hit);
+        if (hit) {
+            const int pos = count + __popc(m & ((1u << lane) - 1u));
+            if (pos < B.max_nbr)
+                out[pos] = code;
+        }
+        count += __popc(m);
+    }
+    if (count > B.max_nbr) {
+        overflow = true;
+        count = B.max_nbr;
+    }
+    if (lane == 0) {
+        B.nnbr[(size_t)r * B.nt + t] = count;
+        if (overflow) atomicOr(&st.status[r], 4);
+    }
+}
+
+// Non-bonded forces: one warp per i tile; lane l owns slot 32 t + l.
+template <int ELEC, bool ENERGY>
+__global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __restrict__ topo,
+                                                   RunParams P, int r0) {
+    __shared__ float4 sj[4][32];
+    __shared__ float2 sp[4][32];
+    __shared__ int sid[4][32];
+    const int r = blockIdx.y + r0;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 4 + w;
+    if (t >= B.nt) return;
+    const size_t base = (size_t)r * B.np;
+    const int si = t * 32 + lane;
+    const float4 xi = B.pos[base + si];
+    const float2 li = B.par[base + si];
+    const int idi = B.id[base + si];
+    const unsigned long long em = (idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
+    const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
+    const int cnt = B.nnbr[(size_t)r * B.nt + t];
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    for (int q = 0; q < cnt; ++q) {
+        const int jt = (int)lst[q];
+        const int sjl = jt * 32 + lane;
+        sj[w][lane] = B.pos[base + sjl];
+        sp[w][lane] = B.par[base + sjl];
+        sid[w][lane] = B.id[base + sjl];
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const float4 xj = sj[w][k];
+            const float2 lj = sp[w][k];
+            const int idj = sid[w][k];
+            const float dx = min_img(xj.x - xi.x, B.L, B.invL), dy = min_img(xj.y - xi.y, B.L, B.invL),
+                        dz = min_img(xj.z - xi.z, B.L, B.invL);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool ok = r2 < P.pc.rc2 && idj != idi && idj >= 0 && idi >= 0;
+            const unsigned dj = (unsigned)(idj - idi + kExclWindow);
+            if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
+            float ep = 0.f;
+            float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
+            s = ok ? s : 0.0f;
+            fx = fmaf(s, dx, fx);
+            fy = fmaf(s, dy, fy);
+            fz = fmaf(s, dz, fz);
+            if (ENERGY) e += ok ? 0.5f * ep : 0.0f;
+        }
+        __syncwarp();
+    }
+    B.fnb[base + si] = make_float4(fx, fy, fz, e);
+}
+
+// Chain terms of one replica: bonds, angles (minimum image), z and the ratchet,
+// the bias force; writes fch (bonded + bias) per chain atom. Also closes the
+// rebuild bookkeeping of the step.
+template <bool ENERGY>
+__global__ void __launch_bounds__(512) k_box_chain(BoxDev B, const TopoDev* __restrict__ topo,
+                                                   StateDev st, RunParams P, int r0,
+                                                   int do_ratchet, int count_step) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long zred[16];
+    __shared__ double ered[16];
+    __shared__ double s_factor;
+    __shared__ int s_bias;
+    const int r = blockIdx.x + r0;
+    const TopoDev tp = *topo;
+    const int nch = B.n_chain, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4* x = (float4*)smem_raw;                       // nch chain positions
+    long long* F = (long long*)(x + nch);                // 3 nch fixed point
+    float* hc = (float*)(F + 3 * nch);                   // contacts
+    const size_t base = (size_t)r * B.np;
+    for (int a = tid; a < nch; a += blockDim.x) x[a] = B.pos[base + B.slot_of[(size_t)r * B.n_atoms + a]];
+    for (int i = tid; i < 3 * nch; i += blockDim.x) F[i] = 0;
+    __syncthreads();
+    const float L = B.L, iL = B.invL;
+    double eb = 0.0;
+    for (int b = tid; b < tp.n_bonds; b += blockDim.x) {
+        const int2 ij = tp.bond_ij[b];
+        const float2 par = tp.bond_par[b];
+        const float dx = min_img(x[ij.y].x - x[ij.x].x, L, iL), dy = min_img(x[ij.y].y - x[ij.x].y, L, iL),
+                    dz = min_img(x[ij.y].z - x[ij.x].z, L, iL);
+        const float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float dr = rr - par.x;
+        const float f = par.y * dr / rr;
+        const long long qx = f2fix(f * dx), qy = f2fix(f * dy), qz = f2fix(f * dz);
+        atomicAdd((unsigned long long*)&F[3 * ij.x], (unsigned long long)qx);
+        atomicAdd((unsigned long long*)&F[3 * ij.x + 1], (unsigned long long)qy);
+        atomicAdd((unsigned long long*)&F[3 * ij.x + 2], (unsigned long long)qz);
+        atomicAdd((unsigned long long*)&F[3 * ij.y], (unsigned long long)(-qx));
+        atomicAdd((unsigned long long*)&F[3 * ij.y + 1], (unsigned long long)(-qy));
+        atomicAdd((unsigned long long*)&F[3 * ij.y + 2], (unsigned long long)(-qz));
+        if (ENERGY) eb += 0.5 * (double)par.y * (double)dr * (double)dr;
+    }
+    for (int q = tid; q < tp.n_angles; q += blockDim.x) {
+        const int4 ijk = tp.ang_ijk[q];
+        const float2 par = tp.ang_par[q];
+        const float ux = min_img(x[ijk.x].x - x[ijk.y].x, L, iL), uy = min_img(x[ijk.x].y - x[ijk.y].y, L, iL),
+                    uz = min_img(x[ijk.x].z - x[ijk.y].z, L, iL);
+        const float wx = min_img(x[ijk.z].x - x[ijk.y].x, L, iL), wy = min_img(x[ijk.z].y - x[ijk.y].y, L, iL),
+                    wz = min_img(x[ijk.z].z - x[ijk.y].z, L, iL);
+        const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+        const float sn = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
+        const float cs = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
+        const float ru2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+        const float rw2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+        const float dth = atan2f(sn, cs) - par.x;
+        const float g = -par.y * dth / sn;
+        const float au = cs / ru2, aw = cs / rw2;
+        const float f1x = g * fmaf(au, ux, -wx), f1y = g * fmaf(au, uy, -wy), f1z = g * fmaf(au, uz, -wz);
+        const float f3x = g * fmaf(aw, wx, -ux), f3y = g * fmaf(aw, wy, -uy), f3z = g * fmaf(aw, wz, -uz);
+        const long long a1 = f2fix(f1x), a2 = f2fix(f1y), a3 = f2fix(f1z);
+        const long long c1 = f2fix(f3x), c2 = f2fix(f3y), c3 = f2fix(f3z);
+        atomicAdd((unsigned long long*)&F[3 * ijk.x], (unsigned long long)a1);
+        atomicAdd((unsigned long long*)&F[3 * ijk.x + 1], (unsigned long long)a2);
+        atomicAdd((unsigned long long*)&F[3 * ijk.x + 2], (unsigned long long)a3);
+        atomicAdd((unsigned long long*)&F[3 * ijk.z], (unsigned long long)c1);
+        atomicAdd((unsigned long long*)&F[3 * ijk.z + 1], (unsigned long long)c2);
+        atomicAdd((unsigned long long*)&F[3 * ijk.z + 2], (unsigned long long)c3);
+        atomicAdd((unsigned long long*)&F[3 * ijk.y], (unsigned long long)(-a1 - c1));
+        atomicAdd((unsigned long long*)&F[3 * ijk.y + 1], (unsigned long long)(-a2 - c2));
+        atomicAdd((unsigned long long*)&F[3 * ijk.y + 2], (unsigned long long)(-a3 - c3));
+        if (ENERGY) eb += 0.5 * (double)par.y * (double)dth * (double)dth;
+    }
+    // z of Eq. (zrMD): (C - C0)^2 in float-float, summed in 2^-40 fixed point
+    long long zacc = 0;
+    if (P.bias == 1) {
+        for (int c = tid; c < tp.n_contacts; c += blockDim.x) {
+            const int2 ij = tp.con_ij[c];
+            const float4 a = x[ij.x], b = x[ij.y];
+            // exact float-float separation, then the minimum-image shift (a multiple of L)
+            ff dx = ff_diff(b.x, a.x), dy = ff_diff(b.y, a.y), dz = ff_diff(b.z, a.z);
+            dx = ff_add_f(dx, -L * rintf((b.x - a.x) * iL));
+            dy = ff_add_f(dy, -L * rintf((b.y - a.y) * iL));
+            dz = ff_add_f(dz, -L * rintf((b.z - a.z) * iL));
+            const ff u = ff_mul(ff_r2(dx, dy, dz), P.inv_r0sq_ff);
+            const ff C = contact_C_ff(u);
+            const float2 c0 = tp.con_C0[c];
+            const ff d = ff_add(C, ff{-c0.x, -c0.y});
+            hc[c] = (d.hi + d.lo) * contact_dC_du(u.hi);
+            zacc += ff2fix40(ff_sqr(d));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        zacc += __shfl_down_sync(kFullB, zacc, o);
+        eb += __shfl_down_sync(kFullB, eb, o);
+    }
+    if (lane == 0) {
+        zred[warp] = zacc;
+        ered[warp] = eb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long zt = 0;
+        double et = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            zt += zred[w];
+            et += ered[w];
+        }
+        double factor = 0.0;
+        if (P.bias == 1) {
+            const double z = (double)zt * 9.094947017729282e-13;  // 2^-40
+            st.z[r] = z;
+            if (do_ratchet) {  // Eq. (FrMD) with theta(0) = 1
+                if (z < st.zm[r])
+                    st.zm[r] = z;
+                else
+                    factor = -P.k_R * (z - st.zm[r]);
+            }
+        }
+        s_factor = factor;
+        s_bias = factor != 0.0;
+        if (ENERGY) B.eb[r] = et;
+        if (B.need[r])
+            B.need[r] = 0;  // the rebuild of this step is complete
+        else if (count_step)
+            B.since[r] += 1;
+    }
+    __syncthreads();
+    const float k = -(float)s_factor * 4.0f * P.inv_r0sq;
+    float tb = 0.f;
+    for (int a = tid; a < nch; a += blockDim.x) {
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        if (s_bias) {
+            const float4 xa = x[a];
+            for (int q = tp.con_off[a]; q < tp.con_off[a + 1]; ++q) {
+                const int2 cp = tp.con_nbr[q];
+                const float4 xp = x[cp.y];
+                const float h = hc[cp.x];
+                bx = fmaf(h, min_img(xp.x - xa.x, L, iL), bx);
+                by = fmaf(h, min_img(xp.y - xa.y, L, iL), by);
+                bz = fmaf(h, min_img(xp.z - xa.z, L, iL), bz);
+            }
+            bx *= k;
+            by *= k;
+            bz *= k;
+            tb += (bx * bx + by * by + bz * bz) * tp.inv_m[a];
+        }
+        B.fch[(size_t)r * nch + a] = make_float4(fix2f(F[3 * a]) + bx, fix2f(F[3 * a + 1]) + by,
+                                                 fix2f(F[3 * a + 2]) + bz, 0.f);
+    }
+    // bias functional: fixed order (lane tree, then warps in index order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tb += __shfl_down_sync(kFullB, tb, o);
+    __shared__ float tred[16];
+    if (lane == 0) tred[warp] = tb;
+    __syncthreads();
+    if (tid == 0 && s_bias && count_step) {
+        float ts = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ts += tred[w];
+        st.T[r] += (double)P.dt / P.gamma * (double)ts;
+    }
+}
+
+// BAOAB half steps per slot: B closes the evaluated step, A starts the next one.
+__global__ void k_box_integrate(BoxDev B, const TopoDev* __restrict__ topo, StateDev st,
+                                RunParams P, const uint32_t* __restrict__ rep_ids, long long step,
+                                int do_b, int do_a) {
+    const int r = blockIdx.y;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.np || st.status[r] != 0) return;
+    const size_t base = (size_t)r * B.np;
+    const int a = B.id[base + s];
+    if (a < 0) return;
+    const TopoDev& tp = *topo;
+    float4 f = B.fnb[base + s];
+    if (a < B.n_chain) {
+        const float4 c = B.fch[(size_t)r * B.n_chain + a];
+        f.x += c.x;
+        f.y += c.y;
+        f.z += c.z;
+    }
+    const float im = tp.inv_m[a];
+    const float hdt = P.half_dt;
+    float4 v = B.vel[base + s];
+    float4 x = B.pos[base + s];
+    if (do_b) {
+        v.x = fmaf(hdt * im, f.x, v.x);
+        v.y = fmaf(hdt * im, f.y, v.y);
+        v.z = fmaf(hdt * im, f.z, v.z);
+    }
+    if (do_a) {
+        v.x = fmaf(hdt * im, f.x, v.x);
+        v.y = fmaf(hdt * im, f.y, v.y);
+        v.z = fmaf(hdt * im, f.z, v.z);
+        x.x = fmaf(hdt, v.x, x.x);
+        x.y = fmaf(hdt, v.y, x.y);
+        x.z = fmaf(hdt, v.z, x.z);
+        const uint4 rb = philox4x32_10(make_uint4((uint32_t)a, rep_ids[r], (uint32_t)step, 0u),
+                                       P.key0, P.key1);
+        const float4 xi = normals4_f32(rb);
+        const float sd = tp.noise_sd[a];
+        v.x = fmaf(P.c1, v.x, sd * xi.x);
+        v.y = fmaf(P.c1, v.y, sd * xi.y);
+        v.z = fmaf(P.c1, v.z, sd * xi.z);
+        x.x = fmaf(hdt, v.x, x.x);
+        x.y = fmaf(hdt, v.y, x.y);
+        x.z = fmaf(hdt, v.z, x.z);
+        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
+              isfinite(v.z)))
+            atomicOr(&st.status[r], SCPS_FLAG_NONFINITE);
+        B.pos[base + s] = x;
+        const float4 p0 = B.pos_ref[base + s];
+        const float ddx = x.x - p0.x, ddy = x.y - p0.y, ddz = x.z - p0.z;
+        const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+        atomicMax(&B.maxd2[r], __float_as_uint(d2));  // non-negative floats order as unsigned
+    }
+    B.vel[base + s] = v;
+}
+
+// Frame output of the evaluated configuration (positions in atom-id order).
+__global__ void k_box_frame(BoxDev B, StateDev st, RunParams P, long long frame_atoms) {
+    const int r = blockIdx.y;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.np) return;
+    const int a = B.id[(size_t)r * B.np + s];
+    if (a < 0) return;
+    const long long slot = st.n_saved[r] % P.max_frames;
+    const float4 x = B.pos[(size_t)r * B.np + s];
+    float* fr = st.frames + 3 * ((long long)r * frame_atoms + slot * B.n_atoms + a);
+    fr[0] = x.x;
+    fr[1] = x.y;
+    fr[2] = x.z;
+}
+
+// Frame scalars; the potential energy is the sum of the per-slot shares in slot order.
+__global__ void k_box_frame_scalars(BoxDev B, StateDev st, RunParams P) {
+    const int r = blockIdx.x;
+    __shared__ double red[256];
+    double e = 0.0;
+    for (int s = threadIdx.x; s < B.np; s += blockDim.x) e += (double)B.fnb[(size_t)r * B.np + s].w;
+    red[threadIdx.x] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
+        const long long slot = st.n_saved[r] % P.max_frames;
+        const long long fi = (long long)r * P.max_frames + slot;
+        st.fz[fi] = st.z[r];
+        st.fzm[fi] = st.zm[r];
+        st.fe[fi] = t + B.eb[r];
+        st.fT[fi] = st.T[r];
+        st.n_saved[r] += 1;
+    }
+}
+
+__global__ void k_box_step_count(StateDev st, int R, long long k) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R && st.status[r] == 0) st.step[r] += k;
+}
+
+// ------------------------------------------------------------------ host side
+size_t box_chain_smem(int n_chain, int n_contacts) {
+    return sizeof(float4) * n_chain + sizeof(long long) * 3 * n_chain + sizeof(float) * n_contacts;
+}
+
+// One force evaluation of replicas [r0, r0 + nr): rebuild when forced (or, when
+// `auto_ok`, when due), pair forces, chain terms and the ratchet.
+static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev& st,
+                            const RunParams& P, int r0, int nr, int elec, int ncon_max,
+                            bool energy, int do_ratchet, int count_step, int auto_ok,
+                            cudaStream_t s) {
+    k_box_sort<<<nr, 1024, 0, s>>>(B, topo, st, r0, auto_ok);
+    const dim3 gt((B.nt + 3) / 4, nr);
+    k_box_tiles<<<gt, 128, 0, s>>>(B, r0);
+    k_box_list<<<gt, 128, 0, s>>>(B, st, r0);
+#define PAIRS(E)                                                                                \
+    switch (elec) {                                                                             \
+        case ELEC_DDIEL: k_box_pairs<ELEC_DDIEL, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;  \
+        case ELEC_RF: k_box_pairs<ELEC_RF, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;        \
+        case ELEC_PLAIN: k_box_pairs<ELEC_PLAIN, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;  \
+        default: k_box_pairs<ELEC_NONE, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;           \
+    }
+    if (energy) {
+        PAIRS(true)
+    } else {
+        PAIRS(false)
+    }
+#undef PAIRS
+    const size_t smem = box_chain_smem(B.n_chain, ncon_max);
+    if (energy)
+        k_box_chain<true><<<nr, 512, smem, s>>>(B, topo, st, P, r0, do_ratchet, count_step);
+    else
+        k_box_chain<false><<<nr, 512, smem, s>>>(B, topo, st, P, r0, do_ratchet, count_step);
+    return cudaGetLastError();
+}
+
+cudaError_t box_prepare(const BoxDev& B, int n_contacts_max) {
+    const size_t smem = box_chain_smem(B.n_chain, n_contacts_max);
+    cudaError_t e = cudaFuncSetAttribute(k_box_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_box_chain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+// n_steps steps of replicas [0, R) (kernel launches on stream s).
+cudaError_t box_run(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
+                    const uint32_t* rep_ids, int R, int elec, int ncon_max, long long step0,
+                    long long n_steps, long long frame_atoms, cudaStream_t s) {
+    const dim3 ga((B.np + 255) / 256, R);
+    // re-evaluate the current configuration (no scheduled rebuild here, so the
+    // result does not depend on how steps are split into calls)
+    cudaError_t e = box_eval(B, topo, st, P, 0, R, elec, ncon_max, false, 1, 0, 0, s);
+    if (e != cudaSuccess) return e;
+    k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step0, 0, 1);
+    for (long long k = 1; k <= n_steps; ++k) {
+        const long long step = step0 + k;
+        const bool save = P.save_interval > 0 && step % P.save_interval == 0;
+        e = box_eval(B, topo, st, P, 0, R, elec, ncon_max, save, 1, 1, 1, s);
+        if (e != cudaSuccess) return e;
+        if (save) k_box_frame<<<ga, 256, 0, s>>>(B, st, P, frame_atoms);
+        k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step, 1, k < n_steps ? 1 : 0);
+        if (save) k_box_frame_scalars<<<R, 256, 0, s>>>(B, st, P);
+    }
+    k_box_step_count<<<(R + 127) / 128, 128, 0, s>>>(st, R, n_steps);
+    return cudaGetLastError();
+}
+
+// Energy and forces of one configuration X (atom order) in the evaluation slot r_eval.
+__global__ void k_box_load_frame(BoxDev B, const TopoDev* __restrict__ topo, StateDev st,
+                                 const float* __restrict__ X, int r) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.np) return;
+    const size_t base = (size_t)r * B.np;
+    if (s < B.n_atoms) {
+        B.pos[base + s] = make_float4(X[3 * s], X[3 * s + 1], X[3 * s + 2], topo->qs[s]);
+        B.vel[base + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        B.id[base + s] = s;
+        B.slot_of[(size_t)r * B.n_atoms + s] = s;
+    } else {
+        B.id[base + s] = -1;
+    }
+    if (s == 0) {
+        B.need[r] = 1;
+        st.status[r] = 0;
+    }
+}
+
+cudaError_t box_load(const BoxDev& B, const TopoDev* topo, const StateDev& st, const float* X,
+                     int r, cudaStream_t s) {
+    k_box_load_frame<<<(B.np + 255) / 256, 256, 0, s>>>(B, topo, st, X, r);
+    return cudaGetLastError();
+}
+
+__global__ void k_box_store_forces(BoxDev B, int r, float* __restrict__ F) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.np) return;
+    const size_t base = (size_t)r * B.np;
+    const int a = B.id[base + s];
+    if (a < 0) return;
+    float4 f = B.fnb[base + s];
+    if (a < B.n_chain) {
+        const float4 c = B.fch[(size_t)r * B.n_chain + a];
+        f.x += c.x;
+        f.y += c.y;
+        f.z += c.z;
+    }
+    F[3 * a] = f.x;
+    F[3 * a + 1] = f.y;
+    F[3 * a + 2] = f.z;
+}
+
+__global__ void k_box_store_energy(BoxDev B, StateDev st, int r, double* U, double* Z) {
+    __shared__ double red[256];
+    double e = 0.0;
+    for (int s = threadIdx.x; s < B.np; s += blockDim.x) e += (double)B.fnb[(size_t)r * B.np + s].w;
+    red[threadIdx.x] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
+        *U = t + B.eb[r];
+        if (Z) *Z = st.z[r];
+    }
+}
+
+cudaError_t box_energy_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st,
+                              const RunParams& P, int r_eval, int elec, int ncon_max,
+                              const float* X, double* U, float* F, double* Z, cudaStream_t s) {
+    const int g = (B.np + 255) / 256;
+    k_box_load_frame<<<g, 256, 0, s>>>(B, topo, st, X, r_eval);
+    cudaError_t e = box_eval(B, topo, st, P, r_eval, 1, elec, ncon_max, true, 0, 0, 0, s);
+    if (e != cudaSuccess) return e;
+    if (F) k_box_store_forces<<<g, 256, 0, s>>>(B, r_eval, F);
+    k_box_store_energy<<<1, 256, 0, s>>>(B, st, r_eval, U, Z);
+    return cudaGetLastError();
+}
+
+}  // namespace scps

@@ -33,6 +33,16 @@ cudaError_t launch_native_map(int nc, const int2* pairs, const double* xN, doubl
 cudaError_t launch_add_steps(long long* step, int n, long long k, cudaStream_t s);
 cudaError_t launch_hvp(int elec, const TopoDev* topo, const RunParams& P, const float* X,
                        const float* V, float* HV, long long n_frames, int nta, cudaStream_t s);
+cudaError_t box_prepare(const BoxDev& B, int n_contacts_max);
+cudaError_t box_load(const BoxDev& B, const TopoDev* topo, const StateDev& st, const float* X,
+                     int r, cudaStream_t s);
+cudaError_t box_run(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
+                    const uint32_t* rep_ids, int R, int elec, int ncon_max, long long step0,
+                    long long n_steps, long long frame_atoms, cudaStream_t s);
+cudaError_t box_energy_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st,
+                              const RunParams& P, int r_eval, int elec, int ncon_max,
+                              const float* X, double* U, float* F, double* Z, cudaStream_t s);
+constexpr int kMaxBoxAtoms = 1 << 20;
 }  // namespace scps
 
 using namespace scps;
@@ -94,6 +104,8 @@ struct scps_system {
     int bias_kind = SCPS_BIAS_NONE;
     scps_info info{};
     size_t bytes = 0;
+    bool is_box = false;
+    BoxDev box{};
 
     template <class T>
     cudaError_t alloc(T** p, size_t n) {
@@ -117,10 +129,10 @@ struct scps_system {
 
 namespace {
 
-int validate_topology(const scps_topology_desc& t, int idx) {
-    if (t.n_atoms <= 0 || t.n_atoms > kMaxChainAtoms)
+int validate_topology(const scps_topology_desc& t, int idx, int max_atoms) {
+    if (t.n_atoms <= 0 || t.n_atoms > max_atoms)
         return fail(SCPS_ERR_INVALID_ARG, "topology %d: n_atoms %d outside [1, %d]", idx, t.n_atoms,
-                    kMaxChainAtoms);
+                    max_atoms);
     if (!t.mass || !t.charge || !t.sigma || !t.eps)
         return fail(SCPS_ERR_INVALID_ARG, "topology %d: per-atom array is NULL", idx);
     if (t.n_bonds < 0 || t.n_angles < 0 || t.n_excl < 0)
@@ -295,9 +307,18 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     if (d->model == SCPS_MODEL_CHAIN) {
         if (d->n_topologies <= 0 || !d->topologies || !d->replica_topology)
             return bail(fail(SCPS_ERR_INVALID_ARG, "chain model needs topologies and replica_topology"));
-        if (d->box != 0.0)
-            return bail(fail(SCPS_ERR_UNSUPPORTED, "periodic boxes are not supported by the chain model"));
         if (!(d->cutoff > 0.0)) return bail(fail(SCPS_ERR_INVALID_ARG, "cutoff must be > 0"));
+        s->is_box = d->box != 0.0;
+        if (s->is_box) {
+            const double skin = d->skin > 0.0 ? d->skin : 0.15;
+            if (!(d->box > 2.0 * (d->cutoff + skin)))
+                return bail(fail(SCPS_ERR_INVALID_ARG, "box %.3f nm is too small for cutoff + skin",
+                                 d->box));
+            if (d->n_topologies != 1)
+                return bail(fail(SCPS_ERR_UNSUPPORTED, "the periodic box takes one topology"));
+            if (d->exec != SCPS_EXEC_RESIDENT)
+                return bail(fail(SCPS_ERR_UNSUPPORTED, "the periodic box has one execution form"));
+        }
         if (d->elec < SCPS_ELEC_NONE || d->elec > SCPS_ELEC_PLAIN)
             return bail(fail(SCPS_ERR_INVALID_ARG, "unknown electrostatics %d", d->elec));
         if (d->elec == SCPS_ELEC_DDIEL && !(d->k_dd > 0.0))
@@ -306,7 +327,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
             return bail(fail(SCPS_ERR_UNSUPPORTED, "the chain model integrates with BAOAB"));
         s->topos.resize(d->n_topologies);
         for (int t = 0; t < d->n_topologies; ++t) {
-            int rc = validate_topology(d->topologies[t], t);
+            int rc = validate_topology(d->topologies[t], t, s->is_box ? kMaxBoxAtoms : kMaxChainAtoms);
             if (rc) return bail(rc);
             rc = build_topology(s, d->topologies[t], s->topos[t]);
             if (rc) return bail(rc);
@@ -347,12 +368,13 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         if (e_ != cudaSuccess)                               \
             return bail(fail(SCPS_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e_))); \
     } while (0)
-    ALLOC(st.zm, R);
-    ALLOC(st.z, R);
-    ALLOC(st.step, R);
-    ALLOC(st.T, R);
-    ALLOC(st.status, R);
-    ALLOC(st.n_saved, R);
+    const int Rs = R + (s->is_box ? 1 : 0);  // the box keeps one more slot for evaluations
+    ALLOC(st.zm, Rs);
+    ALLOC(st.z, Rs);
+    ALLOC(st.step, Rs);
+    ALLOC(st.T, Rs);
+    ALLOC(st.status, Rs);
+    ALLOC(st.n_saved, Rs);
     ALLOC(st.fz, (size_t)R * mf);
     ALLOC(st.fzm, (size_t)R * mf);
     ALLOC(st.fe, (size_t)R * mf);
@@ -393,6 +415,54 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         const bool one_cta_per_sm = (long long)R * s->cluster <= n_sm;
         s->threads = d->threads ? d->threads : (one_cta_per_sm ? 1024 : auto_threads(s->nta));
         s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
+    }
+    if (s->is_box) {
+        const scps_topology_desc& t = d->topologies[0];
+        int nch = 0;  // bonded atoms come first: the chain is atoms [0, nch)
+        for (int b = 0; b < 2 * t.n_bonds; ++b) nch = std::max(nch, t.bonds[b] + 1);
+        for (int a = 0; a < 3 * t.n_angles; ++a) nch = std::max(nch, t.angles[a] + 1);
+        for (int e = 0; e < 2 * t.n_excl; ++e) nch = std::max(nch, t.excl[e] + 1);
+        BoxDev& B = s->box;
+        B.n_atoms = t.n_atoms;
+        B.n_chain = std::max(nch, 1);
+        B.np = ((t.n_atoms + kTile - 1) / kTile) * kTile;
+        B.nt = B.np / kTile;
+        B.max_nbr = 256;
+        B.rebuild_every = d->rebuild_every > 0 ? d->rebuild_every : 20;
+        B.L = (float)d->box;
+        B.invL = (float)(1.0 / d->box);
+        B.nc = std::max(1, std::min(16, (int)(d->box / 0.4)));
+        const double skin = d->skin > 0.0 ? d->skin : 0.15;
+        B.rlist2 = (float)((d->cutoff + skin) * (d->cutoff + skin));
+        B.skin2_quarter = (float)(0.25 * skin * skin);
+        const size_t np = (size_t)Rs * B.np;
+#define BALLOC(p, n)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = s->alloc(&(p), (size_t)(n));                                       \
+        if (e_ != cudaSuccess)                                                              \
+            return bail(fail(SCPS_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e_)));     \
+    } while (0)
+        BALLOC(B.pos, np);
+        BALLOC(B.vel, np);
+        BALLOC(B.par, np);
+        BALLOC(B.id, np);
+        BALLOC(B.fnb, np);
+        BALLOC(B.pos2, np);
+        BALLOC(B.vel2, np);
+        BALLOC(B.key, np);
+        BALLOC(B.pos_ref, np);
+        BALLOC(B.slot_of, (size_t)Rs * B.n_atoms);
+        BALLOC(B.tlo, (size_t)Rs * B.nt);
+        BALLOC(B.thi, (size_t)Rs * B.nt);
+        BALLOC(B.nbr, (size_t)Rs * B.nt * B.max_nbr);
+        BALLOC(B.nnbr, (size_t)Rs * B.nt);
+        BALLOC(B.need, Rs);
+        BALLOC(B.since, Rs);
+        BALLOC(B.maxd2, Rs);
+        BALLOC(B.fch, (size_t)Rs * B.n_chain);
+        BALLOC(B.eb, Rs);
+#undef BALLOC
+        if (box_prepare(B, 0) != cudaSuccess) return bail(fail(SCPS_ERR_CUDA, "box set-up failed"));
     }
     rc = scps_set_state(s, d->x0, d->v0, nullptr, nullptr, nullptr);
     if (rc) return bail(rc);
@@ -499,9 +569,21 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
             s->topos[t].ncon = nc;
             ncon_max = std::max(ncon_max, nc);
         }
-        const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, ncon_max);
-        if (smem > 227 * 1024)
-            return fail(SCPS_ERR_UNSUPPORTED, "shared memory %zu B exceeds the per-CTA limit", smem);
+        if (s->is_box) {
+            for (int c = 0; c < b->n_pairs[0]; ++c)
+                if (b->pairs[0][2 * c] >= s->box.n_chain || b->pairs[0][2 * c + 1] >= s->box.n_chain)
+                    return fail(SCPS_ERR_INVALID_ARG, "contact %d is not between chain atoms", c);
+            const size_t smem = sizeof(float4) * s->box.n_chain + sizeof(long long) * 3 * s->box.n_chain +
+                                sizeof(float) * ncon_max;
+            if (smem > 227 * 1024)
+                return fail(SCPS_ERR_UNSUPPORTED, "chain of %d atoms and %d contacts is too large",
+                            s->box.n_chain, ncon_max);
+            SCPS_CU(box_prepare(s->box, ncon_max));
+        } else {
+            const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, ncon_max);
+            if (smem > 227 * 1024)
+                return fail(SCPS_ERR_UNSUPPORTED, "shared memory %zu B exceeds the per-CTA limit", smem);
+        }
         if (s->d.exec == SCPS_EXEC_PLAIN && ncon_max > 16384)
             return fail(SCPS_ERR_UNSUPPORTED, "plain form supports up to 16384 contacts");
         s->ncon_max = ncon_max;
@@ -541,6 +623,14 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
         P.n_steps = n_steps;
         SCPS_CU(launch_toy(s->st, P, s->d_rep_ids, cs));
         launches = 1;
+    } else if (s->is_box) {
+        for (int r = 1; r < R; ++r)
+            if (s->host_step[r] != s->host_step[0])
+                return fail(SCPS_ERR_STATE, "periodic-box replicas must share one step counter");
+        const long long frame_atoms = (long long)std::max(s->d.max_frames, 1) * s->box.n_atoms;
+        SCPS_CU(box_run(s->box, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max,
+                        s->host_step[0], n_steps, frame_atoms, cs));
+        launches = 8 * (n_steps + 1);
     } else if (s->d.exec == SCPS_EXEC_PLAIN) {
         P.n_steps = n_steps;
         std::vector<RepDev> reps(R);
@@ -596,6 +686,16 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
     if (n_frames == 0) return SCPS_OK;
     if (!X || !U) return fail(SCPS_ERR_INVALID_ARG, "X and U are required");
     if (z && s->base.bias != 1) return fail(SCPS_ERR_STATE, "z needs a contact bias (scps_set_bias)");
+    if (s->is_box) {  // frame by frame in the evaluation slot of the box
+        RunParams P = s->base;
+        if (!z) P.bias = 0;
+        const int n = s->box.n_atoms;
+        for (long long f = 0; f < n_frames; ++f)
+            SCPS_CU(box_energy_forces(s->box, s->d_topos, s->st, P, s->d.n_replicas, s->d.elec,
+                                      s->ncon_max, X + f * n * 3, U + f, F ? F + f * n * 3 : nullptr,
+                                      z ? z + f : nullptr, (cudaStream_t)stream));
+        return SCPS_OK;
+    }
     const TopoHost& th = s->topos[topo];
     const int nta = ((th.n + kTile - 1) / kTile) * kTile;
     const int nt = nta / kTile;
@@ -675,6 +775,31 @@ int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* st
     if (s->model == SCPS_MODEL_TOY2D) {
         if (x) SCPS_CU(cudaMemcpy(x, s->st.xy, sizeof(double2) * R, cudaMemcpyDeviceToHost));
         if (v) std::memset(v, 0, sizeof(double) * 2 * R);
+    } else if (s->is_box) {  // slots are in tile order: place each atom by its id
+        const BoxDev& B = s->box;
+        const size_t np = (size_t)R * B.np;
+        std::vector<float4> hp(np), hv(np);
+        std::vector<int> hid(np);
+        SCPS_CU(cudaMemcpy(hid.data(), B.id, sizeof(int) * np, cudaMemcpyDeviceToHost));
+        if (x) SCPS_CU(cudaMemcpy(hp.data(), B.pos, sizeof(float4) * np, cudaMemcpyDeviceToHost));
+        if (v) SCPS_CU(cudaMemcpy(hv.data(), B.vel, sizeof(float4) * np, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < R; ++r)
+            for (int q = 0; q < B.np; ++q) {
+                const size_t sl = (size_t)r * B.np + q;
+                const int a = hid[sl];
+                if (a < 0) continue;
+                const size_t o = 3 * ((size_t)r * B.n_atoms + a);
+                if (x) {
+                    x[o] = hp[sl].x;
+                    x[o + 1] = hp[sl].y;
+                    x[o + 2] = hp[sl].z;
+                }
+                if (v) {
+                    v[o] = hv[sl].x;
+                    v[o + 1] = hv[sl].y;
+                    v[o + 2] = hv[sl].z;
+                }
+            }
     } else {
         std::vector<float4> h(s->n_atoms_total);
         if (x) {
@@ -710,6 +835,35 @@ int scps_set_state(scps_system* s, const double* x, const double* v, const doubl
             for (int r = 0; r < 2 * R; ++r)
                 if (!std::isfinite(x[r])) return fail(SCPS_ERR_NONFINITE, "non-finite position");
             SCPS_CU(cudaMemcpy(s->st.xy, x, sizeof(double2) * R, cudaMemcpyHostToDevice));
+        }
+    } else if (s->is_box) {  // positions go in atom order; the next step rebuilds the lists
+        const BoxDev& B = s->box;
+        if (v && !x) return fail(SCPS_ERR_UNSUPPORTED, "the periodic box sets velocities with positions");
+        if (x) {
+            const size_t n3 = (size_t)3 * R * B.n_atoms;
+            std::vector<float> hx(n3), hv(n3, 0.f);
+            for (size_t i = 0; i < n3; ++i) {
+                if (!std::isfinite(x[i]) || (v && !std::isfinite(v[i])))
+                    return fail(SCPS_ERR_NONFINITE, "non-finite position or velocity");
+                hx[i] = (float)x[i];
+                if (v) hv[i] = (float)v[i];
+            }
+            float* dx = nullptr;
+            SCPS_CU(cudaMalloc(&dx, sizeof(float) * n3));
+            cudaError_t e = cudaMemcpy(dx, hx.data(), sizeof(float) * n3, cudaMemcpyHostToDevice);
+            for (int r = 0; r < R && e == cudaSuccess; ++r)
+                e = box_load(B, s->d_topos, s->st, dx + (size_t)3 * r * B.n_atoms, r, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            cudaFree(dx);
+            SCPS_CU(e);
+            // velocities: slots are in atom order right after the load
+            std::vector<float4> h4((size_t)R * B.np, make_float4(0.f, 0.f, 0.f, 0.f));
+            for (int r = 0; r < R; ++r)
+                for (int a = 0; a < B.n_atoms; ++a) {
+                    const size_t o = 3 * ((size_t)r * B.n_atoms + a);
+                    h4[(size_t)r * B.np + a] = make_float4(hv[o], hv[o + 1], hv[o + 2], 0.f);
+                }
+            SCPS_CU(cudaMemcpy(B.vel, h4.data(), sizeof(float4) * h4.size(), cudaMemcpyHostToDevice));
         }
     } else {
         std::vector<float4> h(s->n_atoms_total);

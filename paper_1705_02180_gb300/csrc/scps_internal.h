@@ -82,4 +82,29 @@ struct RunParams {
     double gamma;
 };
 
+// Periodic-box state of all replicas (slot arrays are [replica][np], in tile order).
+struct BoxDev {
+    int n_atoms, n_chain, np, nt, max_nbr, rebuild_every, nc;
+    float L, invL, rlist2, skin2_quarter;
+    float4* pos;      // (x, y, z, qs)
+    float4* vel;
+    float2* par;      // (sigma/2, sqrt(24 eps))
+    int* id;          // atom id of each slot, -1 for padding
+    float4* fnb;      // non-bonded force (w: energy share)
+    float4* pos2;     // sort buffers
+    float4* vel2;
+    int* slot_of;     // [replica][n_atoms]
+    int* key;
+    float4* pos_ref;  // positions at the last rebuild
+    float4* tlo;      // [replica][nt] tile boxes
+    float4* thi;
+    uint32_t* nbr;    // [replica][nt][max_nbr]: j tile | shift code << 20
+    int* nnbr;        // [replica][nt]
+    int* need;        // [replica] rebuild flag
+    int* since;       // [replica] evaluations since the last rebuild
+    unsigned* maxd2;  // [replica] largest squared displacement since then (float bits)
+    float4* fch;      // [replica][n_chain] bonded + bias force on chain atoms
+    double* eb;       // [replica] bonded energy (save steps)
+};
+
 }  // namespace scps

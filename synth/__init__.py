@@ -11,3 +11,4 @@ from .chain import ChainSystem, make_chain, residues_for_atoms
 from .toy import ToySystem, make_toy
 
 __all__ = ["ChainSystem", "make_chain", "residues_for_atoms", "ToySystem", "make_toy"]
+from .box import BoxSystem, make_box  # noqa: E402
