@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="chain", choices=["chain", "batched", "box", "toy", "hvp"],
+                   help="chain: the headline workload; the others measure the other configurations")
     return p.parse_args()
 
 
@@ -187,10 +189,137 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_calls(torch, step_fn, K, W):
+    """W untimed calls, then K calls timed with CUDA events on a private stream (L2
+    flushed between calls, outside the events). Returns per-call seconds and clocks."""
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            step_fn(stream.cuda_stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step_fn(stream.cuda_stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3, clk
+
+
+def run_extra(args):
+    """The other workloads of the build target, one JSON line each."""
+    import torch
+
+    import paper_1705_02180_gb300 as pkg
+    torch.cuda.set_device(0)
+    W, K = max(args.warmup, 3), args.steps
+    if args.workload == "batched":
+        sizes = [19, 35, 75]
+        counts = [171, 171, 170]
+        chains = [synth.make_chain(r, seed=1) for r in sizes]
+        reps = np.concatenate([np.full(n, t) for t, n in enumerate(counts)])
+        x0 = np.concatenate([chains[t].x_unfolded for t in reps])
+        v0 = np.concatenate([chains[t].velocities(1, KT_300, SEED + k)[0] for k, t in enumerate(reps)])
+        spc = args.md_steps_per_call
+        s = pkg.System(topologies=[pkg.chain_topology(c) for c in chains], replica_topology=reps,
+                       x0=x0, v0=v0, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002,
+                       gamma=1.0, kT=KT_300, seed=SEED, threads=args.threads,
+                       steps_per_graph=spc)
+        s.set_contact_bias([c.contacts for c in chains], [c.x_native for c in chains], k_R=1e-4)
+        durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
+        atoms = int(sum(chains[t].n_atoms for t in reps))
+        info = s.info()
+        out = {"metric": "biased-Langevin atom-steps/s", "value": atoms * spc * K / durs.sum(),
+               "unit": "atom-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
+               "config": {"workload": "512 replicas: 171 x 304 + 171 x 560 + 170 x 1200 atoms, "
+                                      "one resident launch, dt 2 fs, 300 K, k_R 1e-4",
+                          "atoms": atoms, "md_steps_per_call": spc,
+                          "threads_per_cta": info["threads"], "cluster": info["cluster_size"]},
+               "gpu_launches": int(info["graph_nodes_last_call"]) * K, "clocks": clk}
+        s.close()
+    elif args.workload == "box":
+        b = synth.make_box(35, 24000, seed=1)
+        R = 16
+        c = b.chain
+        x0 = np.stack([b.x] * R).reshape(-1, 3)
+        v0 = b.velocities(R, KT_300, SEED).reshape(-1, 3)
+        spc = min(args.md_steps_per_call, 100)
+        s = pkg.System(topologies=[b.topology()], replica_topology=[0] * R, x0=x0, v0=v0,
+                       cutoff=1.0, elec=pkg.ELEC_RF, eps_rf=78.5, box=b.box, dt=0.002, gamma=1.0,
+                       kT=KT_300, seed=SEED, skin=0.15, rebuild_every=20)
+        s.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4)
+        durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
+        atoms = b.n_atoms * R
+        rate = atoms * spc * K / durs.sum()
+        bytes_per_atom_step = 100  # x,q read + write, v read + write, parameters, forces
+        out = {"metric": "biased-Langevin atom-steps/s", "value": rate, "unit": "atom-steps/s",
+               "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
+               "config": {"workload": f"{R} replicas x ({c.n_atoms}-atom chain + 24000 solvent "
+                                      f"sites), L {b.box:.3f} nm, RF, rc 1.0, skin 0.15, rebuild "
+                                      "<= 20 steps, dt 2 fs, 300 K",
+                          "atoms": atoms, "md_steps_per_call": spc},
+               "hbm": {"algorithmic_GBps": rate * bytes_per_atom_step / 1e9,
+                       "bytes_per_atom_step": bytes_per_atom_step},
+               # per call: one re-evaluation (5 kernels) + its A half step, then
+               # 5 + 1 kernels per step and the step counter
+               "gpu_launches": K * (6 + 6 * spc + 1), "clocks": clk}
+        rc, st = s.status()
+        out["status"] = int(rc)
+        s.close()
+    elif args.workload == "toy":
+        toy = synth.make_toy(256)
+        s = pkg.System(model=pkg.MODEL_TOY2D, x0=toy.start_positions(), integrator=pkg.INT_EM,
+                       dt=toy.dt, gamma=toy.gamma, kT=toy.kT, seed=toy.seed)
+        s.set_toy_bias(toy.k_R, x_ref=1.0)
+        durs, clk = timed_calls(torch, lambda st: s.step(toy.n_steps, stream=st), K, W)
+        out = {"metric": "particle-steps/s", "value": 256 * toy.n_steps * K / durs.sum(),
+               "unit": "particle-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": K,
+               "warmup": W, "config": {"workload": "256 replicas x 1e4 overdamped steps, FP64"},
+               "clocks": clk}
+        s.close()
+    elif args.workload == "hvp":
+        from paper_1705_02180_gb300.autograd import force_norm_action
+        c = synth.make_chain(35, seed=1)
+        T = 1000
+        g = np.random.default_rng(5)
+        base = np.where((np.arange(T) % 2 == 0)[:, None, None], c.x_unfolded[None], c.x_native[None])
+        X = torch.from_numpy((base + g.normal(0, 0.01, base.shape)).astype(np.float32)).cuda()
+        s = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0], x0=c.x_unfolded,
+                       dt=0.002, gamma=1.0, kT=KT_300, seed=1)
+
+        def once(_stream):
+            Xr = X.clone().requires_grad_(True)
+            A = force_norm_action(s, Xr, segment=50)
+            A.backward()
+
+        durs, clk = timed_calls(torch, once, K, W)
+        out = {"metric": "frames/s (forward + backward + double backward)", "value": T * K / durs.sum(),
+               "unit": "frames/s", "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
+               "config": {"workload": "sum_t |grad U(X_t)|^2 over 1000 frames x 560 atoms, "
+                                      "checkpointing every 50 frames"},
+               "clocks": clk}
+        s.close()
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    out.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+                "workload_name": args.workload})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "chain":
+        return run_extra(args)
     import torch
 
     import paper_1705_02180_gb300 as pkg

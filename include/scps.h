@@ -49,6 +49,7 @@ extern "C" {
 #define SCPS_REPLICA_OK 0
 #define SCPS_REPLICA_NONFINITE 1    /* non-finite position/velocity: replica frozen */
 #define SCPS_REPLICA_FORCE_RANGE 2  /* a force partial exceeded the fixed-point range */
+#define SCPS_REPLICA_LIST_OVERFLOW 4 /* periodic box: a tile had more j clusters than the list holds */
 
 /* ----------------------------------------------------------------- enums */
 enum { SCPS_MODEL_CHAIN = 0, SCPS_MODEL_TOY2D = 1 };
@@ -99,8 +100,8 @@ typedef struct {
     double k_dd;        /* distance-dependent dielectric eps_r = k_dd r (nm^-1), e.g. 40 */
     double eps_rf;      /* reaction-field dielectric, e.g. 78.5 */
     double box;         /* 0: open boundaries; > 0: cubic periodic box of this edge (nm), with
-                           minimum-image bonded terms and contacts, cell-sorted tiles and tile
-                           neighbour lists (one topology; its bonded atoms, the "chain", come
+                           minimum-image bonded terms and contacts, column-sorted tiles and
+                           cluster pair lists (one topology; its bonded atoms, the "chain", come
                            first; the remaining atoms are solvent sites). Reaction field is the
                            intended electrostatics. Needs box > 2 (cutoff + skin). */
     /* integrator */
@@ -199,8 +200,11 @@ int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* st
 int scps_set_state(scps_system* s, const double* x, const double* v, const double* zm,
                    const int64_t* step, const double* bias_T);
 
-/* Synchronises and returns SCPS_OK or the first error of the enqueued work;
- * per_replica (host, n_replicas, may be NULL) receives SCPS_REPLICA_* bits. */
+/* Synchronises and returns SCPS_OK or the first error of the enqueued work:
+ * SCPS_ERR_NONFINITE when a replica has the NONFINITE or FORCE_RANGE bit,
+ * else SCPS_ERR_LIST_OVERFLOW when one has the LIST_OVERFLOW bit. A flagged
+ * replica is frozen. per_replica (host, n_replicas, may be NULL) receives
+ * the SCPS_REPLICA_* bits. */
 int scps_get_status(scps_system* s, int32_t* per_replica);
 
 int scps_get_info(const scps_system* s, scps_info* info);

@@ -1,12 +1,16 @@
 // Solvated periodic box: rMD replicas of one chain in LJ + Coulomb solvent
-// (reaction field), cubic box, cell-sorted tiles and tile neighbour lists.
+// (reaction field), cubic box, column-sorted tiles and cluster pair lists.
 //
 // Per step (kernels in stream order):
-//   [rebuild, when due]  wrap, sort atoms by (Morton cell, atom id) into tiles
-//                        of 32, tile boxes, per i-tile list of j tiles within
-//                        r_c + skin with the periodic shift of each j tile
-//   pairs                one warp per i tile; each lane owns one atom and adds
-//                        up its own force over the listed j tiles (both
+//   [rebuild, when due]  wrap; sort atoms into ncol x ncol columns in (x, y),
+//                        by z inside a column (ties by atom id); cut every
+//                        column into tiles of 32 slots (the last one padded);
+//                        inside a tile, order by x into two halves of 16 and
+//                        each half by y, so that slots 8q..8q+7 form a compact
+//                        j cluster; tile and cluster boxes; per i tile the list
+//                        of j clusters within r_c + skin of the tile box
+//   pairs                one warp per i tile; each lane owns one slot and adds
+//                        up its own force over the listed clusters (both
 //                        directions of every pair: no atomics, a fixed order)
 //   chain                one CTA per replica: bonds, angles, z(X) of Eq.
 //                        (zrMD), the ratchet of Eq. (FrMD), the bias force
@@ -21,16 +25,9 @@ namespace scps {
 namespace {
 
 constexpr unsigned kFullB = 0xffffffffu;
-constexpr int kKeyBits = 12;            // Morton key of up to 16^3 cells
-constexpr int kNumKeys = 1 << kKeyBits;
-
-__device__ __forceinline__ int morton3(int x, int y, int z) {
-    int k = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        k |= (((x >> b) & 1) << (3 * b)) | (((y >> b) & 1) << (3 * b + 1)) | (((z >> b) & 1) << (3 * b + 2));
-    return k;
-}
+constexpr int kNumKeys = 8192;  // ncol^2 * nz <= kNumKeys
+constexpr int kMaxCols = 256;   // ncol <= 16
+constexpr int kSortThreads = 1024;
 
 __device__ __forceinline__ float wrapc(float x, float L, float invL) {
     return x - L * floorf(x * invL);
@@ -40,12 +37,28 @@ __device__ __forceinline__ float min_img(float d, float L, float invL) {
     return d - L * rintf(d * invL);
 }
 
+// number of lanes whose (key, lane) is below this lane's
+__device__ __forceinline__ int warp_rank(float key, int lane, bool member, unsigned group) {
+    int rank = 0;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+        const float kk = __shfl_sync(kFullB, key, k);
+        const bool in = (group >> k) & 1u;
+        rank += (member && in && (kk < key || (kk == key && k < lane))) ? 1 : 0;
+    }
+    return rank;
+}
+
 }  // namespace
 
-// Rebuild step 1 (one CTA per replica): decide, wrap, sort by (cell key, atom id).
-__global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __restrict__ topo,
-                                                    StateDev st, int r0, int auto_ok) {
+// Rebuild (one CTA of 1024 threads per replica): decide, wrap, sort into
+// padded column tiles, order each tile into j clusters.
+__global__ void __launch_bounds__(kSortThreads) k_box_sort(BoxDev B, const TopoDev* __restrict__ topo,
+                                                          StateDev st, int r0, int auto_ok) {
     __shared__ int cnt[kNumKeys];
+    __shared__ int col_first[kMaxCols + 1];  // compact position of each column's first atom
+    __shared__ int col_tile[kMaxCols + 1];   // first tile of each column
+    __shared__ int wtot[32];
     __shared__ int decide;
     const int r = blockIdx.x + r0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -57,16 +70,20 @@ __global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __re
     __syncthreads();
     if (!decide) return;
     const TopoDev tp = *topo;
-    float4* pos = B.pos + (size_t)r * B.np;
-    float4* vel = B.vel + (size_t)r * B.np;
-    int* id = B.id + (size_t)r * B.np;
-    int* key = B.key + (size_t)r * B.np;
+    const size_t base = (size_t)r * B.np;
+    float4* pos = B.pos + base;
+    float4* vel = B.vel + base;
+    int* id = B.id + base;
+    int* key = B.key + base;
     int* slot_of = B.slot_of + (size_t)r * B.n_atoms;
-    float4* pos2 = B.pos2 + (size_t)r * B.np;
-    float4* vel2 = B.vel2 + (size_t)r * B.np;
+    float4* pos2 = B.pos2 + base;
+    float4* vel2 = B.vel2 + base;
+    int* id2 = B.id2 + base;
+    const int ncol = B.ncol, nz = B.nz, ncols = ncol * ncol;
     for (int k = tid; k < kNumKeys; k += blockDim.x) cnt[k] = 0;
+    for (int s = tid; s < B.np; s += blockDim.x) id2[s] = -1;
     __syncthreads();
-    const float cs = (float)B.nc * B.invL;
+    const float cs = (float)ncol * B.invL, zs = (float)nz * B.invL;
     for (int s = tid; s < B.np; s += blockDim.x) {
         const int a = id[s];
         if (a < 0) continue;
@@ -75,20 +92,21 @@ __global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __re
         p.y = wrapc(p.y, B.L, B.invL);
         p.z = wrapc(p.z, B.L, B.invL);
         pos[s] = p;
-        const int qx = min((int)(p.x * cs), B.nc - 1), qy = min((int)(p.y * cs), B.nc - 1),
-                  qz = min((int)(p.z * cs), B.nc - 1);
-        const int k = morton3(qx, qy, qz);
+        const int qx = min((int)(p.x * cs), ncol - 1), qy = min((int)(p.y * cs), ncol - 1),
+                  qz = min((int)(p.z * zs), nz - 1);
+        const int k = (qx * ncol + qy) * nz + qz;
         key[s] = k;
         atomicAdd(&cnt[k], 1);
     }
     __syncthreads();
-    // exclusive scan of the key counts (4 keys per thread, 1024 threads)
+    // exclusive scan of the key counts (kNumKeys / 1024 keys per thread)
     {
-        int loc[4], sum = 0;
-        const int base = tid * 4;
+        constexpr int kPer = kNumKeys / kSortThreads;
+        int loc[kPer], sum = 0;
+        const int k0 = tid * kPer;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            loc[q] = (base + q < kNumKeys) ? cnt[base + q] : 0;
+        for (int q = 0; q < kPer; ++q) {
+            loc[q] = cnt[k0 + q];
             sum += loc[q];
         }
         int x = sum;
@@ -97,7 +115,6 @@ __global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __re
             const int y = __shfl_up_sync(kFullB, x, o);
             if (lane >= o) x += y;
         }
-        __shared__ int wtot[32];
         if (lane == 31) wtot[warp] = x;
         __syncthreads();
         if (warp == 0) {
@@ -113,11 +130,22 @@ __global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __re
         int run = (warp > 0 ? wtot[warp - 1] : 0) + x - sum;
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (base + q < kNumKeys) {
-                cnt[base + q] = run;  // becomes the running cursor of key base+q
-                run += loc[q];
-            }
+        for (int q = 0; q < kPer; ++q) {
+            cnt[k0 + q] = run;  // becomes the running cursor of key k0+q
+            run += loc[q];
+        }
+    }
+    __syncthreads();
+    // columns: first compact position and first tile (each column starts a tile)
+    for (int c = tid; c <= ncols; c += blockDim.x) col_first[c] = c < ncols ? cnt[c * nz] : B.n_atoms;
+    __syncthreads();
+    if (tid == 0) {
+        int t = 0;
+        for (int c = 0; c < ncols; ++c) {
+            col_tile[c] = t;
+            t += (col_first[c + 1] - col_first[c] + 31) >> 5;
+        }
+        col_tile[ncols] = t;  // <= nt by the capacity ceil(n/32) + ncol^2
     }
     __syncthreads();
     // scatter in atom-id order, one warp at a time: ties (same key) keep id order
@@ -130,39 +158,50 @@ __global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __re
             if (warp == w) {
                 const unsigned peers = __match_any_sync(kFullB, k);
                 const int rank = __popc(peers & ((1u << lane) - 1u));
-                int dst = 0;
-                if (valid) dst = cnt[k] + rank;
+                int p = 0;
+                if (valid) p = cnt[k] + rank;
                 __syncwarp();
                 if (valid && rank == 0) cnt[k] += __popc(peers);
                 if (valid) {
+                    const int c = k / nz;
+                    const int dst = col_tile[c] * 32 + (p - col_first[c]);
                     pos2[dst] = pos[s];
                     vel2[dst] = vel[s];
-                    slot_of[a] = dst;
+                    id2[dst] = a;
                 }
             }
             __syncthreads();
         }
     }
     __syncthreads();
-    // copy back in tile order; padding slots are far away, without charge or LJ
-    for (int s = tid; s < B.np; s += blockDim.x) {
-        if (s < B.n_atoms) {
-            pos[s] = pos2[s];
-            vel[s] = vel2[s];
-            B.pos_ref[(size_t)r * B.np + s] = pos2[s];
+    // inside each tile: two halves of 16 by x, each ordered by y (padding last)
+    for (int t = warp; t < B.nt; t += nw) {
+        const int s0 = t * 32 + lane;
+        const int a = id2[s0];
+        const bool valid = a >= 0;
+        const float4 p = pos2[s0];
+        const float4 v = vel2[s0];
+        const float kx = valid ? p.x : 3.0e38f, ky = valid ? p.y : 3.0e38f;
+        const int rx = warp_rank(kx, lane, true, kFullB);
+        const unsigned upper = __ballot_sync(kFullB, rx >= 16);
+        const bool hi = rx >= 16;
+        const int ry = warp_rank(ky, lane, true, hi ? upper : ~upper);
+        const int s = t * 32 + (hi ? 16 : 0) + ry;
+        if (valid) {
+            pos[s] = p;
+            vel[s] = v;
+            id[s] = a;
+            B.pos_ref[base + s] = p;
+            B.par[base + s] = tp.lj[a];
+            slot_of[a] = s;
         } else {
             pos[s] = make_float4(1.0e5f * (float)(s + 1), 0.f, 0.f, 0.f);
             vel[s] = make_float4(0.f, 0.f, 0.f, 0.f);
             id[s] = -1;
+            B.pos_ref[base + s] = pos[s];
+            B.par[base + s] = make_float2(0.f, 0.f);
         }
     }
-    __syncthreads();
-    for (int a = tid; a < B.n_atoms; a += blockDim.x) {
-        const int s = slot_of[a];
-        id[s] = a;
-        B.par[(size_t)r * B.np + s] = tp.lj[a];
-    }
-    for (int s = B.n_atoms + tid; s < B.np; s += blockDim.x) B.par[(size_t)r * B.np + s] = make_float2(0.f, 0.f);
     if (tid == 0) {
         B.need[r] = 1;  // the tile and list kernels of this step run
         B.since[r] = 0;
@@ -170,7 +209,7 @@ __global__ void __launch_bounds__(1024) k_box_sort(BoxDev B, const TopoDev* __re
     }
 }
 
-// Rebuild step 2: tile boxes (one warp per tile).
+// Rebuild step 2: tile boxes and j-cluster boxes (one warp per tile).
 __global__ void k_box_tiles(BoxDev B, int r0) {
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
@@ -183,13 +222,18 @@ __global__ void k_box_tiles(BoxDev B, int r0) {
     float lx = valid ? p.x : 3.0e38f, ly = valid ? p.y : 3.0e38f, lz = valid ? p.z : 3.0e38f;
     float hx = valid ? p.x : -3.0e38f, hy = valid ? p.y : -3.0e38f, hz = valid ? p.z : -3.0e38f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 1; o < 32; o <<= 1) {
         lx = fminf(lx, __shfl_xor_sync(kFullB, lx, o));
         ly = fminf(ly, __shfl_xor_sync(kFullB, ly, o));
         lz = fminf(lz, __shfl_xor_sync(kFullB, lz, o));
         hx = fmaxf(hx, __shfl_xor_sync(kFullB, hx, o));
         hy = fmaxf(hy, __shfl_xor_sync(kFullB, hy, o));
         hz = fmaxf(hz, __shfl_xor_sync(kFullB, hz, o));
+        if (o == 4 && (lane & 7) == 0) {  // the box of the 8-slot cluster of this lane
+            const size_t c = (size_t)r * 4 * B.nt + 4 * t + (lane >> 3);
+            B.clo[c] = make_float4(lx, ly, lz, 0.f);
+            B.chi[c] = make_float4(hx, hy, hz, 0.f);
+        }
     }
     if (lane == 0) {
         B.tlo[(size_t)r * B.nt + t] = make_float4(lx, ly, lz, 0.f);
@@ -197,7 +241,7 @@ __global__ void k_box_tiles(BoxDev B, int r0) {
     }
 }
 
-// Rebuild step 3: neighbour tiles of every tile (one warp per i tile), in j order.
+// Rebuild step 3: j clusters near every i tile (one warp per i tile), in cluster order.
 __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
@@ -205,48 +249,47 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     if (t >= B.nt) return;
     const int lane = threadIdx.x & 31;
     const float4 al = B.tlo[(size_t)r * B.nt + t], ah = B.thi[(size_t)r * B.nt + t];
-    const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
     uint32_t* out = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
     int count = 0;
-    bool overflow = false;
-    for (int j0 = 0; j0 < B.nt; j0 += 32) {
-        const int j = j0 + lane;
-        bool hit = false;
-        uint32_t code = 0;
-        if (j < B.nt) {
-            const float4 bl = B.tlo[(size_t)r * B.nt + j], bh = B.thi[(size_t)r * B.nt + j];
-            if (bl.x <= bh.x) {  // tile holds atoms
-                // lower bound of any periodic-image distance between the two boxes:
-                // |minimum-image centre distance| - half widths, per dimension
-                const float gx = fmaxf(0.f, fabsf(min_img(0.5f * (bl.x + bh.x) - cx, B.L, B.invL)) -
-                                                0.5f * ((bh.x - bl.x) + (ah.x - al.x)));
-                const float gy = fmaxf(0.f, fabsf(min_img(0.5f * (bl.y + bh.y) - cy, B.L, B.invL)) -
-                                                0.5f * ((bh.y - bl.y) + (ah.y - al.y)));
-                const float gz = fmaxf(0.f, fabsf(min_img(0.5f * (bl.z + bh.z) - cz, B.L, B.invL)) -
-                                                0.5f * ((bh.z - bl.z) + (ah.z - al.z)));
-                hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
-                code = (uint32_t)j;
+    if (al.x <= ah.x) {  // the i tile holds atoms
+        const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
+        const int ncl = 4 * B.nt;
+        for (int j0 = 0; j0 < ncl; j0 += 32) {
+            const int j = j0 + lane;
+            bool hit = false;
+            if (j < ncl) {
+                const float4 bl = B.clo[(size_t)r * ncl + j], bh = B.chi[(size_t)r * ncl + j];
+                if (bl.x <= bh.x) {  // the cluster holds atoms
+                    // lower bound of any periodic-image distance between the two boxes:
+                    // |minimum-image centre distance| - half widths, per dimension
+                    const float gx = fmaxf(0.f, fabsf(min_img(0.5f * (bl.x + bh.x) - cx, B.L, B.invL)) -
+                                                    0.5f * ((bh.x - bl.x) + (ah.x - al.x)));
+                    const float gy = fmaxf(0.f, fabsf(min_img(0.5f * (bl.y + bh.y) - cy, B.L, B.invL)) -
+                                                    0.5f * ((bh.y - bl.y) + (ah.y - al.y)));
+                    const float gz = fmaxf(0.f, fabsf(min_img(0.5f * (bl.z + bh.z) - cz, B.L, B.invL)) -
+                                                    0.5f * ((bh.z - bl.z) + (ah.z - al.z)));
+                    hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
+                }
             }
+            const unsigned m = __ballot_sync(kFullB, hit);
+            if (hit) {
+                const int pos = count + __popc(m & ((1u << lane) - 1u));
+                if (pos < B.max_nbr) out[pos] = (uint32_t)j;
+            }
+            count += __popc(m);
         }
-        const unsigned m = __ballot_sync(kFullB, hit);
-        if (hit) {
-            const int pos = count + __popc(m & ((1u << lane) - 1u));
-            if (pos < B.max_nbr)
-                out[pos] = code;
-        }
-        count += __popc(m);
     }
-    if (count > B.max_nbr) {
-        overflow = true;
-        count = B.max_nbr;
-    }
+    const bool overflow = count > B.max_nbr;
+    if (overflow) count = B.max_nbr;
     if (lane == 0) {
         B.nnbr[(size_t)r * B.nt + t] = count;
-        if (overflow) atomicOr(&st.status[r], 4);
+        if (overflow) atomicOr(&st.status[r], SCPS_FLAG_LIST_OVERFLOW);
     }
 }
 
-// Non-bonded forces: one warp per i tile; lane l owns slot 32 t + l.
+// Non-bonded forces: one warp per i tile; lane l owns slot 32 t + l. The j
+// slots come four listed clusters at a time (lane l loads slot l & 7 of
+// cluster l >> 3 of the group).
 template <int ELEC, bool ENERGY>
 __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __restrict__ topo,
                                                    RunParams P, int r0) {
@@ -266,12 +309,18 @@ __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __re
     const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
     const int cnt = B.nnbr[(size_t)r * B.nt + t];
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-    for (int q = 0; q < cnt; ++q) {
-        const int jt = (int)lst[q];
-        const int sjl = jt * 32 + lane;
-        sj[w][lane] = B.pos[base + sjl];
-        sp[w][lane] = B.par[base + sjl];
-        sid[w][lane] = B.id[base + sjl];
+    for (int q = 0; q < cnt; q += 4) {
+        const int qe = q + (lane >> 3);
+        if (qe < cnt) {
+            const int sjl = (int)lst[qe] * 8 + (lane & 7);
+            sj[w][lane] = B.pos[base + sjl];
+            sp[w][lane] = B.par[base + sjl];
+            sid[w][lane] = B.id[base + sjl];
+        } else {
+            sj[w][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sp[w][lane] = make_float2(0.f, 0.f);
+            sid[w][lane] = -1;
+        }
         __syncwarp();
 #pragma unroll 4
         for (int k = 0; k < 32; ++k) {

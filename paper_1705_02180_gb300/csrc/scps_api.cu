@@ -425,13 +425,17 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BoxDev& B = s->box;
         B.n_atoms = t.n_atoms;
         B.n_chain = std::max(nch, 1);
-        B.np = ((t.n_atoms + kTile - 1) / kTile) * kTile;
-        B.nt = B.np / kTile;
-        B.max_nbr = 256;
+        // columns about as wide as a cube holding 32 atoms; every column starts
+        // a tile, so ncol^2 tiles more than ceil(n / 32) always suffice
+        const double cube = std::cbrt(32.0 * d->box * d->box * d->box / t.n_atoms);
+        B.ncol = std::max(1, std::min(16, (int)std::lround(d->box / cube)));
+        B.nz = 8192 / (B.ncol * B.ncol);
+        B.nt = (t.n_atoms + kTile - 1) / kTile + B.ncol * B.ncol;
+        B.np = B.nt * kTile;
+        B.max_nbr = std::min(4 * B.nt, 1024);
         B.rebuild_every = d->rebuild_every > 0 ? d->rebuild_every : 20;
         B.L = (float)d->box;
         B.invL = (float)(1.0 / d->box);
-        B.nc = std::max(1, std::min(16, (int)(d->box / 0.4)));
         const double skin = d->skin > 0.0 ? d->skin : 0.15;
         B.rlist2 = (float)((d->cutoff + skin) * (d->cutoff + skin));
         B.skin2_quarter = (float)(0.25 * skin * skin);
@@ -446,6 +450,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.vel, np);
         BALLOC(B.par, np);
         BALLOC(B.id, np);
+        BALLOC(B.id2, np);
         BALLOC(B.fnb, np);
         BALLOC(B.pos2, np);
         BALLOC(B.vel2, np);
@@ -454,6 +459,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.slot_of, (size_t)Rs * B.n_atoms);
         BALLOC(B.tlo, (size_t)Rs * B.nt);
         BALLOC(B.thi, (size_t)Rs * B.nt);
+        BALLOC(B.clo, (size_t)Rs * 4 * B.nt);
+        BALLOC(B.chi, (size_t)Rs * 4 * B.nt);
         BALLOC(B.nbr, (size_t)Rs * B.nt * B.max_nbr);
         BALLOC(B.nnbr, (size_t)Rs * B.nt);
         BALLOC(B.need, Rs);
@@ -912,9 +919,11 @@ int scps_get_status(scps_system* s, int32_t* per_replica) {
     int rc = SCPS_OK;
     for (int r = 0; r < R; ++r) {
         if (per_replica) per_replica[r] = st[r];
-        if (st[r] != SCPS_REPLICA_OK) rc = SCPS_ERR_NONFINITE;
+        if (st[r] & (SCPS_REPLICA_NONFINITE | SCPS_REPLICA_FORCE_RANGE)) rc = SCPS_ERR_NONFINITE;
+        else if (st[r] != SCPS_REPLICA_OK && rc == SCPS_OK) rc = SCPS_ERR_LIST_OVERFLOW;
     }
-    if (rc) fail(rc, "a replica produced non-finite or out-of-range values and was frozen");
+    if (rc == SCPS_ERR_NONFINITE) fail(rc, "a replica produced non-finite or out-of-range values and was frozen");
+    else if (rc) fail(rc, "a neighbour list overflowed and the replica was frozen");
     return rc;
 }
 

@@ -15,6 +15,7 @@ constexpr int kExclWindow = 32;      // excluded pairs must satisfy |i - j| < 32
 // replica status bits (the values of SCPS_REPLICA_* in scps.h)
 #define SCPS_FLAG_NONFINITE 1
 #define SCPS_FLAG_FORCE_RANGE 2
+#define SCPS_FLAG_LIST_OVERFLOW 4
 
 // Per-topology tables in device memory (shared by all replicas of a topology).
 struct TopoDev {
@@ -84,12 +85,14 @@ struct RunParams {
 
 // Periodic-box state of all replicas (slot arrays are [replica][np], in tile order).
 struct BoxDev {
-    int n_atoms, n_chain, np, nt, max_nbr, rebuild_every, nc;
+    int n_atoms, n_chain, np, nt, max_nbr, rebuild_every;
+    int ncol, nz;     // ncol x ncol columns in (x, y), nz bins in z per column
     float L, invL, rlist2, skin2_quarter;
     float4* pos;      // (x, y, z, qs)
     float4* vel;
     float2* par;      // (sigma/2, sqrt(24 eps))
     int* id;          // atom id of each slot, -1 for padding
+    int* id2;         // sort buffer of id
     float4* fnb;      // non-bonded force (w: energy share)
     float4* pos2;     // sort buffers
     float4* vel2;
@@ -98,7 +101,9 @@ struct BoxDev {
     float4* pos_ref;  // positions at the last rebuild
     float4* tlo;      // [replica][nt] tile boxes
     float4* thi;
-    uint32_t* nbr;    // [replica][nt][max_nbr]: j tile | shift code << 20
+    float4* clo;      // [replica][4 nt] boxes of the 8-slot j clusters
+    float4* chi;
+    uint32_t* nbr;    // [replica][nt][max_nbr]: j cluster index
     int* nnbr;        // [replica][nt]
     int* need;        // [replica] rebuild flag
     int* since;       // [replica] evaluations since the last rebuild
