@@ -31,14 +31,16 @@ constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per 
 struct Shared {
     float4* xq;         // (x, y, z, qs)
     float4* v;          // velocities
-    float4* fb;         // bias force per atom (computed by the atom's thread)
+    float4* xi;         // Gaussian numbers of the next O half step, per atom
     float2* lj;         // (sigma/2, sqrt(24 eps))
     long long* Fp[2];   // 3 x nta force partials of this CTA, by parity of the evaluated step
+    long long* Gp[2];   // 3 x nta partials of sum_p (C - C0) C'(u) (x_p - x_i) over the native
+                        // contacts (i, p) this CTA evaluated, by parity (the bias gradient
+                        // without its ratchet factor, which is known only once z is complete)
     float4* blo;        // tile bounding boxes, then half-tile boxes (2 per tile)
     float4* bhi;
     uint32_t* tpl;      // all tile pairs (I << 16 | J), I <= J
     uint32_t* items;    // active half-tile pairs: I | J << 11 | h << 22
-    float* hcoef[2];    // per native contact: (C - C0) dC/du, by parity of the evaluated step
     int* flag;          // force-range flag of the current evaluation
     int nta, nt;
 };
@@ -64,17 +66,17 @@ __device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int nc
     s.nt = nta / kTile;
     s.xq = (float4*)p; p += sizeof(float4) * nta;
     s.v = (float4*)p; p += sizeof(float4) * nta;
-    s.fb = (float4*)p; p += sizeof(float4) * nta;
+    s.xi = (float4*)p; p += sizeof(float4) * nta;
     s.blo = (float4*)p; p += sizeof(float4) * 3 * s.nt;
     s.bhi = (float4*)p; p += sizeof(float4) * 3 * s.nt;
     s.Fp[0] = (long long*)p; p += sizeof(long long) * 3 * nta;
     s.Fp[1] = (long long*)p; p += sizeof(long long) * 3 * nta;
+    s.Gp[0] = (long long*)p; p += sizeof(long long) * 3 * nta;
+    s.Gp[1] = (long long*)p; p += sizeof(long long) * 3 * nta;
     s.lj = (float2*)p; p += sizeof(float2) * nta;
     const int ntp4 = (ntp_max + 3) & ~3;
     s.tpl = (uint32_t*)p; p += sizeof(uint32_t) * ntp4;
-    s.items = (uint32_t*)p; p += sizeof(uint32_t) * 2 * ntp4;
-    s.hcoef[0] = (float*)p; p += sizeof(float) * ncon_max;
-    s.hcoef[1] = (float*)p;
+    s.items = (uint32_t*)p;
     s.flag = nullptr;
     return s;
 }
@@ -222,11 +224,11 @@ __device__ __forceinline__ int cta_rank() {
     return (int)cg::this_cluster().block_rank();
 }
 
-// One native contact: (C - C0)^2 in float-float, returned as a 2^-40 fixed-point
-// value; (C - C0) dC/du is stored for the bias gradient in every CTA of the cluster.
-template <int CL>
-__device__ __forceinline__ long long contact_term(float* own_hcoef, float* peer_hcoef,
-                                                  const Shared& sm, const TopoDev& tp,
+// One native contact (i, p): (C - C0)^2 in float-float, returned as a 2^-40
+// fixed-point value. h (x_p - x_i) with h = (C - C0) dC/du goes to G_i and its
+// negative to G_p, so that grad_i (C - C0)^2 = -4 h (x_p - x_i) / r0^2 is
+// -4 G_i / r0^2 summed over the atom's contacts (Eq. zrMD, Eq. Cij).
+__device__ __forceinline__ long long contact_term(const Shared& sm, long long* G, const TopoDev& tp,
                                                   const RunParams& P, int c) {
     const int2 ij = tp.con_ij[c];
     const float4 a = sm.xq[ij.x], b = sm.xq[ij.y];
@@ -236,9 +238,28 @@ __device__ __forceinline__ long long contact_term(float* own_hcoef, float* peer_
     const float2 c0 = tp.con_C0[c];
     const ff d = ff_add(C, ff{-c0.x, -c0.y});
     const float h = (d.hi + d.lo) * contact_dC_du(u.hi);
-    own_hcoef[c] = h;
-    if (CL == 2) peer_hcoef[c] = h;
+    const long long gx = f2fix(h * (b.x - a.x)), gy = f2fix(h * (b.y - a.y)),
+                    gz = f2fix(h * (b.z - a.z));
+    const int nta = sm.nta;
+    atomicAdd((unsigned long long*)&G[ij.x], (unsigned long long)gx);
+    atomicAdd((unsigned long long*)&G[nta + ij.x], (unsigned long long)gy);
+    atomicAdd((unsigned long long*)&G[2 * nta + ij.x], (unsigned long long)gz);
+    atomicAdd((unsigned long long*)&G[ij.y], (unsigned long long)(-gx));
+    atomicAdd((unsigned long long*)&G[nta + ij.y], (unsigned long long)(-gy));
+    atomicAdd((unsigned long long*)&G[2 * nta + ij.y], (unsigned long long)(-gz));
     return ff2fix40(ff_sqr(d));
+}
+
+// Gaussian numbers of the O half step of global step `step` for atoms
+// 32 q .. 32 q + 31 (Philox4x32-10, counter (atom, replica id, step, 0)).
+__device__ __forceinline__ void noise_chunk(const Shared& sm, const RunParams& P, uint32_t rep_id,
+                                            long long step, int q, int n, int lane) {
+    const int i = q * kTile + lane;
+    if (i < n) {
+        const uint4 rb = philox4x32_10(make_uint4((uint32_t)i, rep_id, (uint32_t)step, 0u), P.key0,
+                                       P.key1);
+        sm.xi[i] = normals4_f32(rb);
+    }
 }
 
 // Box of 32 positions of one warp (invalid lanes hold +inf/-inf sentinels):
@@ -341,18 +362,22 @@ __device__ void build_items(const Shared& sm, Scalars& sc, int ntp, float rc2) {
 
 // Force evaluation of the configuration in shared memory (boxes current) for
 // the evaluated step of parity b. Work items come from the queue of the
-// cluster; this CTA's share goes to Fp[b]; the ratchet decision is taken by
-// every CTA from the same fixed-point sums; with the bias engaged, every CTA
-// fills fb for all atoms. On return the CTA is synchronised.
+// cluster; this CTA's share goes to Fp[b] and Gp[b]; the ratchet decision is
+// taken by every CTA from the same fixed-point sums. With noise_step >= 0 the
+// CTA also draws the Gaussian numbers of that step's O half step for all atoms
+// (each CTA of a cluster integrates every atom). On return the CTA is
+// synchronised.
 template <int ELEC, bool ENERGY, int CL>
 __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
-                         bool do_ratchet) {
+                         bool do_ratchet, uint32_t rep_id, long long noise_step) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int nt = tp.n_tiles, ntp = nt * (nt + 1) / 2;
-    const int rank = cta_rank<CL>();
     long long* F = sm.Fp[b];
+    long long* G = sm.Gp[b];
     sm.flag = &sc.flag[b];
     build_items(sm, sc, ntp, P.pc.rc2);
+    if (noise_step >= 0)
+        for (int q = warp; q < nt; q += nw) noise_chunk(sm, P, rep_id, noise_step, q, tp.n_atoms, lane);
     // work queue: half tile pairs, then contact, bond and angle chunks
     const int n_half = sc.n_items;
     const int ncon = P.bias == 1 ? tp.n_contacts : 0;
@@ -360,8 +385,6 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
     const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
     int* counter = rank_ptr<CL>(&sc.work_next[b], 0);
-    float* own_hcoef = sm.hcoef[b];
-    float* peer_hcoef = CL == 2 ? rank_ptr<CL>(sm.hcoef[b], rank ^ 1) : nullptr;
     long long e = 0, zacc = 0;  // fixed point: sums independent of the work order
     for (;;) {
         int k = 0;
@@ -379,7 +402,7 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             if (ENERGY) e += f2fix(ep);
         } else if (k < e_con) {
             const int c = (k - n_half) * kChunk + lane;
-            if (c < ncon) zacc += contact_term<CL>(own_hcoef, peer_hcoef, sm, tp, P, c);
+            if (c < ncon) zacc += contact_term(sm, G, tp, P, c);
         } else if (k < e_bond) {
             const int q = (k - e_con) * kChunk + lane;
             if (q < tp.n_bonds) {
@@ -434,25 +457,6 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         }
     }
     __syncthreads();
-    // bias force factor * grad z per atom, summed over the atom's contacts in a fixed
-    // order: grad_i (C - C0)^2 = -4 (C - C0) C'(u) (x_p - x_i) / r0^2 for partner p
-    if (sc.bias_on) {
-        const float k = -(float)sc.factor * 4.0f * P.inv_r0sq;
-        for (int i = tid; i < tp.n_atoms; i += blockDim.x) {
-            const float4 xi = sm.xq[i];
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (int q = tp.con_off[i]; q < tp.con_off[i + 1]; ++q) {
-                const int2 cp = tp.con_nbr[q];
-                const float4 xp = sm.xq[cp.y];
-                const float hc = own_hcoef[cp.x];
-                fx = fmaf(hc, xp.x - xi.x, fx);
-                fy = fmaf(hc, xp.y - xi.y, fy);
-                fz = fmaf(hc, xp.z - xi.z, fz);
-            }
-            sm.fb[i] = make_float4(k * fx, k * fy, k * fz, 0.f);
-        }
-        __syncthreads();
-    }
 }
 
 // Sum of this CTA's and the peer's fixed-point partials at index idx.
@@ -503,11 +507,12 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             sm.lj[i] = make_float2(0.f, 0.f);
             sm.v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        sm.fb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int i = tid; i < nta3; i += blockDim.x) {
         sm.Fp[0][i] = 0;
         sm.Fp[1][i] = 0;
+        sm.Gp[0][i] = 0;
+        sm.Gp[1][i] = 0;
     }
     tile_pair_table(sm, nt);
     if (tid == 0) {
@@ -529,9 +534,12 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
     const int peer = rank ^ 1;
     const long long* pFp[2] = {CL == 2 ? rank_ptr<CL>(sm.Fp[0], peer) : nullptr,
                                CL == 2 ? rank_ptr<CL>(sm.Fp[1], peer) : nullptr};
+    const long long* pGp[2] = {CL == 2 ? rank_ptr<CL>(sm.Gp[0], peer) : nullptr,
+                               CL == 2 ? rank_ptr<CL>(sm.Gp[1], peer) : nullptr};
     const float hdt = P.half_dt;
     if (sc.status == 0 && P.n_steps > 0) {
-        evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true);
+        // the O half step that follows an evaluation uses the noise of the same step index
+        evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true, rep.rep_id, step);
         for (long long s = 0; s <= P.n_steps; ++s) {
             // B of the step just evaluated (s > 0), then A of the next one (s < n_steps)
             const bool do_b = s > 0, do_a = s < P.n_steps;
@@ -540,6 +548,8 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             const bool save = do_b && P.save_interval > 0 && (step % P.save_interval) == 0;
             const long long slot = sc.n_saved % P.max_frames;
             const long long* own = sm.Fp[b];
+            const long long* gown = sm.Gp[b];
+            const float kb = -(float)sc.factor * 4.0f * P.inv_r0sq;  // F_bias = kb G
             float tb = 0.f;
             for (int base = 0; base < nta; base += blockDim.x) {
                 const int i = base + tid;
@@ -550,11 +560,13 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                     float fx = sum_fix<CL>(own, pFp[b], i), fy = sum_fix<CL>(own, pFp[b], nta + i),
                           fz = sum_fix<CL>(own, pFp[b], 2 * nta + i);
                     if (bias) {
-                        const float4 f = sm.fb[i];
-                        if (do_b) tb += (f.x * f.x + f.y * f.y + f.z * f.z) * im;
-                        fx += f.x;
-                        fy += f.y;
-                        fz += f.z;
+                        const float bx = kb * sum_fix<CL>(gown, pGp[b], i),
+                                    by = kb * sum_fix<CL>(gown, pGp[b], nta + i),
+                                    bz = kb * sum_fix<CL>(gown, pGp[b], 2 * nta + i);
+                        if (do_b) tb += (bx * bx + by * by + bz * bz) * im;
+                        fx += bx;
+                        fy += by;
+                        fz += bz;
                     }
                     float4 v = sm.v[i];
                     x = sm.xq[i];
@@ -576,9 +588,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                         x.x = fmaf(hdt, v.x, x.x);
                         x.y = fmaf(hdt, v.y, x.y);
                         x.z = fmaf(hdt, v.z, x.z);
-                        const uint4 rb = philox4x32_10(
-                            make_uint4((uint32_t)i, rep.rep_id, (uint32_t)step, 0u), P.key0, P.key1);
-                        const float4 xi = normals4_f32(rb);
+                        const float4 xi = sm.xi[i];  // drawn during the evaluation
                         const float sd = tp.noise_sd[i];
                         v.x = fmaf(P.c1, v.x, sd * xi.x);
                         v.y = fmaf(P.c1, v.y, sd * xi.y);
@@ -601,7 +611,10 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             }
             // this CTA's partials of the next evaluation start from zero
             if (do_a)
-                for (int i = tid; i < nta3; i += blockDim.x) sm.Fp[nb][i] = 0;
+                for (int i = tid; i < nta3; i += blockDim.x) {
+                    sm.Fp[nb][i] = 0;
+                    sm.Gp[nb][i] = 0;
+                }
             if (bias && do_b) {
                 tb = warp_sum_f(tb);
                 if (lane == 0) sc.red_t[warp] = tb;
@@ -631,9 +644,9 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             ++step;
             const bool save_next = P.save_interval > 0 && (step % P.save_interval) == 0;
             if (save_next)
-                evaluate<ELEC, true, CL>(sm, sc, tp, P, nb, true);
+                evaluate<ELEC, true, CL>(sm, sc, tp, P, nb, true, rep.rep_id, step);
             else
-                evaluate<ELEC, false, CL>(sm, sc, tp, P, nb, true);
+                evaluate<ELEC, false, CL>(sm, sc, tp, P, nb, true, rep.rep_id, step);
             if (sc.status != 0) break;  // force out of range: frozen before the update
         }
     }
@@ -679,7 +692,10 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
             sm.lj[i] = make_float2(0.f, 0.f);
         }
     }
-    for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) sm.Fp[0][i] = 0;
+    for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) {
+        sm.Fp[0][i] = 0;
+        sm.Gp[0][i] = 0;
+    }
     tile_pair_table(sm, nt);
     if (threadIdx.x == 0) {
         sc.zm = 0.0;
@@ -691,7 +707,7 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
     __syncthreads();
     all_boxes(sm, n);
     __syncthreads();
-    evaluate<ELEC, true, 1>(sm, sc, tp, P, 0, false);
+    evaluate<ELEC, true, 1>(sm, sc, tp, P, 0, false, 0u, -1);
     if (F) {
         float* ff_out = F + f * n * 3;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -710,8 +726,9 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
 size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max) {
     const int nt = nta / kTile;
     const size_t ntp4 = (size_t)((ntp_max + 3) & ~3);
-    return sizeof(float4) * nta * 3 + sizeof(float4) * 6 * nt + sizeof(long long) * 6 * nta +
-           sizeof(float2) * nta + sizeof(uint32_t) * 3 * ntp4 + sizeof(float) * 2 * ncon_max;
+    (void)ncon_max;  // contacts live in the topology (global memory)
+    return sizeof(float4) * nta * 3 + sizeof(float4) * 6 * nt + sizeof(long long) * 12 * nta +
+           sizeof(float2) * nta + sizeof(uint32_t) * 3 * ntp4;
 }
 
 template <int ELEC, int CL>
