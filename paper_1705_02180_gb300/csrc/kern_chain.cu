@@ -2,11 +2,13 @@
 //
 // One thread-block cluster of CL CTAs (CL = 1 or 2) owns one replica for a
 // whole launch of n_steps steps. Positions, velocities and int64 fixed-point
-// force partials live in shared memory; the CTAs of a cluster pull force work
-// from one queue (a counter in the shared memory of CTA 0) and read each
-// other's partials through distributed shared memory. Every step evaluates
+// force partials live in shared memory; the CTAs of a cluster split the force
+// work list between them (the warps of each CTA pull their items from a counter
+// in their own shared memory) and read each other's partials through
+// distributed shared memory. Every step evaluates
 //   bonded terms + non-bonded pairs (32 x 16 half tile pairs, skipped when
-//   their bounding boxes are farther apart than the cutoff)       -grad U
+//   their bounding boxes are farther apart than the cutoff; a tile with
+//   itself in one 16-step round)                                   -grad U
 //   z(X) of Eq. (zrMD) from C_ij of Eq. (Cij) in float-float     collective coordinate
 //   ratchet of Eq. (FrMD) in FP64 (z < z_m: z_m = z, no bias)   bias force
 //   BAOAB update with Philox4x32-10 noise (Eq. Lang)
@@ -30,8 +32,8 @@ constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per 
 
 struct Shared {
     float4* xq;         // (x, y, z, qs)
-    float4* v;          // velocities
-    float4* xi;         // Gaussian numbers of the next O half step, per atom
+    float4* v;          // velocities (w: 1/m)
+    float4* xi;         // noise of the next O half step per atom (sd times Gaussian numbers)
     float2* lj;         // (sigma/2, sqrt(24 eps))
     long long* Fp[2];   // 3 x nta force partials of this CTA, by parity of the evaluated step
     long long* Gp[2];   // 3 x nta partials of sum_p (C - C0) C'(u) (x_p - x_i) over the native
@@ -40,18 +42,15 @@ struct Shared {
     float4* blo;        // tile bounding boxes, then half-tile boxes (2 per tile)
     float4* bhi;
     uint32_t* tpl;      // all tile pairs (I << 16 | J), I <= J
-    uint32_t* items;    // active half-tile pairs: I | J << 11 | h << 22
     int* flag;          // force-range flag of the current evaluation
     int nta, nt;
 };
 
 struct Scalars {
-    int n_items;
-    int work_next[2];   // work counters by parity (the cluster uses the one of CTA 0)
+    int work_next[2];   // this CTA's work counter, by parity of the evaluated step
     int status;         // replica status (identical in every CTA of a cluster)
     int bias_on;
     int flag[2];        // force-range bits raised during the evaluation of a given parity
-    int scan[33];
     long long n_saved;
     double zm, z, factor, epot, T;
     long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity
@@ -76,7 +75,6 @@ __device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int nc
     s.lj = (float2*)p; p += sizeof(float2) * nta;
     const int ntp4 = (ntp_max + 3) & ~3;
     s.tpl = (uint32_t*)p; p += sizeof(uint32_t) * ntp4;
-    s.items = (uint32_t*)p;
     s.flag = nullptr;
     return s;
 }
@@ -115,7 +113,7 @@ __device__ __forceinline__ void add_fix(const Shared& sm, long long* F, int i, f
 // 16h + ((l + t) & 15) at iteration t and the j-force accumulators rotate one
 // lane per iteration, so lane l ends with slot l & 15; the two half-warps'
 // shares of each j are then added with one exchange. NEAR tile pairs
-// (J - I <= 1) test exclusions and, on the diagonal, keep j > i only.
+// (J = I + 1) test exclusions.
 template <int ELEC, bool ENERGY, bool NEAR>
 __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const TopoDev& tp,
                                            const PairConst& pc, int I, int J, int h, int lane) {
@@ -136,8 +134,7 @@ __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         bool ok = r2 < pc.rc2;
         if (NEAR) {
-            const int dj = j - i + kExclWindow;  // in [1, 95]: j - i in (-32, 64)
-            ok = ok && (I != J || j > i);
+            const int dj = j - i + kExclWindow;  // in [33, 95]: j - i in [1, 64)
             if (dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
         }
         float e = 0.f;
@@ -160,6 +157,51 @@ __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const
     fjz += __shfl_xor_sync(kFull, fjz, 16);
     add_fix(sm, F, i, fix, fiy, fiz);
     if (lane < 16) add_fix(sm, F, jb + lane, fjx, fjy, fjz);
+    return eacc;
+}
+
+// The 496 pairs of tile I with itself in 16 iterations of one warp: at
+// iteration k lane l takes the pair (l, (l + k) & 31) (k = 16 on lanes 0..15
+// only), so every pair comes exactly once. The j-force accumulators rotate one
+// lane per iteration; at the end lane l holds atom (l + 17) & 31's, and one
+// exchange brings each to its atom's lane.
+template <int ELEC, bool ENERGY>
+__device__ __forceinline__ float diag_tile(const Shared& sm, long long* F, const TopoDev& tp,
+                                           const PairConst& pc, int I, int lane) {
+    const int i = I * kTile + lane;
+    const float4 xi = sm.xq[i];
+    const float2 li = sm.lj[i];
+    const unsigned long long em = i < tp.n_atoms ? tp.excl[i] : 0ull;
+    float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
+    const int src = (lane + 1) & 31;
+#pragma unroll 4
+    for (int k = 1; k <= 16; ++k) {
+        const int j = I * kTile + ((lane + k) & 31);
+        const float4 xj = sm.xq[j];
+        const float2 lj = sm.lj[j];
+        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const int dj = j - i + kExclWindow;  // in [1, 63]: |j - i| < 32
+        const bool ok = r2 < pc.rc2 && (k < 16 || lane < 16) && !((em >> dj) & 1ull);
+        float e = 0.f;
+        float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
+        s = ok ? s : 0.0f;
+        fix = fmaf(s, dx, fix);
+        fiy = fmaf(s, dy, fiy);
+        fiz = fmaf(s, dz, fiz);
+        fjx = fmaf(-s, dx, fjx);
+        fjy = fmaf(-s, dy, fjy);
+        fjz = fmaf(-s, dz, fjz);
+        if (ENERGY) eacc += ok ? e : 0.0f;
+        fjx = __shfl_sync(kFull, fjx, src);
+        fjy = __shfl_sync(kFull, fjy, src);
+        fjz = __shfl_sync(kFull, fjz, src);
+    }
+    const int back = (lane + 15) & 31;
+    fjx = __shfl_sync(kFull, fjx, back);
+    fjy = __shfl_sync(kFull, fjy, back);
+    fjz = __shfl_sync(kFull, fjz, back);
+    add_fix(sm, F, i, fix + fjx, fiy + fjy, fiz + fjz);
     return eacc;
 }
 
@@ -250,15 +292,18 @@ __device__ __forceinline__ long long contact_term(const Shared& sm, long long* G
     return ff2fix40(ff_sqr(d));
 }
 
-// Gaussian numbers of the O half step of global step `step` for atoms
-// 32 q .. 32 q + 31 (Philox4x32-10, counter (atom, replica id, step, 0)).
-__device__ __forceinline__ void noise_chunk(const Shared& sm, const RunParams& P, uint32_t rep_id,
-                                            long long step, int q, int n, int lane) {
+// Noise of the O half step of global step `step` for atoms 32 q .. 32 q + 31:
+// sqrt((1 - c1^2) kT / m_i) times Gaussian numbers from Philox4x32-10 with
+// counter (atom, replica id, step, 0).
+__device__ __forceinline__ void noise_chunk(const Shared& sm, const TopoDev& tp, const RunParams& P,
+                                            uint32_t rep_id, long long step, int q, int lane) {
     const int i = q * kTile + lane;
-    if (i < n) {
+    if (i < tp.n_atoms) {
         const uint4 rb = philox4x32_10(make_uint4((uint32_t)i, rep_id, (uint32_t)step, 0u), P.key0,
                                        P.key1);
-        sm.xi[i] = normals4_f32(rb);
+        const float4 g = normals4_f32(rb);
+        const float sd = tp.noise_sd[i];
+        sm.xi[i] = make_float4(sd * g.x, sd * g.y, sd * g.z, 0.f);
     }
 }
 
@@ -313,51 +358,39 @@ __device__ __forceinline__ float box_gap2(float4 al, float4 ah, float4 bl, float
     return fmaf(gx, gx, fmaf(gy, gy, gz * gz));
 }
 
-// Active half-tile pairs in a fixed order (identical in every CTA of a cluster).
-__device__ void build_items(const Shared& sm, Scalars& sc, int ntp, float rc2) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    int carry = 0;
-    for (int base = 0; base < ntp; base += blockDim.x) {
-        const int p = base + tid;
-        unsigned m = 0;
-        uint32_t w = 0;
-        if (p < ntp) {
-            w = sm.tpl[p];
-            const int I = (int)(w >> 16), J = (int)(w & 0xffff);
-            const float4 al = sm.blo[I], ah = sm.bhi[I];
-            if (box_gap2(al, ah, sm.blo[sm.nt + 2 * J], sm.bhi[sm.nt + 2 * J]) < rc2) m |= 1u;
-            if (box_gap2(al, ah, sm.blo[sm.nt + 2 * J + 1], sm.bhi[sm.nt + 2 * J + 1]) < rc2) m |= 2u;
-        }
-        const int cnt = __popc(m);
-        int x = cnt;  // inclusive warp scan
+// Summed fixed-point partials (this CTA + peer) of one atom: force and bias gradient.
+struct AtomSums {
+    long long f[3], g[3];
+};
+
+// Loads the summed partials of atom i for parity b (the peer's through distributed
+// shared memory); all loads are issued before any sum is formed.
+template <int CL>
+__device__ __forceinline__ void load_sums(const Shared& sm, int b, int peer, int i, bool bias,
+                                          AtomSums& a) {
+    const int nta = sm.nta;
+    const long long* F = sm.Fp[b];
+    const long long* G = sm.Gp[b];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) sc.scan[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int t = lane < nw ? sc.scan[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, t, o);
-                if (lane >= o) t += y;
-            }
-            sc.scan[lane] = t;
-        }
-        __syncthreads();
-        int pos = carry + (warp > 0 ? sc.scan[warp - 1] : 0) + x - cnt;
-        if (m) {
-            const uint32_t I = w >> 16, J = w & 0xffff;
-            if (m & 1u) sm.items[pos++] = I | (J << 11);
-            if (m & 2u) sm.items[pos] = I | (J << 11) | (1u << 22);
-        }
-        carry += sc.scan[nw - 1];
-        __syncthreads();
+    for (int c = 0; c < 3; ++c) {
+        a.f[c] = F[c * nta + i];
+        a.g[c] = bias ? G[c * nta + i] : 0;
     }
-    if (tid == 0) sc.n_items = carry;
-    __syncthreads();
+    if (CL == 2) {
+        const long long* pF = rank_ptr<CL>(sm.Fp[b], peer);
+        const long long* pG = rank_ptr<CL>(sm.Gp[b], peer);
+        long long r[3], q[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            r[c] = pF[c * nta + i];
+            q[c] = bias ? pG[c * nta + i] : 0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.f[c] += r[c];
+            a.g[c] += q[c];
+        }
+    }
 }
 
 // Force evaluation of the configuration in shared memory (boxes current) for
@@ -375,30 +408,40 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     long long* F = sm.Fp[b];
     long long* G = sm.Gp[b];
     sm.flag = &sc.flag[b];
-    build_items(sm, sc, ntp, P.pc.rc2);
     if (noise_step >= 0)
-        for (int q = warp; q < nt; q += nw) noise_chunk(sm, P, rep_id, noise_step, q, tp.n_atoms, lane);
-    // work queue: half tile pairs, then contact, bond and angle chunks
-    const int n_half = sc.n_items;
+        for (int q = warp; q < nt; q += nw) noise_chunk(sm, tp, P, rep_id, noise_step, q, lane);
+    // work list: half-tile candidates (two per tile pair, in tile-pair order; the tile
+    // with itself is one item), then contact, bond and angle chunks. The warp that
+    // pulls a half tile whose box is farther than the cutoff from the i tile's box
+    // skips it. Item k belongs to CTA k mod CL of the cluster, whose warps pull their
+    // items from a counter in their own shared memory; the two halves of a tile pair
+    // are listed in alternating order, so both CTAs get half of the diagonal items.
+    const int n_half = 2 * ntp;
     const int ncon = P.bias == 1 ? tp.n_contacts : 0;
     const int e_con = n_half + (ncon + kChunk - 1) / kChunk;
     const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
     const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
-    int* counter = rank_ptr<CL>(&sc.work_next[b], 0);
+    int* counter = &sc.work_next[b];
+    const int rank = cta_rank<CL>();
     long long e = 0, zacc = 0;  // fixed point: sums independent of the work order
     for (;;) {
-        int k = 0;
-        if (lane == 0) k = atomicAdd(counter, 1);
-        k = __shfl_sync(kFull, k, 0);
+        int m = 0;
+        if (lane == 0) m = atomicAdd(counter, 1);
+        const int k = __shfl_sync(kFull, m, 0) * CL + rank;
         if (k >= e_all) break;
         if (k < n_half) {
-            const uint32_t w = sm.items[k];
-            const int I = (int)(w & 0x7ff), J = (int)((w >> 11) & 0x7ff), h = (int)(w >> 22);
-            float ep;
-            if (J - I <= 1)
-                ep = half_tile<ELEC, ENERGY, true>(sm, F, tp, P.pc, I, J, h, lane);
-            else
-                ep = half_tile<ELEC, ENERGY, false>(sm, F, tp, P.pc, I, J, h, lane);
+            const uint32_t w = sm.tpl[k >> 1];
+            const int I = (int)(w >> 16), J = (int)(w & 0xffff), h = (k ^ (k >> 1)) & 1;
+            float ep = 0.f;
+            if (I == J) {
+                if (h == 0) ep = diag_tile<ELEC, ENERGY>(sm, F, tp, P.pc, I, lane);
+            } else if (box_gap2(sm.blo[I], sm.bhi[I], sm.blo[sm.nt + 2 * J + h],
+                                sm.bhi[sm.nt + 2 * J + h]) < P.pc.rc2) {
+                if (J == I + 1)
+                    ep = half_tile<ELEC, ENERGY, true>(sm, F, tp, P.pc, I, J, h, lane);
+                else
+                    ep = half_tile<ELEC, ENERGY, false>(sm, F, tp, P.pc, I, J, h, lane);
+            }
             if (ENERGY) e += f2fix(ep);
         } else if (k < e_con) {
             const int c = (k - n_half) * kChunk + lane;
@@ -424,6 +467,12 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         sc.red_e[b][warp] = e;
     }
     cluster_barrier<CL>();
+    // the partials of the other parity were last read (here and in the peer CTA)
+    // before this barrier: clear them for the next evaluation meanwhile
+    for (int i = tid; i < 3 * sm.nta; i += blockDim.x) {
+        sm.Fp[b ^ 1][i] = 0;
+        sm.Gp[b ^ 1][i] = 0;
+    }
     // shares of z, energy and flags from every CTA of the cluster (integer sums)
     if (warp == 0) {
         long long zt = 0, et = 0;
@@ -457,14 +506,6 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         }
     }
     __syncthreads();
-}
-
-// Sum of this CTA's and the peer's fixed-point partials at index idx.
-template <int CL>
-__device__ __forceinline__ float sum_fix(const long long* own, const long long* peer, int idx) {
-    long long v = own[idx];
-    if (CL == 2) v += peer[idx];
-    return fix2f(v);
 }
 
 __device__ void tile_pair_table(const Shared& sm, int nt) {
@@ -501,7 +542,8 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             const float4 x = st.x[rep.atom_off + i];
             sm.xq[i] = make_float4(x.x, x.y, x.z, tp.qs[i]);
             sm.lj[i] = tp.lj[i];
-            sm.v[i] = st.v[rep.atom_off + i];
+            const float4 v = st.v[rep.atom_off + i];
+            sm.v[i] = make_float4(v.x, v.y, v.z, tp.inv_m[i]);
         } else {  // padding: far apart from everything, no charge, no LJ
             sm.xq[i] = make_float4(1.0e5f * (float)(i + 1), 0.f, 0.f, 0.f);
             sm.lj[i] = make_float2(0.f, 0.f);
@@ -532,23 +574,20 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
     all_boxes(sm, n);
     cluster_barrier<CL>();  // every CTA of the cluster is initialised before any remote access
     const int peer = rank ^ 1;
-    const long long* pFp[2] = {CL == 2 ? rank_ptr<CL>(sm.Fp[0], peer) : nullptr,
-                               CL == 2 ? rank_ptr<CL>(sm.Fp[1], peer) : nullptr};
-    const long long* pGp[2] = {CL == 2 ? rank_ptr<CL>(sm.Gp[0], peer) : nullptr,
-                               CL == 2 ? rank_ptr<CL>(sm.Gp[1], peer) : nullptr};
     const float hdt = P.half_dt;
     if (sc.status == 0 && P.n_steps > 0) {
         // the O half step that follows an evaluation uses the noise of the same step index
         evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true, rep.rep_id, step);
+        // position of `step` in the save cycle and ring slot of the next frame, kept as
+        // counters so that the loop has no 64-bit divisions
+        int save_phase = P.save_interval > 0 ? (int)(step % P.save_interval) : -1;
+        int slot = P.max_frames > 0 ? (int)(sc.n_saved % P.max_frames) : 0;
         for (long long s = 0; s <= P.n_steps; ++s) {
             // B of the step just evaluated (s > 0), then A of the next one (s < n_steps)
             const bool do_b = s > 0, do_a = s < P.n_steps;
             const int b = (int)(step & 1), nb = b ^ 1;
             const bool bias = sc.bias_on;
-            const bool save = do_b && P.save_interval > 0 && (step % P.save_interval) == 0;
-            const long long slot = sc.n_saved % P.max_frames;
-            const long long* own = sm.Fp[b];
-            const long long* gown = sm.Gp[b];
+            const bool save = do_b && save_phase == 0;
             const float kb = -(float)sc.factor * 4.0f * P.inv_r0sq;  // F_bias = kb G
             float tb = 0.f;
             for (int base = 0; base < nta; base += blockDim.x) {
@@ -556,26 +595,26 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                 const bool valid = i < n;
                 float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (valid) {
-                    const float im = tp.inv_m[i];
-                    float fx = sum_fix<CL>(own, pFp[b], i), fy = sum_fix<CL>(own, pFp[b], nta + i),
-                          fz = sum_fix<CL>(own, pFp[b], 2 * nta + i);
+                    AtomSums a;
+                    load_sums<CL>(sm, b, peer, i, bias, a);
+                    float4 v = sm.v[i];
+                    const float im = v.w;
+                    float fx = fix2f(a.f[0]), fy = fix2f(a.f[1]), fz = fix2f(a.f[2]);
                     if (bias) {
-                        const float bx = kb * sum_fix<CL>(gown, pGp[b], i),
-                                    by = kb * sum_fix<CL>(gown, pGp[b], nta + i),
-                                    bz = kb * sum_fix<CL>(gown, pGp[b], 2 * nta + i);
+                        const float bx = kb * fix2f(a.g[0]), by = kb * fix2f(a.g[1]),
+                                    bz = kb * fix2f(a.g[2]);
                         if (do_b) tb += (bx * bx + by * by + bz * bz) * im;
                         fx += bx;
                         fy += by;
                         fz += bz;
                     }
-                    float4 v = sm.v[i];
                     x = sm.xq[i];
                     if (do_b) {  // B: closes the evaluated step
                         v.x = fmaf(hdt * im, fx, v.x);
                         v.y = fmaf(hdt * im, fy, v.y);
                         v.z = fmaf(hdt * im, fz, v.z);
                         if (save && rank == 0) {
-                            float* fr = st.frames + 3 * (rep.frame_off + slot * n + i);
+                            float* fr = st.frames + 3 * (rep.frame_off + (long long)slot * n + i);
                             fr[0] = x.x;
                             fr[1] = x.y;
                             fr[2] = x.z;
@@ -589,10 +628,9 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                         x.y = fmaf(hdt, v.y, x.y);
                         x.z = fmaf(hdt, v.z, x.z);
                         const float4 xi = sm.xi[i];  // drawn during the evaluation
-                        const float sd = tp.noise_sd[i];
-                        v.x = fmaf(P.c1, v.x, sd * xi.x);
-                        v.y = fmaf(P.c1, v.y, sd * xi.y);
-                        v.z = fmaf(P.c1, v.z, sd * xi.z);
+                        v.x = fmaf(P.c1, v.x, xi.x);
+                        v.y = fmaf(P.c1, v.y, xi.y);
+                        v.z = fmaf(P.c1, v.z, xi.z);
                         x.x = fmaf(hdt, v.x, x.x);
                         x.y = fmaf(hdt, v.y, x.y);
                         x.z = fmaf(hdt, v.z, x.z);
@@ -609,12 +647,6 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                     warp_boxes(sm, (base >> 5) + warp, lo, hi, lane);
                 }
             }
-            // this CTA's partials of the next evaluation start from zero
-            if (do_a)
-                for (int i = tid; i < nta3; i += blockDim.x) {
-                    sm.Fp[nb][i] = 0;
-                    sm.Gp[nb][i] = 0;
-                }
             if (bias && do_b) {
                 tb = warp_sum_f(tb);
                 if (lane == 0) sc.red_t[warp] = tb;
@@ -640,9 +672,11 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             }
             // leave after the last B, or when the new state is non-finite (identical in
             // every CTA of the cluster: same inputs, same arithmetic)
+            if (save) slot = slot + 1 == P.max_frames ? 0 : slot + 1;
             if (!do_a || sc.status != 0) break;
             ++step;
-            const bool save_next = P.save_interval > 0 && (step % P.save_interval) == 0;
+            if (save_phase >= 0) save_phase = save_phase + 1 == P.save_interval ? 0 : save_phase + 1;
+            const bool save_next = save_phase == 0;
             if (save_next)
                 evaluate<ELEC, true, CL>(sm, sc, tp, P, nb, true, rep.rep_id, step);
             else
@@ -656,7 +690,8 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         for (int i = tid; i < n; i += blockDim.x) {
             const float4 x = sm.xq[i];
             st.x[rep.atom_off + i] = make_float4(x.x, x.y, x.z, 0.f);
-            st.v[rep.atom_off + i] = sm.v[i];
+            const float4 v = sm.v[i];
+            st.v[rep.atom_off + i] = make_float4(v.x, v.y, v.z, 0.f);
         }
         if (tid == 0) {
             st.zm[r] = sc.zm;
@@ -728,7 +763,7 @@ size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max) {
     const size_t ntp4 = (size_t)((ntp_max + 3) & ~3);
     (void)ncon_max;  // contacts live in the topology (global memory)
     return sizeof(float4) * nta * 3 + sizeof(float4) * 6 * nt + sizeof(long long) * 12 * nta +
-           sizeof(float2) * nta + sizeof(uint32_t) * 3 * ntp4;
+           sizeof(float2) * nta + sizeof(uint32_t) * ntp4;
 }
 
 template <int ELEC, int CL>
