@@ -8,7 +8,9 @@
 //                        inside a tile, order by x into two halves of 16 and
 //                        each half by y, so that slots 8q..8q+7 form a compact
 //                        j cluster; tile and cluster boxes; per i tile the list
-//                        of j clusters within r_c + skin of the tile box
+//                        of j clusters within r_c + skin of the tile box, each
+//                        with the periodic shift that is the minimum image of
+//                        all its pairs (else the tile takes it pair by pair)
 //   pairs                one warp per i tile; each lane owns one slot and adds
 //                        up its own force over the listed clusters (both
 //                        directions of every pair: no atomics, a fixed order)
@@ -148,29 +150,38 @@ __global__ void __launch_bounds__(kSortThreads) k_box_sort(BoxDev B, const TopoD
         col_tile[ncols] = t;  // <= nt by the capacity ceil(n/32) + ncol^2
     }
     __syncthreads();
-    // scatter in atom-id order, one warp at a time: ties (same key) keep id order
-    for (int c0 = 0; c0 < B.n_atoms; c0 += blockDim.x) {
-        const int a = c0 + tid;
-        const bool valid = a < B.n_atoms;
-        const int s = valid ? slot_of[a] : 0;
-        const int k = valid ? key[s] : -1 - lane;
-        for (int w = 0; w < nw; ++w) {
-            if (warp == w) {
-                const unsigned peers = __match_any_sync(kFullB, k);
-                const int rank = __popc(peers & ((1u << lane) - 1u));
-                int p = 0;
-                if (valid) p = cnt[k] + rank;
-                __syncwarp();
-                if (valid && rank == 0) cnt[k] += __popc(peers);
-                if (valid) {
-                    const int c = k / nz;
-                    const int dst = col_tile[c] * 32 + (p - col_first[c]);
-                    pos2[dst] = pos[s];
-                    vel2[dst] = vel[s];
-                    id2[dst] = a;
-                }
+    // scatter: slots within a key come in arbitrary order from the atomics ...
+    for (int a = tid; a < B.n_atoms; a += blockDim.x) {
+        const int s = slot_of[a];
+        const int k = key[s];
+        const int p = atomicAdd(&cnt[k], 1);
+        const int c = k / nz;
+        const int dst = col_tile[c] * 32 + (p - col_first[c]);
+        pos2[dst] = pos[s];
+        vel2[dst] = vel[s];
+        id2[dst] = a;
+    }
+    __syncthreads();
+    // ... and are then put in atom-id order, one key per thread (a key holds a few
+    // atoms); cnt[k] now ends key k, so key k spans [cnt[k - 1], cnt[k])
+    for (int k = tid; k < ncols * nz; k += blockDim.x) {
+        const int lo = k > 0 ? cnt[k - 1] : 0, hi = cnt[k];
+        if (hi - lo < 2) continue;
+        const int c = k / nz;
+        const int off = col_tile[c] * 32 - col_first[c];
+        for (int q = lo + 1; q < hi; ++q) {  // insertion sort by id
+            const int ia = id2[off + q];
+            const float4 pa = pos2[off + q], va = vel2[off + q];
+            int u = q - 1;
+            while (u >= lo && id2[off + u] > ia) {
+                id2[off + u + 1] = id2[off + u];
+                pos2[off + u + 1] = pos2[off + u];
+                vel2[off + u + 1] = vel2[off + u];
+                --u;
             }
-            __syncthreads();
+            id2[off + u + 1] = ia;
+            pos2[off + u + 1] = pa;
+            vel2[off + u + 1] = va;
         }
     }
     __syncthreads();
@@ -235,13 +246,22 @@ __global__ void k_box_tiles(BoxDev B, int r0) {
             B.chi[c] = make_float4(hx, hy, hz, 0.f);
         }
     }
+    const int a = B.id[(size_t)r * B.np + s];
+    const bool chain = __any_sync(kFullB, a >= 0 && a < B.n_chain);
     if (lane == 0) {
         B.tlo[(size_t)r * B.nt + t] = make_float4(lx, ly, lz, 0.f);
         B.thi[(size_t)r * B.nt + t] = make_float4(hx, hy, hz, 0.f);
+        B.tflag[(size_t)r * B.nt + t] = chain ? 1 : 0;
     }
 }
 
 // Rebuild step 3: j clusters near every i tile (one warp per i tile), in cluster order.
+// Each entry carries the periodic shift s (per axis -1, 0 or 1, in units of L) that
+// takes the cluster's box centre nearest to the tile's. When |d_c + s L| plus both
+// half widths plus the skin (the most two atoms can close in before the next
+// rebuild) stays below L / 2 on every axis, s is the minimum image of every pair of
+// the two boxes until then; otherwise the tile is flagged for the per-pair minimum
+// image.
 __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
@@ -251,45 +271,126 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     const float4 al = B.tlo[(size_t)r * B.nt + t], ah = B.thi[(size_t)r * B.nt + t];
     uint32_t* out = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
     int count = 0;
+    bool inexact = false;
+    const float room = 0.5f * B.L - 2.0f * sqrtf(B.skin2_quarter);  // L/2 - skin
     if (al.x <= ah.x) {  // the i tile holds atoms
         const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
+        const float hx = 0.5f * (ah.x - al.x), hy = 0.5f * (ah.y - al.y), hz = 0.5f * (ah.z - al.z);
         const int ncl = 4 * B.nt;
         for (int j0 = 0; j0 < ncl; j0 += 32) {
             const int j = j0 + lane;
-            bool hit = false;
+            bool hit = false, exact = true;
+            uint32_t code = 0;
             if (j < ncl) {
                 const float4 bl = B.clo[(size_t)r * ncl + j], bh = B.chi[(size_t)r * ncl + j];
                 if (bl.x <= bh.x) {  // the cluster holds atoms
-                    // lower bound of any periodic-image distance between the two boxes:
-                    // |minimum-image centre distance| - half widths, per dimension
-                    const float gx = fmaxf(0.f, fabsf(min_img(0.5f * (bl.x + bh.x) - cx, B.L, B.invL)) -
-                                                    0.5f * ((bh.x - bl.x) + (ah.x - al.x)));
-                    const float gy = fmaxf(0.f, fabsf(min_img(0.5f * (bl.y + bh.y) - cy, B.L, B.invL)) -
-                                                    0.5f * ((bh.y - bl.y) + (ah.y - al.y)));
-                    const float gz = fmaxf(0.f, fabsf(min_img(0.5f * (bl.z + bh.z) - cz, B.L, B.invL)) -
-                                                    0.5f * ((bh.z - bl.z) + (ah.z - al.z)));
+                    const float dx = 0.5f * (bl.x + bh.x) - cx, dy = 0.5f * (bl.y + bh.y) - cy,
+                                dz = 0.5f * (bl.z + bh.z) - cz;
+                    const float sx = -rintf(dx * B.invL), sy = -rintf(dy * B.invL),
+                                sz = -rintf(dz * B.invL);
+                    const float ex = fabsf(fmaf(sx, B.L, dx)), ey = fabsf(fmaf(sy, B.L, dy)),
+                                ez = fabsf(fmaf(sz, B.L, dz));
+                    const float wx = hx + 0.5f * (bh.x - bl.x), wy = hy + 0.5f * (bh.y - bl.y),
+                                wz = hz + 0.5f * (bh.z - bl.z);
+                    // lower bound of any periodic-image distance between the two boxes
+                    const float gx = fmaxf(0.f, ex - wx), gy = fmaxf(0.f, ey - wy),
+                                gz = fmaxf(0.f, ez - wz);
                     hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
+                    exact = ex + wx < room && ey + wy < room && ez + wz < room;
+                    code = (uint32_t)j | ((uint32_t)(sx + 1.f) << 24) | ((uint32_t)(sy + 1.f) << 26) |
+                           ((uint32_t)(sz + 1.f) << 28);
                 }
             }
             const unsigned m = __ballot_sync(kFullB, hit);
             if (hit) {
                 const int pos = count + __popc(m & ((1u << lane) - 1u));
-                if (pos < B.max_nbr) out[pos] = (uint32_t)j;
+                if (pos < B.max_nbr) out[pos] = code;
             }
             count += __popc(m);
+            inexact = inexact || (hit && !exact);
         }
     }
     const bool overflow = count > B.max_nbr;
     if (overflow) count = B.max_nbr;
+    const bool any_inexact = __any_sync(kFullB, inexact);
     if (lane == 0) {
         B.nnbr[(size_t)r * B.nt + t] = count;
+        B.tflag[(size_t)r * B.nt + t] |= any_inexact ? 2 : 0;
         if (overflow) atomicOr(&st.status[r], SCPS_FLAG_LIST_OVERFLOW);
     }
 }
 
-// Non-bonded forces: one warp per i tile; lane l owns slot 32 t + l. The j
-// slots come four listed clusters at a time (lane l loads slot l & 7 of
-// cluster l >> 3 of the group).
+// Non-bonded forces of i tile t on one warp; lane l owns slot 32 t + l. The j
+// slots come four listed clusters at a time (lane l stages slot l & 7 of
+// cluster l >> 3 of the group, moved by the entry's periodic shift unless
+// MINIMG, where every pair takes its own minimum image). EXCL tests the
+// exclusion mask (tiles holding chain atoms); padding slots sit far away
+// from everything (MINIMG tests their ids instead).
+template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG>
+__device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev* __restrict__ topo,
+                                                  const RunParams& P, int r, int t, int lane,
+                                                  float4 (&sj)[32], float2 (&sp)[32], int (&sid)[32]) {
+    const size_t base = (size_t)r * B.np;
+    const int si = t * 32 + lane;
+    const float4 xi = B.pos[base + si];
+    const float2 li = B.par[base + si];
+    const int idi = B.id[base + si];
+    const unsigned long long em = (EXCL && idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
+    const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
+    const int cnt = B.nnbr[(size_t)r * B.nt + t];
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    for (int q = 0; q < cnt; q += 4) {
+        const int qe = q + (lane >> 3);
+        if (qe < cnt) {
+            const uint32_t code = lst[qe];
+            const int sjl = (int)(code & 0xffffffu) * 8 + (lane & 7);
+            float4 p = B.pos[base + sjl];
+            if (!MINIMG) {
+                p.x = fmaf((float)((int)((code >> 24) & 3u) - 1), B.L, p.x);
+                p.y = fmaf((float)((int)((code >> 26) & 3u) - 1), B.L, p.y);
+                p.z = fmaf((float)((int)((code >> 28) & 3u) - 1), B.L, p.z);
+            }
+            sj[lane] = p;
+            sp[lane] = B.par[base + sjl];
+            sid[lane] = B.id[base + sjl];
+        } else {
+            sj[lane] = make_float4(1.0e18f, 0.f, 0.f, 0.f);  // beyond any cutoff
+            sp[lane] = make_float2(0.f, 0.f);
+            sid[lane] = -1;
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const float4 xj = sj[k];
+            const float2 lj = sp[k];
+            const int idj = sid[k];
+            float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            if (MINIMG) {
+                dx = min_img(dx, B.L, B.invL);
+                dy = min_img(dy, B.L, B.invL);
+                dz = min_img(dz, B.L, B.invL);
+            }
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool ok = r2 < P.pc.rc2 && idj != idi;
+            if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
+            if (EXCL) {
+                const unsigned dj = (unsigned)(idj - idi + kExclWindow);
+                if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
+            }
+            float ep = 0.f;
+            float sc = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
+            sc = ok ? sc : 0.0f;
+            fx = fmaf(sc, dx, fx);
+            fy = fmaf(sc, dy, fy);
+            fz = fmaf(sc, dz, fz);
+            if (ENERGY) e += ok ? 0.5f * ep : 0.0f;
+        }
+        __syncwarp();
+    }
+    return make_float4(fx, fy, fz, e);
+}
+
+// Non-bonded forces: one warp per i tile, the variant chosen by the tile's flags.
 template <int ELEC, bool ENERGY>
 __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __restrict__ topo,
                                                    RunParams P, int r0) {
@@ -300,50 +401,14 @@ __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __re
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * 4 + w;
     if (t >= B.nt) return;
-    const size_t base = (size_t)r * B.np;
-    const int si = t * 32 + lane;
-    const float4 xi = B.pos[base + si];
-    const float2 li = B.par[base + si];
-    const int idi = B.id[base + si];
-    const unsigned long long em = (idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
-    const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
-    const int cnt = B.nnbr[(size_t)r * B.nt + t];
-    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-    for (int q = 0; q < cnt; q += 4) {
-        const int qe = q + (lane >> 3);
-        if (qe < cnt) {
-            const int sjl = (int)lst[qe] * 8 + (lane & 7);
-            sj[w][lane] = B.pos[base + sjl];
-            sp[w][lane] = B.par[base + sjl];
-            sid[w][lane] = B.id[base + sjl];
-        } else {
-            sj[w][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-            sp[w][lane] = make_float2(0.f, 0.f);
-            sid[w][lane] = -1;
-        }
-        __syncwarp();
-#pragma unroll 4
-        for (int k = 0; k < 32; ++k) {
-            const float4 xj = sj[w][k];
-            const float2 lj = sp[w][k];
-            const int idj = sid[w][k];
-            const float dx = min_img(xj.x - xi.x, B.L, B.invL), dy = min_img(xj.y - xi.y, B.L, B.invL),
-                        dz = min_img(xj.z - xi.z, B.L, B.invL);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool ok = r2 < P.pc.rc2 && idj != idi && idj >= 0 && idi >= 0;
-            const unsigned dj = (unsigned)(idj - idi + kExclWindow);
-            if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
-            float ep = 0.f;
-            float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
-            s = ok ? s : 0.0f;
-            fx = fmaf(s, dx, fx);
-            fy = fmaf(s, dy, fy);
-            fz = fmaf(s, dz, fz);
-            if (ENERGY) e += ok ? 0.5f * ep : 0.0f;
-        }
-        __syncwarp();
+    const int fl = B.tflag[(size_t)r * B.nt + t];
+    float4 f;
+    switch (fl & 3) {
+        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w]); break;
+        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w]); break;
+        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w]); break;
     }
-    B.fnb[base + si] = make_float4(fx, fy, fz, e);
+    B.fnb[(size_t)r * B.np + t * 32 + lane] = f;
 }
 
 // Chain terms of one replica: bonds, angles (minimum image), z and the ratchet,

@@ -463,6 +463,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.chi, (size_t)Rs * 4 * B.nt);
         BALLOC(B.nbr, (size_t)Rs * B.nt * B.max_nbr);
         BALLOC(B.nnbr, (size_t)Rs * B.nt);
+        BALLOC(B.tflag, (size_t)Rs * B.nt);
         BALLOC(B.need, Rs);
         BALLOC(B.since, Rs);
         BALLOC(B.maxd2, Rs);

@@ -103,8 +103,10 @@ struct BoxDev {
     float4* thi;
     float4* clo;      // [replica][4 nt] boxes of the 8-slot j clusters
     float4* chi;
-    uint32_t* nbr;    // [replica][nt][max_nbr]: j cluster index
+    uint32_t* nbr;    // [replica][nt][max_nbr]: j cluster | periodic shift << 24 (2 bits per axis)
     int* nnbr;        // [replica][nt]
+    int* tflag;       // [replica][nt]: 1 = tile holds chain atoms, 2 = a listed cluster needs
+                      // the minimum image per pair (its shift is not the same for all pairs)
     int* need;        // [replica] rebuild flag
     int* since;       // [replica] evaluations since the last rebuild
     unsigned* maxd2;  // [replica] largest squared displacement since then (float bits)
