@@ -277,7 +277,8 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
         const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
         const float hx = 0.5f * (ah.x - al.x), hy = 0.5f * (ah.y - al.y), hz = 0.5f * (ah.z - al.z);
         const int ncl = 4 * B.nt;
-        for (int j0 = 0; j0 < ncl; j0 += 32) {
+        // each pair once: clusters of this tile and of later tiles only
+        for (int j0 = 4 * t; j0 < ncl; j0 += 32) {
             const int j = j0 + lane;
             bool hit = false, exact = true;
             uint32_t code = 0;
@@ -320,16 +321,22 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     }
 }
 
-// Non-bonded forces of i tile t on one warp; lane l owns slot 32 t + l. The j
-// slots come four listed clusters at a time (lane l stages slot l & 7 of
+// Non-bonded forces of i tile t on one warp, each pair once (Newton's third
+// law): lane l owns slot 32 t + l and adds up its force as i atom in registers.
+// The j slots come four listed clusters at a time (lane l stages slot l & 7 of
 // cluster l >> 3 of the group, moved by the entry's periodic shift unless
-// MINIMG, where every pair takes its own minimum image). EXCL tests the
-// exclusion mask (tiles holding chain atoms); padding slots sit far away
-// from everything (MINIMG tests their ids instead).
+// MINIMG, where every pair takes its own minimum image); at iteration u lane l
+// takes staged slot (l + u) & 31 and the j-force accumulators rotate one lane
+// per iteration, so after 32 lane l holds staged slot l's, which it adds to the
+// slot's fixed-point j force. A pair counts when its j slot comes after its i
+// slot (lists hold clusters of this tile and later tiles). EXCL tests the
+// exclusion mask (tiles holding chain atoms); padding slots sit far away from
+// everything (MINIMG tests their ids instead).
 template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG>
 __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev* __restrict__ topo,
                                                   const RunParams& P, int r, int t, int lane,
-                                                  float4 (&sj)[32], float2 (&sp)[32], int (&sid)[32]) {
+                                                  float4 (&sj)[32], float2 (&sp)[32], int (&sid)[32],
+                                                  int (&sslot)[32]) {
     const size_t base = (size_t)r * B.np;
     const int si = t * 32 + lane;
     const float4 xi = B.pos[base + si];
@@ -338,12 +345,15 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
     const unsigned long long em = (EXCL && idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
     const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
     const int cnt = B.nnbr[(size_t)r * B.nt + t];
+    long long* fx_acc = B.facc + 3 * base;
+    const int src = (lane + 1) & 31;
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     for (int q = 0; q < cnt; q += 4) {
         const int qe = q + (lane >> 3);
+        int sjl = -1;
         if (qe < cnt) {
             const uint32_t code = lst[qe];
-            const int sjl = (int)(code & 0xffffffu) * 8 + (lane & 7);
+            sjl = (int)(code & 0xffffffu) * 8 + (lane & 7);
             float4 p = B.pos[base + sjl];
             if (!MINIMG) {
                 p.x = fmaf((float)((int)((code >> 24) & 3u) - 1), B.L, p.x);
@@ -358,12 +368,14 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
             sp[lane] = make_float2(0.f, 0.f);
             sid[lane] = -1;
         }
+        sslot[lane] = sjl;
         __syncwarp();
+        float gx = 0.f, gy = 0.f, gz = 0.f;  // j-force accumulators (rotating)
 #pragma unroll 4
-        for (int k = 0; k < 32; ++k) {
+        for (int u = 0; u < 32; ++u) {
+            const int k = (lane + u) & 31;
             const float4 xj = sj[k];
             const float2 lj = sp[k];
-            const int idj = sid[k];
             float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
             if (MINIMG) {
                 dx = min_img(dx, B.L, B.invL);
@@ -371,11 +383,14 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
                 dz = min_img(dz, B.L, B.invL);
             }
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool ok = r2 < P.pc.rc2 && idj != idi;
-            if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
-            if (EXCL) {
-                const unsigned dj = (unsigned)(idj - idi + kExclWindow);
-                if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
+            bool ok = r2 < P.pc.rc2 && sslot[k] > si;
+            if (MINIMG || EXCL) {
+                const int idj = sid[k];
+                if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
+                if (EXCL) {
+                    const unsigned dj = (unsigned)(idj - idi + kExclWindow);
+                    if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
+                }
             }
             float ep = 0.f;
             float sc = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
@@ -383,7 +398,18 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
             fx = fmaf(sc, dx, fx);
             fy = fmaf(sc, dy, fy);
             fz = fmaf(sc, dz, fz);
-            if (ENERGY) e += ok ? 0.5f * ep : 0.0f;
+            gx = fmaf(-sc, dx, gx);
+            gy = fmaf(-sc, dy, gy);
+            gz = fmaf(-sc, dz, gz);
+            if (ENERGY) e += ok ? ep : 0.0f;
+            gx = __shfl_sync(kFullB, gx, src);
+            gy = __shfl_sync(kFullB, gy, src);
+            gz = __shfl_sync(kFullB, gz, src);
+        }
+        if (sjl >= 0) {  // lane l now holds staged slot l's j force
+            atomicAdd((unsigned long long*)&fx_acc[sjl], (unsigned long long)f2fix(gx));
+            atomicAdd((unsigned long long*)&fx_acc[B.np + sjl], (unsigned long long)f2fix(gy));
+            atomicAdd((unsigned long long*)&fx_acc[2 * B.np + sjl], (unsigned long long)f2fix(gz));
         }
         __syncwarp();
     }
@@ -397,6 +423,7 @@ __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __re
     __shared__ float4 sj[4][32];
     __shared__ float2 sp[4][32];
     __shared__ int sid[4][32];
+    __shared__ int sslot[4][32];
     const int r = blockIdx.y + r0;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * 4 + w;
@@ -404,11 +431,26 @@ __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __re
     const int fl = B.tflag[(size_t)r * B.nt + t];
     float4 f;
     switch (fl & 3) {
-        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w]); break;
-        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w]); break;
-        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w]); break;
+        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w], sslot[w]); break;
+        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w], sslot[w]); break;
+        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w], sslot[w]); break;
     }
     B.fnb[(size_t)r * B.np + t * 32 + lane] = f;
+}
+
+// Total non-bonded force on slot s of replica r: its i part plus its fixed-point
+// j part, which is cleared for the next evaluation.
+__device__ __forceinline__ float4 take_nb_force(const BoxDev& B, int r, int s) {
+    const size_t base = (size_t)r * B.np;
+    long long* acc = B.facc + 3 * base;
+    float4 f = B.fnb[base + s];
+    f.x += fix2f(acc[s]);
+    f.y += fix2f(acc[B.np + s]);
+    f.z += fix2f(acc[2 * B.np + s]);
+    acc[s] = 0;
+    acc[B.np + s] = 0;
+    acc[2 * B.np + s] = 0;
+    return f;
 }
 
 // Chain terms of one replica: bonds, angles (minimum image), z and the ratchet,
@@ -579,12 +621,12 @@ __global__ void k_box_integrate(BoxDev B, const TopoDev* __restrict__ topo, Stat
                                 int do_b, int do_a) {
     const int r = blockIdx.y;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.np || st.status[r] != 0) return;
+    if (s >= B.np) return;
     const size_t base = (size_t)r * B.np;
+    float4 f = take_nb_force(B, r, s);  // also clears the j part (frozen replicas too)
     const int a = B.id[base + s];
-    if (a < 0) return;
+    if (a < 0 || st.status[r] != 0) return;
     const TopoDev& tp = *topo;
-    float4 f = B.fnb[base + s];
     if (a < B.n_chain) {
         const float4 c = B.fch[(size_t)r * B.n_chain + a];
         f.x += c.x;
@@ -763,13 +805,15 @@ cudaError_t box_load(const BoxDev& B, const TopoDev* topo, const StateDev& st, c
     return cudaGetLastError();
 }
 
+// Forces of the evaluation slot r in atom order (F may be NULL: the j parts are
+// cleared all the same).
 __global__ void k_box_store_forces(BoxDev B, int r, float* __restrict__ F) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B.np) return;
     const size_t base = (size_t)r * B.np;
+    float4 f = take_nb_force(B, r, s);
     const int a = B.id[base + s];
-    if (a < 0) return;
-    float4 f = B.fnb[base + s];
+    if (a < 0 || !F) return;
     if (a < B.n_chain) {
         const float4 c = B.fch[(size_t)r * B.n_chain + a];
         f.x += c.x;
@@ -802,7 +846,7 @@ cudaError_t box_energy_forces(const BoxDev& B, const TopoDev* topo, const StateD
     k_box_load_frame<<<g, 256, 0, s>>>(B, topo, st, X, r_eval);
     cudaError_t e = box_eval(B, topo, st, P, r_eval, 1, elec, ncon_max, true, 0, 0, 0, s);
     if (e != cudaSuccess) return e;
-    if (F) k_box_store_forces<<<g, 256, 0, s>>>(B, r_eval, F);
+    k_box_store_forces<<<g, 256, 0, s>>>(B, r_eval, F);
     k_box_store_energy<<<1, 256, 0, s>>>(B, st, r_eval, U, Z);
     return cudaGetLastError();
 }

@@ -452,6 +452,9 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.id, np);
         BALLOC(B.id2, np);
         BALLOC(B.fnb, np);
+        BALLOC(B.facc, 3 * np);
+        if (cudaMemset(B.facc, 0, sizeof(long long) * 3 * np) != cudaSuccess)
+            return bail(fail(SCPS_ERR_CUDA, "cudaMemset failed"));
         BALLOC(B.pos2, np);
         BALLOC(B.vel2, np);
         BALLOC(B.key, np);

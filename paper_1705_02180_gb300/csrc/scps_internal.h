@@ -93,7 +93,9 @@ struct BoxDev {
     float2* par;      // (sigma/2, sqrt(24 eps))
     int* id;          // atom id of each slot, -1 for padding
     int* id2;         // sort buffer of id
-    float4* fnb;      // non-bonded force (w: energy share)
+    float4* fnb;      // non-bonded force on the slot as i atom (w: energy share)
+    long long* facc;  // [replica][3][np] non-bonded force on the slot as j atom, fixed point
+                      // 2^-20 (order-free sums; cleared by whoever consumes it)
     float4* pos2;     // sort buffers
     float4* vel2;
     int* slot_of;     // [replica][n_atoms]
