@@ -220,8 +220,10 @@ __global__ void __launch_bounds__(kSortThreads) k_box_sort(BoxDev B, const TopoD
     }
 }
 
-// Rebuild step 2: tile boxes and j-cluster boxes (one warp per tile).
-__global__ void k_box_tiles(BoxDev B, int r0) {
+// Rebuild step 2: tile boxes and j-cluster boxes (one warp per tile), and which
+// tiles and clusters hold only atoms with the LJ parameters of the last atom (a
+// solvent site), whose pair constants the pair kernel then computes once.
+__global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) {
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
     const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -230,6 +232,9 @@ __global__ void k_box_tiles(BoxDev B, int r0) {
     const int s = t * 32 + lane;
     const float4 p = B.pos[(size_t)r * B.np + s];
     const bool valid = B.id[(size_t)r * B.np + s] >= 0;
+    const float2 ref = topo->lj[B.n_atoms - 1];
+    const float2 par = B.par[(size_t)r * B.np + s];
+    const unsigned pure = __ballot_sync(kFullB, !valid || (par.x == ref.x && par.y == ref.y));
     float lx = valid ? p.x : 3.0e38f, ly = valid ? p.y : 3.0e38f, lz = valid ? p.z : 3.0e38f;
     float hx = valid ? p.x : -3.0e38f, hy = valid ? p.y : -3.0e38f, hz = valid ? p.z : -3.0e38f;
 #pragma unroll
@@ -242,7 +247,8 @@ __global__ void k_box_tiles(BoxDev B, int r0) {
         hz = fmaxf(hz, __shfl_xor_sync(kFullB, hz, o));
         if (o == 4 && (lane & 7) == 0) {  // the box of the 8-slot cluster of this lane
             const size_t c = (size_t)r * 4 * B.nt + 4 * t + (lane >> 3);
-            B.clo[c] = make_float4(lx, ly, lz, 0.f);
+            const bool cpure = ((pure >> (lane & ~7)) & 0xffu) == 0xffu;
+            B.clo[c] = make_float4(lx, ly, lz, cpure ? 1.f : 0.f);
             B.chi[c] = make_float4(hx, hy, hz, 0.f);
         }
     }
@@ -251,7 +257,7 @@ __global__ void k_box_tiles(BoxDev B, int r0) {
     if (lane == 0) {
         B.tlo[(size_t)r * B.nt + t] = make_float4(lx, ly, lz, 0.f);
         B.thi[(size_t)r * B.nt + t] = make_float4(hx, hy, hz, 0.f);
-        B.tflag[(size_t)r * B.nt + t] = chain ? 1 : 0;
+        B.tflag[(size_t)r * B.nt + t] = (chain ? 1 : 0) | (pure == kFullB ? 4 : 0);
     }
 }
 
@@ -299,7 +305,7 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
                     hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
                     exact = ex + wx < room && ey + wy < room && ez + wz < room;
                     code = (uint32_t)j | ((uint32_t)(sx + 1.f) << 24) | ((uint32_t)(sy + 1.f) << 26) |
-                           ((uint32_t)(sz + 1.f) << 28);
+                           ((uint32_t)(sz + 1.f) << 28) | (bl.w != 0.f ? 1u << 30 : 0u);
                 }
             }
             const unsigned m = __ballot_sync(kFullB, hit);
@@ -321,22 +327,75 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     }
 }
 
+// The pairs of i lane `lane` with one staged group of 32 j slots: at iteration
+// u the lane takes staged slot (l + u) & 31, and the j-force accumulators
+// rotate one lane per iteration, so after 32 lane l holds staged slot l's.
+// SELF: the group holds the tile's own clusters; a pair counts when its j slot
+// comes after its i slot. FAST: every i and j atom has the reference LJ
+// parameters, whose pair constants U are computed once.
+template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG, bool SELF, bool FAST>
+__device__ __forceinline__ void group_pairs(const BoxDev& B, const RunParams& P, const LJPair& U,
+                                            float4 xi, float2 li, int idi, unsigned long long em,
+                                            int si, int lane, const float4* sj, const float2* sp,
+                                            const int* sid, const int* sslot, float4& fi,
+                                            float& gx, float& gy, float& gz) {
+    const int src = (lane + 1) & 31;
+#pragma unroll 4
+    for (int u = 0; u < 32; ++u) {
+        const int k = (lane + u) & 31;
+        const float4 xj = sj[k];
+        float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        if (MINIMG) {
+            dx = min_img(dx, B.L, B.invL);
+            dy = min_img(dy, B.L, B.invL);
+            dz = min_img(dz, B.L, B.invL);
+        }
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool ok = r2 < P.pc.rc2;
+        if (SELF) ok = ok && sslot[k] > si;
+        if (MINIMG || EXCL) {
+            const int idj = sid[k];
+            if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
+            if (EXCL) {
+                const unsigned dj = (unsigned)(idj - idi + kExclWindow);
+                if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
+            }
+        }
+        float ep = 0.f, sc;
+        if (FAST) {
+            sc = pair_s_lj<ELEC, ENERGY>(r2, U, xi.w * xj.w, P.pc, &ep);
+        } else {
+            const float2 lj = sp[k];
+            sc = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
+        }
+        sc = ok ? sc : 0.0f;
+        fi.x = fmaf(sc, dx, fi.x);
+        fi.y = fmaf(sc, dy, fi.y);
+        fi.z = fmaf(sc, dz, fi.z);
+        gx = fmaf(-sc, dx, gx);
+        gy = fmaf(-sc, dy, gy);
+        gz = fmaf(-sc, dz, gz);
+        if (ENERGY) fi.w += ok ? ep : 0.0f;
+        gx = __shfl_sync(kFullB, gx, src);
+        gy = __shfl_sync(kFullB, gy, src);
+        gz = __shfl_sync(kFullB, gz, src);
+    }
+}
+
 // Non-bonded forces of i tile t on one warp, each pair once (Newton's third
 // law): lane l owns slot 32 t + l and adds up its force as i atom in registers.
 // The j slots come four listed clusters at a time (lane l stages slot l & 7 of
 // cluster l >> 3 of the group, moved by the entry's periodic shift unless
-// MINIMG, where every pair takes its own minimum image); at iteration u lane l
-// takes staged slot (l + u) & 31 and the j-force accumulators rotate one lane
-// per iteration, so after 32 lane l holds staged slot l's, which it adds to the
-// slot's fixed-point j force. A pair counts when its j slot comes after its i
-// slot (lists hold clusters of this tile and later tiles). EXCL tests the
-// exclusion mask (tiles holding chain atoms); padding slots sit far away from
-// everything (MINIMG tests their ids instead).
+// MINIMG, where every pair takes its own minimum image); each lane then adds the
+// j force of the slot it staged to that slot's fixed-point j force. Lists hold
+// the tile's own clusters first, then clusters of later tiles only. EXCL tests
+// the exclusion mask (tiles holding chain atoms); padding slots sit far away
+// from everything (MINIMG tests their ids instead).
 template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG>
 __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev* __restrict__ topo,
                                                   const RunParams& P, int r, int t, int lane,
-                                                  float4 (&sj)[32], float2 (&sp)[32], int (&sid)[32],
-                                                  int (&sslot)[32]) {
+                                                  bool tile_pure, float4 (&sj)[32], float2 (&sp)[32],
+                                                  int (&sid)[32], int (&sslot)[32]) {
     const size_t base = (size_t)r * B.np;
     const int si = t * 32 + lane;
     const float4 xi = B.pos[base + si];
@@ -345,15 +404,18 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
     const unsigned long long em = (EXCL && idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
     const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
     const int cnt = B.nnbr[(size_t)r * B.nt + t];
-    long long* fx_acc = B.facc + 3 * base;
-    const int src = (lane + 1) & 31;
-    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    long long* jacc = B.facc + 3 * base;
+    const float2 ref = topo->lj[B.n_atoms - 1];
+    const LJPair U = lj_pair(ref.x + ref.x, ref.y * ref.y, P.pc);
+    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int q = 0; q < cnt; q += 4) {
         const int qe = q + (lane >> 3);
         int sjl = -1;
+        bool cpure = true;
         if (qe < cnt) {
             const uint32_t code = lst[qe];
             sjl = (int)(code & 0xffffffu) * 8 + (lane & 7);
+            cpure = (code >> 30) & 1u;
             float4 p = B.pos[base + sjl];
             if (!MINIMG) {
                 p.x = fmaf((float)((int)((code >> 24) & 3u) - 1), B.L, p.x);
@@ -369,51 +431,32 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
             sid[lane] = -1;
         }
         sslot[lane] = sjl;
+        const bool gpure = __all_sync(kFullB, cpure);
         __syncwarp();
-        float gx = 0.f, gy = 0.f, gz = 0.f;  // j-force accumulators (rotating)
-#pragma unroll 4
-        for (int u = 0; u < 32; ++u) {
-            const int k = (lane + u) & 31;
-            const float4 xj = sj[k];
-            const float2 lj = sp[k];
-            float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            if (MINIMG) {
-                dx = min_img(dx, B.L, B.invL);
-                dy = min_img(dy, B.L, B.invL);
-                dz = min_img(dz, B.L, B.invL);
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        if (q == 0) {
+            group_pairs<ELEC, ENERGY, EXCL, MINIMG, true, false>(B, P, U, xi, li, idi, em, si, lane, sj, sp,
+                                                                 sid, sslot, fi, gx, gy, gz);
+        } else {
+            bool fast = false;
+            if constexpr (!EXCL && !MINIMG) fast = tile_pure && gpure;
+            if constexpr (!EXCL && !MINIMG) {
+                if (fast)
+                    group_pairs<ELEC, ENERGY, false, false, false, true>(B, P, U, xi, li, idi, em, si, lane,
+                                                                         sj, sp, sid, sslot, fi, gx, gy, gz);
             }
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool ok = r2 < P.pc.rc2 && sslot[k] > si;
-            if (MINIMG || EXCL) {
-                const int idj = sid[k];
-                if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
-                if (EXCL) {
-                    const unsigned dj = (unsigned)(idj - idi + kExclWindow);
-                    if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
-                }
-            }
-            float ep = 0.f;
-            float sc = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
-            sc = ok ? sc : 0.0f;
-            fx = fmaf(sc, dx, fx);
-            fy = fmaf(sc, dy, fy);
-            fz = fmaf(sc, dz, fz);
-            gx = fmaf(-sc, dx, gx);
-            gy = fmaf(-sc, dy, gy);
-            gz = fmaf(-sc, dz, gz);
-            if (ENERGY) e += ok ? ep : 0.0f;
-            gx = __shfl_sync(kFullB, gx, src);
-            gy = __shfl_sync(kFullB, gy, src);
-            gz = __shfl_sync(kFullB, gz, src);
+            if (!fast)
+                group_pairs<ELEC, ENERGY, EXCL, MINIMG, false, false>(B, P, U, xi, li, idi, em, si, lane,
+                                                                      sj, sp, sid, sslot, fi, gx, gy, gz);
         }
-        if (sjl >= 0) {  // lane l now holds staged slot l's j force
-            atomicAdd((unsigned long long*)&fx_acc[sjl], (unsigned long long)f2fix(gx));
-            atomicAdd((unsigned long long*)&fx_acc[B.np + sjl], (unsigned long long)f2fix(gy));
-            atomicAdd((unsigned long long*)&fx_acc[2 * B.np + sjl], (unsigned long long)f2fix(gz));
+        if (sjl >= 0) {  // lane l holds the j force of the slot it staged
+            atomicAdd((unsigned long long*)&jacc[sjl], (unsigned long long)f2fix(gx));
+            atomicAdd((unsigned long long*)&jacc[B.np + sjl], (unsigned long long)f2fix(gy));
+            atomicAdd((unsigned long long*)&jacc[2 * B.np + sjl], (unsigned long long)f2fix(gz));
         }
         __syncwarp();
     }
-    return make_float4(fx, fy, fz, e);
+    return fi;
 }
 
 // Non-bonded forces: one warp per i tile, the variant chosen by the tile's flags.
@@ -429,11 +472,12 @@ __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __re
     const int t = blockIdx.x * 4 + w;
     if (t >= B.nt) return;
     const int fl = B.tflag[(size_t)r * B.nt + t];
+    const bool pure = (fl & 4) != 0;
     float4 f;
     switch (fl & 3) {
-        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w], sslot[w]); break;
-        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w], sslot[w]); break;
-        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, t, lane, sj[w], sp[w], sid[w], sslot[w]); break;
+        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, t, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
+        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, t, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
+        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, t, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
     }
     B.fnb[(size_t)r * B.np + t * 32 + lane] = f;
 }
@@ -725,7 +769,7 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
                             cudaStream_t s) {
     k_box_sort<<<nr, 1024, 0, s>>>(B, topo, st, r0, auto_ok);
     const dim3 gt((B.nt + 3) / 4, nr);
-    k_box_tiles<<<gt, 128, 0, s>>>(B, r0);
+    k_box_tiles<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_list<<<gt, 128, 0, s>>>(B, st, r0);
 #define PAIRS(E)                                                                                \
     switch (elec) {                                                                             \

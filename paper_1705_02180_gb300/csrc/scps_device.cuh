@@ -211,18 +211,30 @@ struct PairConst {
     float krf, crf;  // reaction field: k_rf, c_rf
 };
 
+// LJ constants of one pair: sigma^2, 24 eps, and (sigma / r_c)^6 with the
+// force term at r_c that the shifted force needs.
+struct LJPair {
+    float sig2, eps24, c6, a_ljc;
+};
+
+__device__ __forceinline__ LJPair lj_pair(float sig, float eps24, const PairConst& pc) {
+    LJPair q;
+    q.sig2 = sig * sig;
+    q.eps24 = eps24;
+    const float c2 = q.sig2 * pc.inv_rc2;
+    q.c6 = c2 * c2 * c2;
+    q.a_ljc = eps24 * q.c6 * fmaf(2.0f, q.c6, -1.0f);  // 24 eps (2 c^12 - c^6) at r_c
+    return q;
+}
+
 template <int ELEC, bool ENERGY>
-__device__ __forceinline__ float pair_s(float r2, float sig, float eps24, float qq,
-                                        const PairConst& pc, float* e) {
+__device__ __forceinline__ float pair_s_lj(float r2, const LJPair& q, float qq, const PairConst& pc,
+                                           float* e) {
     const float inv_r = rsqrtf(r2);
     const float inv_r2 = inv_r * inv_r;
-    const float sig2 = sig * sig;
-    const float s2 = sig2 * inv_r2;
+    const float s2 = q.sig2 * inv_r2;
     const float s6 = s2 * s2 * s2;
-    const float a_lj = eps24 * s6 * fmaf(2.0f, s6, -1.0f);    // 24 eps (2 s^12 - s^6)
-    const float c2 = sig2 * pc.inv_rc2;
-    const float c6 = c2 * c2 * c2;
-    const float a_ljc = eps24 * c6 * fmaf(2.0f, c6, -1.0f);   // same at r_c
+    const float a_lj = q.eps24 * s6 * fmaf(2.0f, s6, -1.0f);  // 24 eps (2 s^12 - s^6)
     // -phi'(r)/r (coulomb part) and -phi'(r_c)
     float cr, cc;
     if (ELEC == ELEC_DDIEL) {        // phi = (qq/2) / r^2, qq = 2 f q_i q_j / k_dd
@@ -239,12 +251,12 @@ __device__ __forceinline__ float pair_s(float r2, float sig, float eps24, float 
         cc = 0.0f;
     }
     // s = phi'(r)/r - phi'(rc)/r = -(a_lj inv_r2 + cr) + (a_ljc / rc + cc) inv_r
-    const float s = fmaf(fmaf(a_ljc, pc.inv_rc, cc), inv_r, -fmaf(a_lj, inv_r2, cr));
+    const float s = fmaf(fmaf(q.a_ljc, pc.inv_rc, cc), inv_r, -fmaf(a_lj, inv_r2, cr));
     if (ENERGY) {
         // phi_sf(r) = phi(r) - phi(rc) + (r - rc) * (-phi'(rc))
         const float r = r2 * inv_r;
-        const float e_lj = eps24 * (1.0f / 6.0f) * (s6 * s6 - s6);
-        const float e_ljc = eps24 * (1.0f / 6.0f) * (c6 * c6 - c6);
+        const float e_lj = q.eps24 * (1.0f / 6.0f) * (s6 * s6 - s6);
+        const float e_ljc = q.eps24 * (1.0f / 6.0f) * (q.c6 * q.c6 - q.c6);
         float ec, ecc;
         if (ELEC == ELEC_DDIEL) {
             ec = 0.5f * qq * inv_r2;
@@ -259,9 +271,15 @@ __device__ __forceinline__ float pair_s(float r2, float sig, float eps24, float 
             ec = 0.0f;
             ecc = 0.0f;
         }
-        *e = (e_lj - e_ljc) + (ec - ecc) + (r - pc.rc) * fmaf(a_ljc, pc.inv_rc, cc);
+        *e = (e_lj - e_ljc) + (ec - ecc) + (r - pc.rc) * fmaf(q.a_ljc, pc.inv_rc, cc);
     }
     return s;
+}
+
+template <int ELEC, bool ENERGY>
+__device__ __forceinline__ float pair_s(float r2, float sig, float eps24, float qq,
+                                        const PairConst& pc, float* e) {
+    return pair_s_lj<ELEC, ENERGY>(r2, lj_pair(sig, eps24, pc), qq, pc, e);
 }
 
 }  // namespace scps

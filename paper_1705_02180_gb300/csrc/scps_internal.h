@@ -103,12 +103,14 @@ struct BoxDev {
     float4* pos_ref;  // positions at the last rebuild
     float4* tlo;      // [replica][nt] tile boxes
     float4* thi;
-    float4* clo;      // [replica][4 nt] boxes of the 8-slot j clusters
+    float4* clo;      // [replica][4 nt] boxes of the 8-slot j clusters (clo.w: 1 = reference LJ only)
     float4* chi;
-    uint32_t* nbr;    // [replica][nt][max_nbr]: j cluster | periodic shift << 24 (2 bits per axis)
+    uint32_t* nbr;    // [replica][nt][max_nbr]: j cluster | periodic shift << 24 (2 bits per
+                      // axis) | 1 << 30 when the cluster holds only reference-LJ atoms
     int* nnbr;        // [replica][nt]
     int* tflag;       // [replica][nt]: 1 = tile holds chain atoms, 2 = a listed cluster needs
-                      // the minimum image per pair (its shift is not the same for all pairs)
+                      // the minimum image per pair (its shift is not the same for all pairs),
+                      // 4 = all its atoms have the reference LJ parameters (the last atom's)
     int* need;        // [replica] rebuild flag
     int* since;       // [replica] evaluations since the last rebuild
     unsigned* maxd2;  // [replica] largest squared displacement since then (float bits)
