@@ -53,93 +53,96 @@ __device__ __forceinline__ int warp_rank(float key, int lane, bool member, unsig
 
 }  // namespace
 
-// Rebuild (one CTA of 1024 threads per replica): decide, wrap, sort into
-// padded column tiles, order each tile into j clusters.
-__global__ void __launch_bounds__(kSortThreads) k_box_sort(BoxDev B, const TopoDev* __restrict__ topo,
-                                                          StateDev st, int r0, int auto_ok) {
-    __shared__ int cnt[kNumKeys];
-    __shared__ int col_first[kMaxCols + 1];  // compact position of each column's first atom
-    __shared__ int col_tile[kMaxCols + 1];   // first tile of each column
-    __shared__ int wtot[32];
+// Rebuild, step 1a (one CTA per replica): decide; on a rebuild clear the key
+// counts and the bookkeeping of the displacement test.
+__global__ void k_box_decide(BoxDev B, StateDev st, int r0, int auto_ok) {
     __shared__ int decide;
     const int r = blockIdx.x + r0;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         const float d2 = __uint_as_float(B.maxd2[r]);
         decide = st.status[r] == 0 &&
                  (B.need[r] || (auto_ok && (B.since[r] >= B.rebuild_every || d2 >= B.skin2_quarter)));
     }
     __syncthreads();
+    if (threadIdx.x == 0) B.need[r] = decide;  // the later rebuild kernels run iff set
     if (!decide) return;
-    const TopoDev tp = *topo;
-    const size_t base = (size_t)r * B.np;
-    float4* pos = B.pos + base;
-    float4* vel = B.vel + base;
-    int* id = B.id + base;
-    int* key = B.key + base;
-    int* slot_of = B.slot_of + (size_t)r * B.n_atoms;
-    float4* pos2 = B.pos2 + base;
-    float4* vel2 = B.vel2 + base;
-    int* id2 = B.id2 + base;
-    const int ncol = B.ncol, nz = B.nz, ncols = ncol * ncol;
-    for (int k = tid; k < kNumKeys; k += blockDim.x) cnt[k] = 0;
-    for (int s = tid; s < B.np; s += blockDim.x) id2[s] = -1;
-    __syncthreads();
-    const float cs = (float)ncol * B.invL, zs = (float)nz * B.invL;
-    for (int s = tid; s < B.np; s += blockDim.x) {
-        const int a = id[s];
-        if (a < 0) continue;
-        float4 p = pos[s];
-        p.x = wrapc(p.x, B.L, B.invL);
-        p.y = wrapc(p.y, B.L, B.invL);
-        p.z = wrapc(p.z, B.L, B.invL);
-        pos[s] = p;
-        const int qx = min((int)(p.x * cs), ncol - 1), qy = min((int)(p.y * cs), ncol - 1),
-                  qz = min((int)(p.z * zs), nz - 1);
-        const int k = (qx * ncol + qy) * nz + qz;
-        key[s] = k;
-        atomicAdd(&cnt[k], 1);
+    int* hist = B.hist + (size_t)r * kNumKeys;
+    for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) hist[k] = 0;
+    if (threadIdx.x == 0) {
+        B.since[r] = 0;
+        B.maxd2[r] = 0u;
     }
-    __syncthreads();
-    // exclusive scan of the key counts (kNumKeys / 1024 keys per thread)
-    {
-        constexpr int kPer = kNumKeys / kSortThreads;
-        int loc[kPer], sum = 0;
-        const int k0 = tid * kPer;
+}
+
+// Rebuild, step 1b (slots): wrap into the box, key = (column, z bin), count keys.
+__global__ void k_box_key(BoxDev B, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B.np) return;
+    const size_t base = (size_t)r * B.np;
+    B.id2[base + s] = -1;
+    const int a = B.id[base + s];
+    if (a < 0) return;
+    float4 p = B.pos[base + s];
+    p.x = wrapc(p.x, B.L, B.invL);
+    p.y = wrapc(p.y, B.L, B.invL);
+    p.z = wrapc(p.z, B.L, B.invL);
+    B.pos[base + s] = p;
+    const float cs = (float)B.ncol * B.invL, zs = (float)B.nz * B.invL;
+    const int qx = min((int)(p.x * cs), B.ncol - 1), qy = min((int)(p.y * cs), B.ncol - 1),
+              qz = min((int)(p.z * zs), B.nz - 1);
+    const int k = (qx * B.ncol + qy) * B.nz + qz;
+    B.key[base + s] = k;
+    atomicAdd(&B.hist[(size_t)r * kNumKeys + k], 1);
+}
+
+// Rebuild, step 1c (one CTA of 1024 threads per replica): exclusive scan of the
+// key counts (they become running cursors); first compact position and first
+// tile of every column (each column starts a tile).
+__global__ void __launch_bounds__(kSortThreads) k_box_scan(BoxDev B, int r0) {
+    __shared__ int wtot[32];
+    const int r = blockIdx.x + r0;
+    if (!B.need[r]) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    int* hist = B.hist + (size_t)r * kNumKeys;
+    int* col_first = B.colinfo + (size_t)r * 2 * (kMaxCols + 1);
+    int* col_tile = col_first + kMaxCols + 1;
+    constexpr int kPer = kNumKeys / kSortThreads;
+    int loc[kPer], sum = 0;
+    const int k0 = tid * kPer;
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            loc[q] = cnt[k0 + q];
-            sum += loc[q];
-        }
-        int x = sum;
+    for (int q = 0; q < kPer; ++q) {
+        loc[q] = hist[k0 + q];
+        sum += loc[q];
+    }
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullB, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? wtot[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFullB, x, o);
-            if (lane >= o) x += y;
+            const int y = __shfl_up_sync(kFullB, t, o);
+            if (lane >= o) t += y;
         }
-        if (lane == 31) wtot[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int t = lane < nw ? wtot[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFullB, t, o);
-                if (lane >= o) t += y;
-            }
-            wtot[lane] = t;
-        }
-        __syncthreads();
-        int run = (warp > 0 ? wtot[warp - 1] : 0) + x - sum;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            cnt[k0 + q] = run;  // becomes the running cursor of key k0+q
-            run += loc[q];
-        }
+        wtot[lane] = t;
     }
     __syncthreads();
-    // columns: first compact position and first tile (each column starts a tile)
-    for (int c = tid; c <= ncols; c += blockDim.x) col_first[c] = c < ncols ? cnt[c * nz] : B.n_atoms;
+    int run = (warp > 0 ? wtot[warp - 1] : 0) + x - sum;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        hist[k0 + q] = run;
+        run += loc[q];
+    }
+    __syncthreads();
+    const int ncols = B.ncol * B.ncol;
+    for (int c = tid; c <= ncols; c += blockDim.x) col_first[c] = c < ncols ? hist[c * B.nz] : B.n_atoms;
     __syncthreads();
     if (tid == 0) {
         int t = 0;
@@ -149,74 +152,96 @@ __global__ void __launch_bounds__(kSortThreads) k_box_sort(BoxDev B, const TopoD
         }
         col_tile[ncols] = t;  // <= nt by the capacity ceil(n/32) + ncol^2
     }
-    __syncthreads();
-    // scatter: slots within a key come in arbitrary order from the atomics ...
-    for (int a = tid; a < B.n_atoms; a += blockDim.x) {
-        const int s = slot_of[a];
-        const int k = key[s];
-        const int p = atomicAdd(&cnt[k], 1);
-        const int c = k / nz;
-        const int dst = col_tile[c] * 32 + (p - col_first[c]);
-        pos2[dst] = pos[s];
-        vel2[dst] = vel[s];
-        id2[dst] = a;
-    }
-    __syncthreads();
-    // ... and are then put in atom-id order, one key per thread (a key holds a few
-    // atoms); cnt[k] now ends key k, so key k spans [cnt[k - 1], cnt[k])
-    for (int k = tid; k < ncols * nz; k += blockDim.x) {
-        const int lo = k > 0 ? cnt[k - 1] : 0, hi = cnt[k];
-        if (hi - lo < 2) continue;
-        const int c = k / nz;
-        const int off = col_tile[c] * 32 - col_first[c];
-        for (int q = lo + 1; q < hi; ++q) {  // insertion sort by id
-            const int ia = id2[off + q];
-            const float4 pa = pos2[off + q], va = vel2[off + q];
-            int u = q - 1;
-            while (u >= lo && id2[off + u] > ia) {
-                id2[off + u + 1] = id2[off + u];
-                pos2[off + u + 1] = pos2[off + u];
-                vel2[off + u + 1] = vel2[off + u];
-                --u;
-            }
-            id2[off + u + 1] = ia;
-            pos2[off + u + 1] = pa;
-            vel2[off + u + 1] = va;
+}
+
+// Rebuild, step 1d (atoms): scatter into the padded column layout. Within a key
+// the atomics give an arbitrary order, which step 1e replaces by atom-id order.
+__global__ void k_box_scatter(BoxDev B, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= B.n_atoms) return;
+    const size_t base = (size_t)r * B.np;
+    const int* col_first = B.colinfo + (size_t)r * 2 * (kMaxCols + 1);
+    const int* col_tile = col_first + kMaxCols + 1;
+    const int s = B.slot_of[(size_t)r * B.n_atoms + a];
+    const int k = B.key[base + s];
+    const int p = atomicAdd(&B.hist[(size_t)r * kNumKeys + k], 1);
+    const int c = k / B.nz;
+    const int dst = col_tile[c] * 32 + (p - col_first[c]);
+    B.pos2[base + dst] = B.pos[base + s];
+    B.vel2[base + dst] = B.vel[base + s];
+    B.id2[base + dst] = a;
+}
+
+// Rebuild, step 1e (keys): put each key's slots in atom-id order (a key holds a
+// few atoms); hist[k] now ends key k, so key k spans [hist[k - 1], hist[k]).
+__global__ void k_box_keyorder(BoxDev B, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B.ncol * B.ncol * B.nz) return;
+    const int* hist = B.hist + (size_t)r * kNumKeys;
+    const int lo = k > 0 ? hist[k - 1] : 0, hi = hist[k];
+    if (hi - lo < 2) return;
+    const int* col_first = B.colinfo + (size_t)r * 2 * (kMaxCols + 1);
+    const int* col_tile = col_first + kMaxCols + 1;
+    const int c = k / B.nz;
+    const size_t off = (size_t)r * B.np + col_tile[c] * 32 - col_first[c];
+    int* id2 = B.id2 + off;
+    float4* pos2 = B.pos2 + off;
+    float4* vel2 = B.vel2 + off;
+    for (int q = lo + 1; q < hi; ++q) {  // insertion sort by id
+        const int ia = id2[q];
+        const float4 pa = pos2[q], va = vel2[q];
+        int u = q - 1;
+        while (u >= lo && id2[u] > ia) {
+            id2[u + 1] = id2[u];
+            pos2[u + 1] = pos2[u];
+            vel2[u + 1] = vel2[u];
+            --u;
         }
+        id2[u + 1] = ia;
+        pos2[u + 1] = pa;
+        vel2[u + 1] = va;
     }
-    __syncthreads();
-    // inside each tile: two halves of 16 by x, each ordered by y (padding last)
-    for (int t = warp; t < B.nt; t += nw) {
-        const int s0 = t * 32 + lane;
-        const int a = id2[s0];
-        const bool valid = a >= 0;
-        const float4 p = pos2[s0];
-        const float4 v = vel2[s0];
-        const float kx = valid ? p.x : 3.0e38f, ky = valid ? p.y : 3.0e38f;
-        const int rx = warp_rank(kx, lane, true, kFullB);
-        const unsigned upper = __ballot_sync(kFullB, rx >= 16);
-        const bool hi = rx >= 16;
-        const int ry = warp_rank(ky, lane, true, hi ? upper : ~upper);
-        const int s = t * 32 + (hi ? 16 : 0) + ry;
-        if (valid) {
-            pos[s] = p;
-            vel[s] = v;
-            id[s] = a;
-            B.pos_ref[base + s] = p;
-            B.par[base + s] = tp.lj[a];
-            slot_of[a] = s;
-        } else {
-            pos[s] = make_float4(1.0e5f * (float)(s + 1), 0.f, 0.f, 0.f);
-            vel[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-            id[s] = -1;
-            B.pos_ref[base + s] = pos[s];
-            B.par[base + s] = make_float2(0.f, 0.f);
-        }
-    }
-    if (tid == 0) {
-        B.need[r] = 1;  // the tile and list kernels of this step run
-        B.since[r] = 0;
-        B.maxd2[r] = 0u;
+}
+
+// Rebuild, step 1f (one warp per tile): inside each tile, two halves of 16 by x,
+// each ordered by y (padding last), so that slots 8q .. 8q+7 form compact
+// clusters; final slot arrays, reference positions, LJ parameters, slot_of.
+__global__ void k_box_subsort(BoxDev B, const TopoDev* __restrict__ topo, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= B.nt) return;
+    const int lane = threadIdx.x & 31;
+    const size_t base = (size_t)r * B.np;
+    const int s0 = t * 32 + lane;
+    const int a = B.id2[base + s0];
+    const bool valid = a >= 0;
+    const float4 p = B.pos2[base + s0];
+    const float4 v = B.vel2[base + s0];
+    const float kx = valid ? p.x : 3.0e38f, ky = valid ? p.y : 3.0e38f;
+    const int rx = warp_rank(kx, lane, true, kFullB);
+    const unsigned upper = __ballot_sync(kFullB, rx >= 16);
+    const bool hi = rx >= 16;
+    const int ry = warp_rank(ky, lane, true, hi ? upper : ~upper);
+    const int s = t * 32 + (hi ? 16 : 0) + ry;
+    if (valid) {
+        B.pos[base + s] = p;
+        B.vel[base + s] = v;
+        B.id[base + s] = a;
+        B.pos_ref[base + s] = p;
+        B.par[base + s] = topo->lj[a];
+        B.slot_of[(size_t)r * B.n_atoms + a] = s;
+    } else {
+        const float4 far = make_float4(1.0e5f * (float)(s + 1), 0.f, 0.f, 0.f);
+        B.pos[base + s] = far;
+        B.vel[base + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        B.id[base + s] = -1;
+        B.pos_ref[base + s] = far;
+        B.par[base + s] = make_float2(0.f, 0.f);
     }
 }
 
@@ -767,8 +792,13 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
                             const RunParams& P, int r0, int nr, int elec, int ncon_max,
                             bool energy, int do_ratchet, int count_step, int auto_ok,
                             cudaStream_t s) {
-    k_box_sort<<<nr, 1024, 0, s>>>(B, topo, st, r0, auto_ok);
+    k_box_decide<<<nr, 256, 0, s>>>(B, st, r0, auto_ok);
+    k_box_key<<<dim3((B.np + 255) / 256, nr), 256, 0, s>>>(B, r0);
+    k_box_scan<<<nr, kSortThreads, 0, s>>>(B, r0);
+    k_box_scatter<<<dim3((B.n_atoms + 255) / 256, nr), 256, 0, s>>>(B, r0);
+    k_box_keyorder<<<dim3((B.ncol * B.ncol * B.nz + 255) / 256, nr), 256, 0, s>>>(B, r0);
     const dim3 gt((B.nt + 3) / 4, nr);
+    k_box_subsort<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_tiles<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_list<<<gt, 128, 0, s>>>(B, st, r0);
 #define PAIRS(E)                                                                                \

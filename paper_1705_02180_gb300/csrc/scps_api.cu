@@ -458,6 +458,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.pos2, np);
         BALLOC(B.vel2, np);
         BALLOC(B.key, np);
+        BALLOC(B.hist, (size_t)Rs * 8192);
+        BALLOC(B.colinfo, (size_t)Rs * 2 * 257);
         BALLOC(B.pos_ref, np);
         BALLOC(B.slot_of, (size_t)Rs * B.n_atoms);
         BALLOC(B.tlo, (size_t)Rs * B.nt);

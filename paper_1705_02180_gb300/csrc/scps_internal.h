@@ -100,6 +100,8 @@ struct BoxDev {
     float4* vel2;
     int* slot_of;     // [replica][n_atoms]
     int* key;
+    int* hist;        // [replica][8192] key counts, then running cursors (rebuild)
+    int* colinfo;     // [replica][2][257] first compact position and first tile per column
     float4* pos_ref;  // positions at the last rebuild
     float4* tlo;      // [replica][nt] tile boxes
     float4* thi;
