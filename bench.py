@@ -159,31 +159,45 @@ def cpu_baseline(c, R, budget_s=15.0):
                      steps)
     dt = time.perf_counter() - t0
     return {"value": nrep * c.n_atoms * steps / dt, "unit": "atom-steps/s", "cores": threads,
-            "kind": "oracle",
+            "kind": "oracle", "atom_steps": nrep * c.n_atoms * steps, "seconds": dt,
             "sample": f"{nrep} replicas x {steps} steps of the {c.n_atoms}-atom chain "
                       f"(FP64 C oracle, OpenMP over replicas), {dt:.1f} s"}
 
 
+def chain_workload_name(c, R):
+    return (f"{R} replicas x {c.n_atoms}-atom synthetic chain rMD (Fip35-scale), "
+            f"dt 2 fs, 300 K, gamma 1/ps, k_R 1e-4")
+
+
 def run_reference(args):
+    """The oracle as it stands, timed on the host cores on this arm's workload: W untimed
+    and K timed bounded samples (each a few replicas x a few steps, sized so that the
+    whole run stays within about a minute)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     c, R = workload(args)
-    vals = []
-    sample = None
-    for _ in range(max(1, min(args.steps, 3))):
-        cb = cpu_baseline(c, R, budget_s=10.0)
-        vals.append(cb["value"])
+    K, W = max(1, args.steps), max(0, args.warmup)
+    budget = max(0.3, 60.0 / (K + W))
+    for _ in range(W):
+        cpu_baseline(c, R, budget_s=budget)
+    work, secs, sample = 0.0, 0.0, None
+    for _ in range(K):
+        cb = cpu_baseline(c, R, budget_s=budget)
+        work += cb["atom_steps"]
+        secs += cb["seconds"]
         sample = cb
-    v = float(np.median(vals))
+    v = work / secs
     line = {"impl": "reference", "metric": "biased-Langevin atom-steps/s", "value": v,
-            "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": len(vals),
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{R} x {c.n_atoms}-atom chain rMD, dt 2 fs, 300 K",
-                       "md_steps_per_call": args.md_steps_per_call},
+            "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": K,
+            "warmup": W, "ms_per_step": secs / K * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": chain_workload_name(c, R), "replicas_per_gpu": R,
+                       "atoms": c.n_atoms, "md_steps_per_call": args.md_steps_per_call,
+                       "native_contacts": int(len(c.contacts))},
             "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": sample["cores"],
-                             "kind": "oracle", "sample": sample["sample"]},
+                             "kind": "oracle",
+                             "sample": f"{K} samples, each {sample['sample']}"},
             "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -396,8 +410,7 @@ def main():
               "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64fix+f64z",
               "data": "synthetic",
-              "config": {"workload": f"{R} replicas x {n}-atom synthetic chain rMD (Fip35-scale), "
-                                     f"dt 2 fs, 300 K, gamma 1/ps, k_R 1e-4",
+              "config": {"workload": chain_workload_name(c, R),
                          "replicas_per_gpu": R, "atoms": n, "md_steps_per_call": spc,
                          "md_steps_total": spc * args.steps, "native_contacts": int(len(c.contacts)),
                          "l2": "flushed between calls (512 MB write)",
@@ -451,7 +464,8 @@ def main():
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                          "calls": reps_e2e}
     if rank == 0 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(c, R)
+        cb = cpu_baseline(c, R)
+        result["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     sysm.close()
     if dist:
         dist.barrier()
