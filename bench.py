@@ -248,6 +248,7 @@ def run_extra(args):
                        gamma=1.0, kT=KT_300, seed=SEED, threads=args.threads,
                        steps_per_graph=spc)
         s.set_contact_bias([c.contacts for c in chains], [c.x_native for c in chains], k_R=1e-4)
+        tune = s.autotune(probe_steps=100) if args.threads == 0 else None
         durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
         atoms = int(sum(chains[t].n_atoms for t in reps))
         info = s.info()
@@ -256,7 +257,9 @@ def run_extra(args):
                "config": {"workload": "512 replicas: 171 x 304 + 171 x 560 + 170 x 1200 atoms, "
                                       "one resident launch, dt 2 fs, 300 K, k_R 1e-4",
                           "atoms": atoms, "md_steps_per_call": spc,
-                          "threads_per_cta": info["threads"], "cluster": info["cluster_size"]},
+                          "threads_per_cta": info["threads"], "cluster": info["cluster_size"],
+                          "plan": ["one launch", "one launch per size class"][info["plan"]],
+                          "autotune": tune},
                "gpu_launches": int(info["graph_nodes_last_call"]) * K, "clocks": clk}
         s.close()
     elif args.workload == "box":

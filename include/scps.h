@@ -146,7 +146,24 @@ typedef struct {
     int64_t graph_nodes_last_call;      /* kernel launches enqueued by the last step call */
     int64_t pair_checks_per_step;       /* tile-pair slots evaluated in the last step call */
     size_t device_bytes;                /* device memory held by the system */
+    int32_t launch_groups;              /* resident form: launches per step call chunk */
+    int32_t plan;                       /* resident form: SCPS_PLAN_* */
 } scps_info;
+
+/* launch plans of the resident form */
+enum { SCPS_PLAN_ONE_LAUNCH = 0,        /* one launch, replicas by decreasing size */
+       SCPS_PLAN_PER_SIZE_CLASS = 1 };  /* one launch per size class (tile-rounded atom
+                                           count), shared memory sized per class, the
+                                           launches running side by side */
+
+typedef struct {
+    int32_t plan;                       /* chosen SCPS_PLAN_* */
+    int32_t cluster_size, threads;      /* chosen CTAs per replica and threads per CTA */
+    int32_t candidates;                 /* configurations timed (0 when taken from the cache) */
+    int32_t from_cache;                 /* 1: the choice came from the process-wide cache */
+    double us_per_step;                 /* probe time per step of the choice */
+    double us_per_step_initial;         /* probe time per step of the configuration before */
+} scps_tune_result;
 
 typedef struct scps_system scps_system;
 
@@ -208,6 +225,16 @@ int scps_set_state(scps_system* s, const double* x, const double* v, const doubl
 int scps_get_status(scps_system* s, int32_t* per_replica);
 
 int scps_get_info(const scps_system* s, scps_info* info);
+
+/* Autotuner of the resident form (chain replicas): times the launch plans
+ * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} on the
+ * system itself, probe_steps steps each from the current state (restored after
+ * every probe; no frames are saved while probing), and keeps the fastest. The
+ * choice is cached per process under (SM count, electrostatics, bias kind,
+ * multiset of replica sizes); use_cache != 0 takes a cached choice without
+ * probing. The plan changes only which CTA runs which replica, so trajectories
+ * are bit-identical under every choice. Synchronous; out may be NULL. */
+int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out);
 
 /* Philox4x32-10 blocks on the device, for checking the noise stream:
  * ctr: device uint32 n x 4, key: two uint32 words, out: device uint32 n x 4. */

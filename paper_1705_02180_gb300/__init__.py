@@ -58,13 +58,22 @@ class Info(C.Structure):
                 ("cluster_size", C.c_int32), ("threads", C.c_int32),
                 ("steps_per_graph", C.c_int32), ("kernels_per_step_call", C.c_int32),
                 ("graph_nodes_last_call", C.c_int64), ("pair_checks_per_step", C.c_int64),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("launch_groups", C.c_int32), ("plan", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("plan", C.c_int32), ("cluster_size", C.c_int32), ("threads", C.c_int32),
+                ("candidates", C.c_int32), ("from_cache", C.c_int32), ("us_per_step", C.c_double),
+                ("us_per_step_initial", C.c_double)]
+
+
+PLAN_ONE_LAUNCH, PLAN_PER_SIZE_CLASS = 0, 1
 
 
 EXPORTS = ["scps_create_system", "scps_destroy_system", "scps_set_bias", "scps_step_replicas",
            "scps_energy_forces", "scps_hvp", "scps_collect_paths", "scps_get_state",
            "scps_set_state", "scps_get_status", "scps_get_info", "scps_philox4x32_10",
-           "scps_energy_forces_noalloc", "scps_last_error"]
+           "scps_energy_forces_noalloc", "scps_autotune", "scps_last_error"]
 
 _lib = None
 
@@ -95,6 +104,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "scps_get_status": [_P, _P], "scps_get_info": [_P, _P],
         "scps_philox4x32_10": [i64, _P, u32, u32, _P, _P],
         "scps_energy_forces_noalloc": [_P, i32, _P, _P, _P, _P],
+        "scps_autotune": [_P, i32, i32, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -279,6 +289,13 @@ class System:
             out.append(dict(frames=fr[:c], z=z[k, :c], zmin=zmin[k, :c], epot=epot[k, :c],
                             T=T[k, :c]))
         return out
+
+    def autotune(self, probe_steps=100, use_cache=True):
+        """Times the resident launch plans, cluster sizes and CTA widths on this system
+        (state restored after every probe) and keeps the fastest; returns the choice."""
+        t = TuneResult()
+        check(load().scps_autotune(self.h, int(probe_steps), 1 if use_cache else 0, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in TuneResult._fields_}
 
     def info(self):
         i = Info()

@@ -33,7 +33,8 @@ constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per 
 struct Shared {
     float4* xq;         // (x, y, z, qs)
     float4* v;          // velocities (w: 1/m)
-    float4* xi;         // noise of the next O half step per atom (sd times Gaussian numbers)
+    float4* xi;         // noise of the next O half step per atom (sd times Gaussian numbers);
+                        // w: the atom's |F_bias|^2 / m of the step just closed
     float2* lj;         // (sigma/2, sqrt(24 eps))
     long long* Fp[2];   // 3 x nta force partials of this CTA, by parity of the evaluated step
     long long* Gp[2];   // 3 x nta partials of sum_p (C - C0) C'(u) (x_p - x_i) over the native
@@ -55,7 +56,6 @@ struct Scalars {
     double zm, z, factor, epot, T;
     long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity
     long long red_e[2][32];  // per-warp shares of the potential energy (units of 2^-20)
-    float red_t[32];         // per-warp shares of sum |F_bias|^2 / m
 };
 
 __device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int ncon_max) {
@@ -303,7 +303,11 @@ __device__ __forceinline__ void noise_chunk(const Shared& sm, const TopoDev& tp,
                                        P.key1);
         const float4 g = normals4_f32(rb);
         const float sd = tp.noise_sd[i];
-        sm.xi[i] = make_float4(sd * g.x, sd * g.y, sd * g.z, 0.f);
+        // xyz only: w holds the atom's bias-functional term, which warp 0 may still be
+        // summing while the next evaluation starts
+        sm.xi[i].x = sd * g.x;
+        sm.xi[i].y = sd * g.y;
+        sm.xi[i].z = sd * g.z;
     }
 }
 
@@ -528,9 +532,9 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
            RunParams P, int nta, int ntp_max, int ncon_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
-    const int r = blockIdx.x / CL;
+    const RepDev rep = reps[blockIdx.x / CL];  // this launch's replicas, in any order
+    const int r = rep.index;
     const int rank = cta_rank<CL>();
-    const RepDev rep = reps[r];
     const TopoDev tp = topos[rep.topo];
     Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
     const int n = tp.n_atoms, nt = tp.n_tiles;
@@ -589,7 +593,6 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             const bool bias = sc.bias_on;
             const bool save = do_b && save_phase == 0;
             const float kb = -(float)sc.factor * 4.0f * P.inv_r0sq;  // F_bias = kb G
-            float tb = 0.f;
             for (int base = 0; base < nta; base += blockDim.x) {
                 const int i = base + tid;
                 const bool valid = i < n;
@@ -603,7 +606,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                     if (bias) {
                         const float bx = kb * fix2f(a.g[0]), by = kb * fix2f(a.g[1]),
                                     bz = kb * fix2f(a.g[2]);
-                        if (do_b) tb += (bx * bx + by * by + bz * bz) * im;
+                        if (do_b) sm.xi[i].w = (bx * bx + by * by + bz * bz) * im;
                         fx += bx;
                         fy += by;
                         fz += bz;
@@ -647,18 +650,15 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                     warp_boxes(sm, (base >> 5) + warp, lo, hi, lane);
                 }
             }
-            if (bias && do_b) {
-                tb = warp_sum_f(tb);
-                if (lane == 0) sc.red_t[warp] = tb;
-            }
             if (tid == 0) sc.flag[nb] = 0;
             __syncthreads();
+            if (warp == 0 && do_b && bias) {  // atoms in a fixed order, whatever the CTA shape
+                float tsum = 0.f;
+                for (int i = lane; i < n; i += 32) tsum += sm.xi[i].w;
+                tsum = warp_sum_f(tsum);
+                if (lane == 0) sc.T += (double)P.dt / P.gamma * (double)tsum;
+            }
             if (tid == 0 && do_b) {
-                if (bias) {
-                    float tsum = 0.f;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += sc.red_t[w];
-                    sc.T += (double)P.dt / P.gamma * (double)tsum;
-                }
                 if (save) {
                     if (rank == 0) {
                         const long long fi = (long long)r * P.max_frames + slot;

@@ -1,12 +1,14 @@
 // C ABI of the rMD engine (include/scps.h): validation, device tables, state,
 // launch plans and CUDA graphs. All compute runs in the kernels of
 // kern_chain.cu and kern_aux.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <limits>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -101,6 +103,15 @@ struct scps_system {
     float* plain_f = nullptr;
     double* plain_d = nullptr;
     int threads = 0, cluster = 1, steps_per_graph = 0;
+    // resident form: one launch per group (groups after the first run on forked streams)
+    struct Group {
+        RepDev* d_reps = nullptr;  // this group's replicas (owned by `allocs`)
+        int count = 0, nta = 0, ntp_max = 0, cluster = 1, threads = 1024;
+    };
+    std::vector<Group> groups;
+    int plan = 0;  // 0: one launch, replicas by decreasing size; 1: one launch per size class
+    std::vector<cudaStream_t> fork_streams;
+    std::vector<cudaEvent_t> fork_events;
     int bias_kind = SCPS_BIAS_NONE;
     scps_info info{};
     size_t bytes = 0;
@@ -264,6 +275,99 @@ void drop_graphs(scps_system* s) {
     s->graph_defs.clear();
 }
 
+int tile_atoms(int n) { return ((n + kTile - 1) / kTile) * kTile; }
+
+// Launch groups of the resident form. plan 0: one group, replicas by decreasing
+// size (large replicas start first, small ones fill the last wave); plan 1: one
+// group per size class (tile-rounded atom count), each with shared memory for its
+// own size. Every group gets the given cluster size and threads per CTA.
+int set_groups(scps_system* s, int plan, int cluster, int threads) {
+    const int R = s->d.n_replicas;
+    std::vector<int> order(R);
+    for (int r = 0; r < R; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return s->topos[s->rep_topo[a]].n > s->topos[s->rep_topo[b]].n;
+    });
+    std::vector<std::vector<int>> members;
+    if (plan == 0) {
+        members.push_back(order);
+    } else {
+        int last = -1;
+        for (int r : order) {
+            const int c = tile_atoms(s->topos[s->rep_topo[r]].n);
+            if (c != last) members.emplace_back();
+            members.back().push_back(r);
+            last = c;
+        }
+    }
+    std::vector<scps_system::Group> groups;
+    for (auto& m : members) {
+        scps_system::Group g;
+        g.count = (int)m.size();
+        int na = 0;
+        for (int r : m) na = std::max(na, s->topos[s->rep_topo[r]].n);
+        g.nta = plan == 0 ? s->nta : tile_atoms(na);
+        const int nt = g.nta / kTile;
+        g.ntp_max = nt * (nt + 1) / 2;
+        g.cluster = cluster;
+        g.threads = threads;
+        std::vector<RepDev> reps(m.size());
+        for (size_t k = 0; k < m.size(); ++k) {
+            const int r = m[k];
+            reps[k] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r};
+        }
+        SCPS_CU(s->upload(&g.d_reps, reps));
+        groups.push_back(g);
+    }
+    while (s->fork_streams.size() + 1 < groups.size()) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        SCPS_CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        SCPS_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        s->fork_streams.push_back(st);
+        s->fork_events.push_back(ev);
+    }
+    if (s->fork_events.size() < groups.size()) {  // one more for the fork itself
+        cudaEvent_t ev;
+        SCPS_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        s->fork_events.push_back(ev);
+    }
+    s->groups = groups;
+    s->plan = plan;
+    s->cluster = cluster;
+    s->threads = threads;
+    drop_graphs(s);
+    return SCPS_OK;
+}
+
+// One launch per group for n_steps steps; groups after the first run on forked
+// streams that join `cs` again (also under stream capture).
+cudaError_t launch_groups(scps_system* s, const RunParams& P0, long long n_steps, cudaStream_t cs) {
+    const size_t G = s->groups.size();
+    if (G > 1) {
+        cudaError_t e = cudaEventRecord(s->fork_events[G - 1], cs);
+        for (size_t k = 1; k < G && e == cudaSuccess; ++k)
+            e = cudaStreamWaitEvent(s->fork_streams[k - 1], s->fork_events[G - 1], 0);
+        if (e != cudaSuccess) return e;
+    }
+    for (size_t k = 0; k < G; ++k) {
+        const scps_system::Group& g = s->groups[k];
+        RunParams P = P0;
+        P.n_steps = n_steps;
+        P.n_replicas = g.count;
+        cudaStream_t st = k == 0 ? cs : s->fork_streams[k - 1];
+        cudaError_t e = launch_resident(s->d.elec, g.cluster, s->d_topos, g.d_reps, s->st, P, g.nta,
+                                        g.ntp_max, s->ncon_max, g.threads, st);
+        if (e != cudaSuccess) return e;
+    }
+    for (size_t k = 1; k < G; ++k) {
+        cudaError_t e = cudaEventRecord(s->fork_events[k - 1], s->fork_streams[k - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, s->fork_events[k - 1], 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -400,7 +504,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     if (d->model == SCPS_MODEL_CHAIN) {
         std::vector<RepDev> reps(R);
         for (int r = 0; r < R; ++r)
-            reps[r] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], 0};
+            reps[r] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r};
         if (cudaMemcpy(s->d_reps, reps.data(), sizeof(RepDev) * R, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(SCPS_ERR_CUDA, "upload of the replica table failed"));
         rc = sync_topos(s);
@@ -415,6 +519,10 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         const bool one_cta_per_sm = (long long)R * s->cluster <= n_sm;
         s->threads = d->threads ? d->threads : (one_cta_per_sm ? 1024 : auto_threads(s->nta));
         s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
+        if (!s->is_box && d->exec == SCPS_EXEC_RESIDENT) {
+            rc = set_groups(s, 0, s->cluster, s->threads);
+            if (rc) return bail(rc);
+        }
     }
     if (s->is_box) {
         const scps_topology_desc& t = d->topologies[0];
@@ -514,6 +622,8 @@ int scps_destroy_system(scps_system* s) {
     if (!s) return SCPS_OK;
     drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (auto st : s->fork_streams) cudaStreamDestroy(st);
+    for (auto ev : s->fork_events) cudaEventDestroy(ev);
     for (void* p : s->allocs) cudaFree(p);
     delete s;
     return SCPS_OK;
@@ -648,7 +758,7 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
         P.n_steps = n_steps;
         std::vector<RepDev> reps(R);
         for (int r = 0; r < R; ++r) {
-            const RepDev rep{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], 0};
+            const RepDev rep{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r};
             SCPS_CU(plain_run_replica(s->d.elec, s->topos[s->rep_topo[r]].dev, s->st, r, rep, P,
                                       s->plain_f, s->plain_d, s->host_step[r], cs));
         }
@@ -664,9 +774,7 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
                 Pc.n_steps = chunk;
                 cudaGraph_t g;
                 SCPS_CU(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-                cudaError_t le = launch_resident(s->d.elec, s->cluster, s->d_topos, s->d_reps, s->st,
-                                                 Pc, s->nta, s->ntp_max, s->ncon_max, s->threads,
-                                                 s->cap_stream);
+                cudaError_t le = launch_groups(s, Pc, chunk, s->cap_stream);
                 cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
                 if (le != cudaSuccess || ce != cudaSuccess)
                     return fail(SCPS_ERR_CUDA, "graph capture failed: %s",
@@ -680,10 +788,9 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
         }
         if (rem > 0) {
             P.n_steps = rem;
-            SCPS_CU(launch_resident(s->d.elec, s->cluster, s->d_topos, s->d_reps, s->st, P, s->nta,
-                                    s->ntp_max, s->ncon_max, s->threads, cs));
+            SCPS_CU(launch_groups(s, P, rem, cs));
         }
-        launches = full + (rem > 0);
+        launches = (full + (rem > 0)) * (long long)s->groups.size();
     }
     for (int r = 0; r < R; ++r) s->host_step[r] += n_steps;
     s->info.graph_nodes_last_call = launches;
@@ -942,8 +1049,156 @@ int scps_get_info(const scps_system* s, scps_info* info) {
     info->cluster_size = s->cluster;
     info->threads = s->threads;
     info->steps_per_graph = s->steps_per_graph;
+    info->launch_groups = (int32_t)s->groups.size();
+    info->plan = s->plan;
     info->kernels_per_step_call = 1;
     info->device_bytes = s->bytes;
+    return SCPS_OK;
+}
+
+int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out) {
+    if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
+    if (s->model != SCPS_MODEL_CHAIN || s->is_box || s->d.exec != SCPS_EXEC_RESIDENT)
+        return fail(SCPS_ERR_UNSUPPORTED, "the tuner covers the resident form of chain replicas");
+    if (probe_steps < 1 || probe_steps > 100000) return fail(SCPS_ERR_INVALID_ARG, "probe_steps outside [1, 1e5]");
+    const int R = s->d.n_replicas;
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
+    // cache key: SM count, electrostatics, bias kind and the multiset of replica sizes
+    std::map<int, int> sizes;
+    for (int r = 0; r < R; ++r) sizes[s->topos[s->rep_topo[r]].n] += 1;
+    std::string key = std::to_string(n_sm) + "|" + std::to_string(s->d.elec) + "|" +
+                      std::to_string(s->bias_kind);
+    for (auto& kv : sizes) key += "|" + std::to_string(kv.first) + "x" + std::to_string(kv.second);
+    static std::mutex mu;
+    static std::map<std::string, std::vector<int>> cache;  // plan, cluster, threads
+    scps_tune_result res{};
+    res.plan = s->plan;
+    res.cluster_size = s->cluster;
+    res.threads = s->threads;
+    if (use_cache) {
+        std::vector<int> hit;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = cache.find(key);
+            if (it != cache.end()) hit = it->second;
+        }
+        if (!hit.empty()) {
+            int rc = set_groups(s, hit[0], hit[1], hit[2]);
+            if (rc) return rc;
+            res.plan = hit[0];
+            res.cluster_size = hit[1];
+            res.threads = hit[2];
+            res.from_cache = 1;
+            if (out) *out = res;
+            return SCPS_OK;
+        }
+    }
+    // snapshot of the state the probes change (no frames are saved while probing)
+    const size_t na = (size_t)s->n_atoms_total;
+    float4 *sx = nullptr, *sv = nullptr;
+    double *szm = nullptr, *sz = nullptr, *sT = nullptr;
+    long long* sstep = nullptr;
+    int* sstat = nullptr;
+    auto release = [&]() {
+        cudaFree(sx); cudaFree(sv); cudaFree(szm); cudaFree(sz); cudaFree(sT); cudaFree(sstep);
+        cudaFree(sstat);
+    };
+    cudaError_t e = cudaMalloc(&sx, sizeof(float4) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&sv, sizeof(float4) * na);
+    if (e == cudaSuccess) e = cudaMalloc(&szm, sizeof(double) * R);
+    if (e == cudaSuccess) e = cudaMalloc(&sz, sizeof(double) * R);
+    if (e == cudaSuccess) e = cudaMalloc(&sT, sizeof(double) * R);
+    if (e == cudaSuccess) e = cudaMalloc(&sstep, sizeof(long long) * R);
+    if (e == cudaSuccess) e = cudaMalloc(&sstat, sizeof(int) * R);
+    auto copy_all = [&](bool save) -> cudaError_t {
+        cudaError_t c = cudaSuccess;
+        auto cp = [&](void* a, void* b, size_t n) {
+            if (c == cudaSuccess) c = cudaMemcpyAsync(save ? a : b, save ? b : a, n, cudaMemcpyDeviceToDevice, s->cap_stream);
+        };
+        cp(sx, s->st.x, sizeof(float4) * na);
+        cp(sv, s->st.v, sizeof(float4) * na);
+        cp(szm, s->st.zm, sizeof(double) * R);
+        cp(sz, s->st.z, sizeof(double) * R);
+        cp(sT, s->st.T, sizeof(double) * R);
+        cp(sstep, s->st.step, sizeof(long long) * R);
+        cp(sstat, s->st.status, sizeof(int) * R);
+        if (c == cudaSuccess) c = cudaStreamSynchronize(s->cap_stream);
+        return c;
+    };
+    if (e == cudaSuccess) e = copy_all(true);
+    if (e != cudaSuccess) {
+        release();
+        return fail(SCPS_ERR_CUDA, "tuner snapshot failed: %s", cudaGetErrorString(e));
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    RunParams P = s->base;
+    P.save_interval = 0;
+    const int initial[3] = {s->plan, s->cluster, s->threads};
+    std::vector<std::vector<int>> cands;
+    cands.push_back({initial[0], initial[1], initial[2]});
+    const int n_plans = sizes.size() > 1 ? 2 : 1;
+    for (int plan = 0; plan < n_plans; ++plan)
+        for (int cl : {1, 2})
+            for (int th : {256, 512, 1024}) {
+                std::vector<int> c{plan, cl, th};
+                if (c != cands[0]) cands.push_back(c);
+            }
+    double best = 1e300;
+    std::vector<int> best_c = cands[0];
+    int timed = 0;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        const std::vector<int>& c = cands[k];
+        if (set_groups(s, c[0], c[1], c[2]) != SCPS_OK) continue;
+        bool fits = true;
+        for (auto& g : s->groups)
+            fits = fits && resident_smem_bytes(g.nta, g.ntp_max, s->ncon_max) <= 227 * 1024;
+        if (!fits) continue;
+        // one short untimed run (first-launch set-up), then the timed probe; state restored after each
+        cudaError_t le = launch_groups(s, P, std::max(1, probe_steps / 4), s->cap_stream);
+        if (le == cudaSuccess) le = copy_all(false);
+        if (le == cudaSuccess) le = cudaEventRecord(e0, s->cap_stream);
+        if (le == cudaSuccess) le = launch_groups(s, P, probe_steps, s->cap_stream);
+        if (le == cudaSuccess) le = cudaEventRecord(e1, s->cap_stream);
+        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+        cudaError_t re = copy_all(false);
+        if (re != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            release();
+            return fail(SCPS_ERR_CUDA, "tuner restore failed: %s", cudaGetErrorString(re));
+        }
+        if (le != cudaSuccess) {
+            (void)cudaGetLastError();  // a launch-configuration error: skip the candidate
+            continue;
+        }
+        ++timed;
+        const double us = 1e3 * ms / probe_steps;
+        if (k == 0) res.us_per_step_initial = us;
+        if (us < best) {
+            best = us;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release();
+    int rc = set_groups(s, best_c[0], best_c[1], best_c[2]);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = best_c;
+    }
+    res.plan = best_c[0];
+    res.cluster_size = best_c[1];
+    res.threads = best_c[2];
+    res.candidates = timed;
+    res.us_per_step = best;
+    if (out) *out = res;
     return SCPS_OK;
 }
 

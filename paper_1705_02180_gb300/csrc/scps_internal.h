@@ -44,7 +44,7 @@ struct RepDev {
     int atom_off;     // offset into the packed per-atom state arrays
     long long frame_off;  // offset (in atoms) of the replica's frame ring buffer
     uint32_t rep_id;  // global replica id (noise counter word)
-    int pad;
+    int index;        // index of the replica in the per-replica state arrays
 };
 
 // Replica state and outputs (device pointers).
