@@ -52,7 +52,11 @@ extern "C" {
 #define SCPS_REPLICA_LIST_OVERFLOW 4 /* periodic box: a tile had more j clusters than the list holds */
 
 /* ----------------------------------------------------------------- enums */
-enum { SCPS_MODEL_CHAIN = 0, SCPS_MODEL_TOY2D = 1 };
+enum { SCPS_MODEL_CHAIN = 0,
+       SCPS_MODEL_TOY2D = 1,     /* U = (x^2 - 1)^2 + y^2, one particle per replica */
+       SCPS_MODEL_FUNNEL2D = 2   /* the asymmetric funnel of Eq. (U) with the parameters of
+                                    Table 1 (Sec. "Diffusion in a 2-dimensional asymmetric
+                                    funnel"), one particle per replica */ };
 enum { SCPS_ELEC_NONE = 0, SCPS_ELEC_DDIEL = 1, SCPS_ELEC_RF = 2, SCPS_ELEC_PLAIN = 3 };
 enum { SCPS_INT_BAOAB = 0, SCPS_INT_EM = 1 };
 /* execution form of scps_step_replicas:
@@ -61,7 +65,15 @@ enum { SCPS_INT_BAOAB = 0, SCPS_INT_EM = 1 };
  *   PLAIN: reference form - one replica per kernel launch per step, FP32 float
  *     atomics in global memory, no graph. Same physics, same noise. */
 enum { SCPS_EXEC_RESIDENT = 0, SCPS_EXEC_PLAIN = 1 };
-enum { SCPS_BIAS_NONE = 0, SCPS_BIAS_RMD_CONTACTS = 1, SCPS_BIAS_RMD_TOY = 2 };
+enum { SCPS_BIAS_NONE = 0,
+       SCPS_BIAS_RMD_CONTACTS = 1,  /* chains: ratchet of Eq. (FrMD) on z(X) of Eq. (zrMD) */
+       SCPS_BIAS_RMD_TOY = 2,       /* two-dimensional models: ratchet on z = (x - x_ref)^2 */
+       SCPS_BIAS_RMD_RADIAL = 3,    /* two-dimensional models: ratchet on z = sqrt(x^2 + y^2) */
+       SCPS_BIAS_TUBE = 4           /* two-dimensional models: the self-consistent rMD forces
+                                       F^s and F^w of Eq. (Fs) and Eq. (Fw) on the tube
+                                       variables s_lambda and w_lambda of a reference path
+                                       (Eq. sX, Eq. wX with the average path in place of the
+                                       instantaneous one), configuration-space distance */ };
 enum { SCPS_ZM_FROM_X = 0, SCPS_ZM_VALUE = 1 };
 
 /* ----------------------------------------------------------------- descriptors */
@@ -134,6 +146,15 @@ typedef struct {
                                            (the paper's z_m(0) = z(X(0))); SCPS_ZM_VALUE */
     double zm_value;
     double toy_x_ref;                   /* toy model: z = (x - toy_x_ref)^2 */
+    /* SCPS_BIAS_TUBE: reference path <X(t'_k)>, k = 0 .. n_ref-1 (host, n_ref x 2), its
+       times t'_k (host, n_ref), lambda, k_s, k_w of Eq. (Fs) and Eq. (Fw), and the path
+       duration t. With D_k = |X - <X(t'_k)>|^2 and pi_k = exp(-lambda D_k) / sum:
+       w = -(1/lambda) log sum_k exp(-lambda D_k), s = 1 - (1/t) sum_k t'_k pi_k. s_m and
+       w_m are their running minima (zm_init as for z_m). */
+    int32_t n_ref;
+    const double* ref;
+    const double* ref_time;
+    double lambda, k_s, k_w, t_path;
 } scps_bias_desc;
 
 typedef struct {
@@ -225,6 +246,14 @@ int scps_set_state(scps_system* s, const double* x, const double* v, const doubl
 int scps_get_status(scps_system* s, int32_t* per_replica);
 
 int scps_get_info(const scps_system* s, scps_info* info);
+
+/* Average path of selected replicas (step 3 of the SCPS iteration): for the
+ * two-dimensional models, out[k] = mean over the replicas in `replicas` (host,
+ * n_sel indices) of their saved frame k, k = 0 .. n_frames-1, oldest first
+ * (host, n_frames x 2). Every selected replica must still hold all its frames
+ * (n_saved <= max_frames) and have at least n_frames of them. Synchronous. */
+int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, int32_t n_frames,
+                      double* out);
 
 /* Autotuner of the resident form (chain replicas): times the launch plans
  * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} on the

@@ -19,7 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "scps_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "scps_oracle_hvp.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "scps_oracle_hvp.c"), os.path.join(_HERE, "scps_oracle_2d.c")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
@@ -86,6 +86,15 @@ def lib():
         _lib.orc_run_toy.restype = C.c_int
         _lib.orc_num_threads.restype = C.c_int
         _lib.orc_hvp.argtypes = [P, P, P, P, P]
+        _lib.orc_funnel.argtypes = [C.c_double, C.c_double, P, P]
+        _lib.orc_funnel.restype = None
+        _lib.orc_tube_vars.argtypes = [C.c_int, P, P, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, P, P, P, P]
+        _lib.orc_tube_vars.restype = None
+        _lib.orc_run_2d.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, C.c_uint64,
+                                    C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_int, P, P, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_int64, C.c_int, C.c_int, P, P, P, P, P]
         _lib.orc_hvp.restype = C.c_int
     return _lib
 
@@ -254,6 +263,57 @@ def run_toy(xy, zm, step, rep_id, seed, dt, gamma, kT, k_R, n_steps, x_ref=1.0, 
     lib().orc_run_toy(R, _p(xy), _p(zm), _p(step), _p(rep_id), seed, dt, gamma, kT, k_R, x_ref,
                       n_steps, save_every, mf, _p(frames), _p(fz), _p(fzm), _p(ns), _p(T))
     return dict(x=xy, zm=zm, step=step, T=T, frames=frames[:, :mf], z=fz[:, :mf],
+                zmin=fzm[:, :mf], n_saved=ns)
+
+
+MODEL_DOUBLE_WELL, MODEL_FUNNEL = 0, 1
+BIAS_2D_NONE, BIAS_2D_X, BIAS_2D_RADIAL, BIAS_2D_TUBE = 0, 2, 3, 4
+
+
+def funnel(x, y):
+    """U and F = -grad U of the asymmetric funnel (Eq. U, Table 1)."""
+    U = C.c_double(0.0)
+    F = np.zeros(2)
+    lib().orc_funnel(float(x), float(y), C.byref(U), _p(F))
+    return U.value, F
+
+
+def tube_vars(ref, tref, lam, t_path, x, y):
+    """s_lambda, w_lambda of the point (x, y) for the reference path ref (K, 2) at times
+    tref (K,), with their gradients: (s, w, grad s, grad w)."""
+    ref = _f64(np.reshape(ref, (-1, 2)))
+    tref = _f64(tref)
+    s, w = C.c_double(0.0), C.c_double(0.0)
+    gs, gw = np.zeros(2), np.zeros(2)
+    lib().orc_tube_vars(len(ref), _p(ref), _p(tref), float(lam), float(t_path), float(x),
+                        float(y), C.byref(s), C.byref(w), _p(gs), _p(gw))
+    return s.value, w.value, gs, gw
+
+
+def run_2d(model, bias, xy, step, rep_id, seed, dt, gamma, kT, n_steps, k_R=0.0, x_ref=1.0,
+           zm=None, sm=None, wm=None, ref=None, tref=None, lam=1.0, k_s=0.0, k_w=0.0,
+           t_path=1.0, save_every=0, max_frames=0, T_acc=None):
+    """Euler-Maruyama runs of the two-dimensional models (arrays are copied)."""
+    xy = _f64(np.reshape(xy, (-1, 2))).copy()
+    R = xy.shape[0]
+    inf = np.full(R, np.inf)
+    zm = inf.copy() if zm is None else _f64(zm).copy()
+    sm = inf.copy() if sm is None else _f64(sm).copy()
+    wm = inf.copy() if wm is None else _f64(wm).copy()
+    step = np.ascontiguousarray(step, np.int64).copy()
+    rep_id = _i32(rep_id)
+    ref = _f64(np.zeros((1, 2)) if ref is None else np.reshape(ref, (-1, 2)))
+    tref = _f64(np.zeros(1) if tref is None else tref)
+    T = np.zeros(R) if T_acc is None else _f64(T_acc).copy()
+    mf = max_frames if save_every > 0 else 0
+    frames = np.zeros((R, max(mf, 1), 2))
+    fz = np.zeros((R, max(mf, 1)))
+    fzm = fz.copy()
+    ns = np.zeros(R, np.int32)
+    lib().orc_run_2d(model, bias, R, _p(xy), _p(zm), _p(sm), _p(wm), _p(step), _p(rep_id), seed,
+                     dt, gamma, kT, k_R, x_ref, len(ref), _p(ref), _p(tref), lam, k_s, k_w,
+                     t_path, n_steps, save_every, mf, _p(frames), _p(fz), _p(fzm), _p(ns), _p(T))
+    return dict(x=xy, zm=zm, sm=sm, wm=wm, step=step, T=T, frames=frames[:, :mf], z=fz[:, :mf],
                 zmin=fzm[:, :mf], n_saved=ns)
 
 

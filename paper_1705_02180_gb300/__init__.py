@@ -18,11 +18,11 @@ from . import build as _build
 SCPS_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "NONFINITE", -4: "LIST_OVERFLOW", -5: "TIMEOUT",
           -6: "STATE", -7: "UNSUPPORTED"}
-MODEL_CHAIN, MODEL_TOY2D = 0, 1
+MODEL_CHAIN, MODEL_TOY2D, MODEL_FUNNEL2D = 0, 1, 2
 ELEC_NONE, ELEC_DDIEL, ELEC_RF, ELEC_PLAIN = 0, 1, 2, 3
 INT_BAOAB, INT_EM = 0, 1
 EXEC_RESIDENT, EXEC_PLAIN = 0, 1
-BIAS_NONE, BIAS_RMD_CONTACTS, BIAS_RMD_TOY = 0, 1, 2
+BIAS_NONE, BIAS_RMD_CONTACTS, BIAS_RMD_TOY, BIAS_RMD_RADIAL, BIAS_TUBE = 0, 1, 2, 3, 4
 ZM_FROM_X, ZM_VALUE = 0, 1
 
 _P = C.c_void_p
@@ -50,7 +50,9 @@ class SystemDesc(C.Structure):
 class BiasDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("k_R", C.c_double), ("r0", C.c_double), ("n_pairs", _P),
                 ("pairs", _P), ("x_native", _P), ("zm_init", C.c_int32),
-                ("zm_value", C.c_double), ("toy_x_ref", C.c_double)]
+                ("zm_value", C.c_double), ("toy_x_ref", C.c_double), ("n_ref", C.c_int32),
+                ("ref", _P), ("ref_time", _P), ("lam", C.c_double), ("k_s", C.c_double),
+                ("k_w", C.c_double), ("t_path", C.c_double)]
 
 
 class Info(C.Structure):
@@ -73,7 +75,7 @@ PLAN_ONE_LAUNCH, PLAN_PER_SIZE_CLASS = 0, 1
 EXPORTS = ["scps_create_system", "scps_destroy_system", "scps_set_bias", "scps_step_replicas",
            "scps_energy_forces", "scps_hvp", "scps_collect_paths", "scps_get_state",
            "scps_set_state", "scps_get_status", "scps_get_info", "scps_philox4x32_10",
-           "scps_energy_forces_noalloc", "scps_autotune", "scps_last_error"]
+           "scps_energy_forces_noalloc", "scps_autotune", "scps_path_average", "scps_last_error"]
 
 _lib = None
 
@@ -105,6 +107,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         "scps_philox4x32_10": [i64, _P, u32, u32, _P, _P],
         "scps_energy_forces_noalloc": [_P, i32, _P, _P, _P, _P],
         "scps_autotune": [_P, i32, i32, _P],
+        "scps_path_average": [_P, i32, _P, i32, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -183,7 +186,7 @@ class System:
                                    _ptr(arrs["excl"]))
         x0 = _f64(x0)
         v0 = None if v0 is None else _f64(v0)
-        if model == MODEL_TOY2D:
+        if model in (MODEL_TOY2D, MODEL_FUNNEL2D):
             n_rep = x0.reshape(-1, 2).shape[0]
             rt = None
         else:
@@ -203,7 +206,7 @@ class System:
         h = C.c_void_p()
         check(lib.scps_create_system(C.byref(d), C.byref(h)))
         self.h = h
-        if model == MODEL_TOY2D:
+        if model in (MODEL_TOY2D, MODEL_FUNNEL2D):
             self.atoms_per_rep = np.ones(n_rep, np.int64)
         else:
             self.atoms_per_rep = np.array([self.n_atoms[t] for t in rt], np.int64)
@@ -237,6 +240,30 @@ class System:
         b = BiasDesc(BIAS_RMD_TOY, k_R, 0.0, None, None, None, zm_init, zm_value, x_ref)
         check(load().scps_set_bias(self.h, C.byref(b)))
 
+    def set_radial_bias(self, k_R, zm_init=ZM_FROM_X, zm_value=0.0):
+        """Two-dimensional models: ratchet on z = sqrt(x^2 + y^2)."""
+        b = BiasDesc(BIAS_RMD_RADIAL, k_R, 0.0, None, None, None, zm_init, zm_value, 0.0)
+        check(load().scps_set_bias(self.h, C.byref(b)))
+
+    def set_tube_bias(self, ref, ref_time, lam, k_s, k_w, t_path, zm_init=ZM_FROM_X, zm_value=0.0):
+        """Two-dimensional models: forces F^s, F^w on the tube variables of a reference path
+        (ref: (K, 2) points, ref_time: (K,) times)."""
+        ref = _f64(np.reshape(ref, (-1, 2)))
+        tm = _f64(np.reshape(ref_time, (-1,)))
+        if len(tm) != len(ref):
+            raise ValueError("ref and ref_time differ in length")
+        self._bias_keep = [ref, tm]
+        b = BiasDesc(BIAS_TUBE, 0.0, 0.0, None, None, None, zm_init, zm_value, 0.0, len(ref),
+                     _ptr(ref), _ptr(tm), lam, k_s, k_w, t_path)
+        check(load().scps_set_bias(self.h, C.byref(b)))
+
+    def path_average(self, replicas, n_frames):
+        """Two-dimensional models: mean of saved frames 0 .. n_frames-1 over `replicas`."""
+        sel = _i32(np.asarray(replicas).reshape(-1))
+        out = np.zeros((int(n_frames), 2))
+        check(load().scps_path_average(self.h, len(sel), _ptr(sel), int(n_frames), _ptr(out)))
+        return out
+
     def clear_bias(self):
         b = BiasDesc(BIAS_NONE, 0.0, 0.0, None, None, None, 0, 0.0, 0.0)
         check(load().scps_set_bias(self.h, C.byref(b)))
@@ -251,7 +278,7 @@ class System:
         return rc, st
 
     def get_state(self):
-        dims = 2 if self.model == MODEL_TOY2D else 3
+        dims = 2 if self.model in (MODEL_TOY2D, MODEL_FUNNEL2D) else 3
         n = int(self.atoms_per_rep.sum())
         x = np.zeros((n, dims))
         v = np.zeros((n, dims))
@@ -271,7 +298,7 @@ class System:
     def collect_paths(self, rep0=0, nrep=None):
         nrep = self.n_replicas - rep0 if nrep is None else nrep
         mf = max(self.max_frames, 1)
-        dims = 2 if self.model == MODEL_TOY2D else 3
+        dims = 2 if self.model in (MODEL_TOY2D, MODEL_FUNNEL2D) else 3
         sizes = self.atoms_per_rep[rep0:rep0 + nrep]
         frames = np.zeros(int(sizes.sum()) * mf * dims, np.float32)
         z = np.zeros((nrep, mf))

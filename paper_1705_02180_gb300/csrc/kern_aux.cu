@@ -1,38 +1,145 @@
-// Two-dimensional toy model, the plain one-replica-per-launch form of the
+// Two-dimensional models, the plain one-replica-per-launch form of the
 // chain step, and the Philox block generator used to check the noise stream.
 #include "scps_internal.h"
 
 namespace scps {
 
 // ---------------------------------------------------------------------------
-// Toy model: one particle per replica on U(x, y) = (x^2 - 1)^2 + y^2, overdamped
-// Langevin (Euler-Maruyama) in FP64 with the ratchet of Eq. (FrMD) on
-// z = (x - x_ref)^2. One thread per replica; the whole launch runs n_steps.
+// Two-dimensional models, one particle per replica, overdamped Langevin
+// (Euler-Maruyama) in FP64; one thread per replica runs the whole launch.
+//   model 0: U = (x^2 - 1)^2 + y^2 (double well)
+//   model 1: the asymmetric funnel of Eq. (U) with the parameters of Table 1
+// Biases (P.bias):
+//   2: ratchet of Eq. (FrMD) on z = (x - x_ref)^2
+//   3: ratchet on z = sqrt(x^2 + y^2), the distance from the funnel centre
+//   4: tube variables s_lambda, w_lambda of a reference path <X(t'_k)> (the
+//      configuration-space form used for the funnel): D_k = |X - <X(t'_k)>|^2,
+//      pi_k = exp(-lambda D_k) / sum, w = -(1/lambda) log sum_k exp(-lambda D_k),
+//      s = 1 - (1/t) sum_k t'_k pi_k, each with its own ratchet (forces F^w, F^s of
+//      Eq. Fw and Eq. Fs; z_m of Eq. FrMD replaced by s_m and w_m)
 // ---------------------------------------------------------------------------
+namespace {
+
+constexpr double kA1 = 30.0, kA2 = 20.0, kA3 = 6.0, kS1 = 1.0, kS2 = 2.0, kS3 = 0.5;
+constexpr double kW = 0.03, kYm = 0.0, kXm = 1.5;
+
+__device__ __forceinline__ double funnel_u(double x, double y) {
+    const double r2 = x * x + y * y;
+    const double d2 = (x - kXm) * (x - kXm) + (y - kYm) * (y - kYm);
+    const double a = r2 + kS1 * kS1, b = r2 + kS2 * kS2, c = d2 + kS3 * kS3;
+    return kW * kW * r2 * r2 - kA1 * kS1 * kS1 / (a * a) + kA2 * kS2 * kS2 / (b * b) -
+           kA3 * kS3 * kS3 / (c * c);
+}
+
+__device__ __forceinline__ double2 funnel_f(double x, double y) {
+    const double r2 = x * x + y * y;
+    const double d2 = (x - kXm) * (x - kXm) + (y - kYm) * (y - kYm);
+    const double a = r2 + kS1 * kS1, b = r2 + kS2 * kS2, c = d2 + kS3 * kS3;
+    // -dU/dr2 for the terms in r2, -dU/dd2 for the gate term
+    const double gr = -2.0 * kW * kW * r2 - 2.0 * kA1 * kS1 * kS1 / (a * a * a) +
+                      2.0 * kA2 * kS2 * kS2 / (b * b * b);
+    const double gd = -2.0 * kA3 * kS3 * kS3 / (c * c * c);
+    return make_double2(2.0 * (gr * x + gd * (x - kXm)), 2.0 * (gr * y + gd * (y - kYm)));
+}
+
+struct Pot2 {
+    double2 f;
+    double u;
+};
+
+__device__ __forceinline__ Pot2 model_force(int model, double2 p) {
+    Pot2 o;
+    if (model == 1) {
+        o.f = funnel_f(p.x, p.y);
+        o.u = funnel_u(p.x, p.y);
+    } else {
+        o.f = make_double2(-4.0 * p.x * (p.x * p.x - 1.0), -2.0 * p.y);
+        o.u = (p.x * p.x - 1.0) * (p.x * p.x - 1.0) + p.y * p.y;
+    }
+    return o;
+}
+
+// Tube variables at p: s, w and their gradients.
+__device__ void tube_vars(const RunParams& P, double2 p, double* s, double* w, double2* gs,
+                          double2* gw) {
+    double dmin = 1e300;
+    for (int k = 0; k < P.tube_k; ++k) {
+        const double2 q = P.tube_ref[k];
+        const double d = (p.x - q.x) * (p.x - q.x) + (p.y - q.y) * (p.y - q.y);
+        dmin = d < dmin ? d : dmin;
+    }
+    // sums with the largest weight scaled to 1 (the formulas are unchanged)
+    double S = 0.0, St = 0.0;
+    double2 g1 = make_double2(0.0, 0.0), g2 = make_double2(0.0, 0.0);
+    for (int k = 0; k < P.tube_k; ++k) {
+        const double2 q = P.tube_ref[k];
+        const double dx = p.x - q.x, dy = p.y - q.y;
+        const double e = exp(-P.tube_lambda * (dx * dx + dy * dy - dmin));
+        const double t = P.tube_time[k];
+        S += e;
+        St += e * t;
+        g1.x += e * 2.0 * dx;  // sum e_k grad D_k
+        g1.y += e * 2.0 * dy;
+        g2.x += e * t * 2.0 * dx;  // sum e_k t_k grad D_k
+        g2.y += e * t * 2.0 * dy;
+    }
+    const double tm = St / S;  // <t'> under pi
+    *w = dmin - log(S) / P.tube_lambda;
+    *s = 1.0 - tm / P.tube_t;
+    *gw = make_double2(g1.x / S, g1.y / S);  // sum pi_k grad D_k
+    const double c = P.tube_lambda / P.tube_t;
+    *gs = make_double2(c * (g2.x / S - tm * g1.x / S), c * (g2.y / S - tm * g1.y / S));
+}
+
+}  // namespace
+
 __global__ void k_toy(StateDev st, RunParams P, const uint32_t* __restrict__ rep_ids) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= P.n_replicas) return;
     double2 p = st.xy[r];
     double zm = st.zm[r], T = st.T[r];
+    double sm = st.sm[r], wm = st.wm[r];
     long long step = st.step[r];
     long long ns = st.n_saved[r];
     const uint32_t id = rep_ids[r];
     const double a = P.toy_dt_over_gamma, sd = P.toy_sd, xr = P.toy_x_ref;
-    double z = (p.x - xr) * (p.x - xr);
+    double z;
     for (long long s = 0; s < P.n_steps; ++s) {
-        double fx = -4.0 * p.x * (p.x * p.x - 1.0);
-        const double fy = -2.0 * p.y;
-        z = (p.x - xr) * (p.x - xr);
-        if (P.bias == 2) {
-            double factor = 0.0;
+        const Pot2 pot = model_force(P.toy_model, p);
+        double fx = pot.f.x, fy = pot.f.y;
+        double bx = 0.0, by = 0.0;
+        if (P.bias == 2 || P.bias == 3) {
+            double gx, gy;
+            if (P.bias == 2) {
+                z = (p.x - xr) * (p.x - xr);
+                gx = 2.0 * (p.x - xr);
+                gy = 0.0;
+            } else {
+                z = sqrt(p.x * p.x + p.y * p.y);
+                gx = z > 0.0 ? p.x / z : 0.0;
+                gy = z > 0.0 ? p.y / z : 0.0;
+            }
+            double factor = 0.0;  // Eq. (FrMD) with theta(0) = 1
             if (z < zm)
                 zm = z;
             else
                 factor = -P.k_R * (z - zm);
-            const double fb = factor * 2.0 * (p.x - xr);
-            fx += fb;
-            T += a * fb * fb;  // (dt / gamma) |F_bias|^2, unit mass
+            bx = factor * gx;
+            by = factor * gy;
+        } else if (P.bias == 4) {
+            double sv, wv;
+            double2 gs, gw;
+            tube_vars(P, p, &sv, &wv, &gs, &gw);
+            double fs = 0.0, fw = 0.0;
+            if (sv < sm) sm = sv; else fs = -P.tube_ks * (sv - sm);
+            if (wv < wm) wm = wv; else fw = -P.tube_kw * (wv - wm);
+            bx = fs * gs.x + fw * gw.x;
+            by = fs * gs.y + fw * gw.y;
+            z = sv;
         }
+        fx += bx;
+        fy += by;
+        T += a * (bx * bx + by * by);  // (dt / gamma) |F_bias|^2, unit mass
         const uint4 rb = philox4x32_10(make_uint4(0u, id, (uint32_t)step, 0u), P.key0, P.key1);
         const double2 xi = normals2_f64(rb.x, rb.y);
         p.x = p.x + a * fx + sd * xi.x;
@@ -41,23 +148,69 @@ __global__ void k_toy(StateDev st, RunParams P, const uint32_t* __restrict__ rep
         if (P.save_interval > 0 && step % P.save_interval == 0) {
             const long long slot = ns % P.max_frames;
             const long long fi = (long long)r * P.max_frames + slot;
-            const double z1 = (p.x - xr) * (p.x - xr);
             st.frames[2 * fi] = (float)p.x;
             st.frames[2 * fi + 1] = (float)p.y;
+            double z1 = 0.0, zm1 = 0.0;
+            if (P.bias == 2) {
+                z1 = (p.x - xr) * (p.x - xr);
+                zm1 = zm < z1 ? zm : z1;
+            } else if (P.bias == 3) {
+                z1 = sqrt(p.x * p.x + p.y * p.y);
+                zm1 = zm < z1 ? zm : z1;
+            } else if (P.bias == 4) {  // frames record s_lambda and its running minimum
+                double wv;
+                double2 gs, gw;
+                tube_vars(P, p, &z1, &wv, &gs, &gw);
+                zm1 = sm < z1 ? sm : z1;
+            }
             st.fz[fi] = z1;
-            st.fzm[fi] = zm < z1 ? zm : z1;
-            st.fe[fi] = (p.x * p.x - 1.0) * (p.x * p.x - 1.0) + p.y * p.y;
+            st.fzm[fi] = zm1;
+            st.fe[fi] = model_force(P.toy_model, p).u;
             st.fT[fi] = T;
             ++ns;
         }
     }
+    // z of the final configuration (s_lambda for the tube bias)
+    if (P.bias == 3) {
+        z = sqrt(p.x * p.x + p.y * p.y);
+    } else if (P.bias == 4) {
+        double wv;
+        double2 gs, gw;
+        tube_vars(P, p, &z, &wv, &gs, &gw);
+    } else {
+        z = (p.x - xr) * (p.x - xr);
+    }
     st.xy[r] = p;
     st.zm[r] = zm;
-    st.z[r] = (p.x - xr) * (p.x - xr);
+    st.sm[r] = sm;
+    st.wm[r] = wm;
+    st.z[r] = z;
     st.T[r] = T;
     st.step[r] = step;
     st.n_saved[r] = ns;
     if (!(isfinite(p.x) && isfinite(p.y))) st.status[r] = 1;
+}
+
+// Average path of selected replicas from their frame buffers (frames k = 0 .. K-1,
+// oldest first, all kept): out[k] = mean over the selection of frame k, summed in
+// selection order (one thread per frame).
+__global__ void k_path_average_2d(StateDev st, int max_frames, int K, const int* __restrict__ sel,
+                                  int n_sel, double2* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double sx = 0.0, sy = 0.0;
+    for (int q = 0; q < n_sel; ++q) {
+        const long long fi = (long long)sel[q] * max_frames + k;
+        sx += (double)st.frames[2 * fi];
+        sy += (double)st.frames[2 * fi + 1];
+    }
+    out[k] = make_double2(sx / n_sel, sy / n_sel);
+}
+
+cudaError_t launch_path_average_2d(const StateDev& st, int max_frames, int K, const int* sel,
+                                   int n_sel, double2* out, cudaStream_t stream) {
+    k_path_average_2d<<<(K + 127) / 128, 128, 0, stream>>>(st, max_frames, K, sel, n_sel, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_toy(const StateDev& st, const RunParams& P, const uint32_t* rep_ids,

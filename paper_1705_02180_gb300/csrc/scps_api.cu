@@ -23,6 +23,8 @@ cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const R
 cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
                         double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
                         int ncon_max, int threads, cudaStream_t stream);
+cudaError_t launch_path_average_2d(const StateDev& st, int max_frames, int K, const int* sel,
+                                   int n_sel, double2* out, cudaStream_t stream);
 cudaError_t launch_toy(const StateDev& st, const RunParams& P, const uint32_t* rep_ids,
                        cudaStream_t stream);
 cudaError_t launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1,
@@ -140,6 +142,8 @@ struct scps_system {
 
 namespace {
 
+bool is_2d(int model) { return model == SCPS_MODEL_TOY2D || model == SCPS_MODEL_FUNNEL2D; }
+
 int validate_topology(const scps_topology_desc& t, int idx, int max_atoms) {
     if (t.n_atoms <= 0 || t.n_atoms > max_atoms)
         return fail(SCPS_ERR_INVALID_ARG, "topology %d: n_atoms %d outside [1, %d]", idx, t.n_atoms,
@@ -252,7 +256,7 @@ int build_topology(scps_system* s, const scps_topology_desc& t, TopoHost& h) {
 }
 
 int atoms_per_replica(const scps_system* s, int r) {
-    return s->model == SCPS_MODEL_TOY2D ? 1 : s->topos[s->rep_topo[r]].n;
+    return is_2d(s->model) ? 1 : s->topos[s->rep_topo[r]].n;
 }
 
 int auto_threads(int nta) {
@@ -377,7 +381,7 @@ const char* scps_last_error(void) { return g_err.c_str(); }
 int scps_create_system(const scps_system_desc* d, scps_system** out) {
     if (!d || !out) return fail(SCPS_ERR_INVALID_ARG, "NULL descriptor or output pointer");
     *out = nullptr;
-    if (d->model != SCPS_MODEL_CHAIN && d->model != SCPS_MODEL_TOY2D)
+    if (d->model != SCPS_MODEL_CHAIN && !is_2d(d->model))
         return fail(SCPS_ERR_INVALID_ARG, "unknown model %d", d->model);
     if (d->n_replicas <= 0) return fail(SCPS_ERR_INVALID_ARG, "n_replicas must be > 0");
     if (!d->x0) return fail(SCPS_ERR_INVALID_ARG, "x0 is NULL");
@@ -463,7 +467,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     s->n_atoms_total = off;
     s->n_frame_atoms = foff;
     const int mf = std::max(d->max_frames, 1);
-    const int dims = d->model == SCPS_MODEL_TOY2D ? 2 : 3;
+    const int dims = is_2d(d->model) ? 2 : 3;
     StateDev& st = s->st;
     int rc = 0;
 #define ALLOC(p, n)                                          \
@@ -494,6 +498,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         ALLOC(s->plain_d, 8);
     } else {
         ALLOC(st.xy, R);
+        ALLOC(st.sm, R);
+        ALLOC(st.wm, R);
     }
 #undef ALLOC
     {
@@ -605,6 +611,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     P.toy_dt_over_gamma = d->dt / d->gamma;
     P.toy_sd = std::sqrt(2.0 * d->kT * d->dt / d->gamma);
     P.toy_x_ref = 1.0;
+    P.toy_model = d->model == SCPS_MODEL_FUNNEL2D ? 1 : 0;
     const double rcut = d->cutoff > 0.0 ? d->cutoff : 1.0;
     P.pc.rc = (float)rcut;
     P.pc.rc2 = (float)(rcut * rcut);
@@ -634,10 +641,36 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
     RunParams& P = s->base;
     if (b->kind == SCPS_BIAS_NONE) {
         P.bias = 0;
-    } else if (b->kind == SCPS_BIAS_RMD_TOY) {
-        if (s->model != SCPS_MODEL_TOY2D) return fail(SCPS_ERR_INVALID_ARG, "toy bias on a chain system");
-        P.bias = 2;
+    } else if (b->kind == SCPS_BIAS_RMD_TOY || b->kind == SCPS_BIAS_RMD_RADIAL) {
+        if (!is_2d(s->model)) return fail(SCPS_ERR_INVALID_ARG, "toy bias on a chain system");
+        P.bias = b->kind == SCPS_BIAS_RMD_TOY ? 2 : 3;
         P.toy_x_ref = b->toy_x_ref;
+    } else if (b->kind == SCPS_BIAS_TUBE) {
+        if (!is_2d(s->model))
+            return fail(SCPS_ERR_UNSUPPORTED, "the tube bias is built for the two-dimensional models");
+        if (b->n_ref < 1 || b->n_ref > 1000000 || !b->ref || !b->ref_time)
+            return fail(SCPS_ERR_INVALID_ARG, "tube bias needs 1 <= n_ref <= 1e6, ref and ref_time");
+        if (!(b->lambda > 0.0) || !(b->t_path > 0.0) || !(b->k_s >= 0.0) || !(b->k_w >= 0.0))
+            return fail(SCPS_ERR_INVALID_ARG, "tube bias needs lambda > 0, t_path > 0, k_s, k_w >= 0");
+        std::vector<double2> ref(b->n_ref);
+        std::vector<double> tm(b->ref_time, b->ref_time + b->n_ref);
+        for (int k = 0; k < b->n_ref; ++k) {
+            ref[k] = make_double2(b->ref[2 * k], b->ref[2 * k + 1]);
+            if (!std::isfinite(ref[k].x) || !std::isfinite(ref[k].y) || !std::isfinite(tm[k]))
+                return fail(SCPS_ERR_NONFINITE, "non-finite reference point %d", k);
+        }
+        double2* d_ref = nullptr;
+        double* d_tm = nullptr;
+        SCPS_CU(s->upload(&d_ref, ref));
+        SCPS_CU(s->upload(&d_tm, tm));
+        P.bias = 4;
+        P.tube_k = b->n_ref;
+        P.tube_ref = d_ref;
+        P.tube_time = d_tm;
+        P.tube_lambda = b->lambda;
+        P.tube_ks = b->k_s;
+        P.tube_kw = b->k_w;
+        P.tube_t = b->t_path;
     } else if (b->kind == SCPS_BIAS_RMD_CONTACTS) {
         if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_INVALID_ARG, "contact bias needs the chain model");
         if (!(b->r0 > 0.0)) return fail(SCPS_ERR_INVALID_ARG, "r0 must be > 0");
@@ -727,6 +760,10 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
     std::vector<double> zero(R, 0.0);
     SCPS_CU(cudaMemcpy(s->st.zm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
     SCPS_CU(cudaMemcpy(s->st.T, zero.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+    if (is_2d(s->model)) {  // s_m and w_m of the tube bias follow the same initial rule as z_m
+        SCPS_CU(cudaMemcpy(s->st.sm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+        SCPS_CU(cudaMemcpy(s->st.wm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
+    }
     drop_graphs(s);
     return SCPS_OK;
 }
@@ -742,7 +779,7 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
             return fail(SCPS_ERR_INVALID_ARG, "step counter would pass 2^32 (noise counter word)");
     RunParams P = s->base;
     long long launches = 0;
-    if (s->model == SCPS_MODEL_TOY2D) {
+    if (is_2d(s->model)) {
         P.n_steps = n_steps;
         SCPS_CU(launch_toy(s->st, P, s->d_rep_ids, cs));
         launches = 1;
@@ -847,7 +884,7 @@ int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames
     if (rep0 < 0 || nrep < 0 || rep0 + nrep > R) return fail(SCPS_ERR_INVALID_ARG, "replica range");
     SCPS_CU(cudaDeviceSynchronize());
     const int mf = std::max(s->d.max_frames, 1);
-    const int dims = s->model == SCPS_MODEL_TOY2D ? 2 : 3;
+    const int dims = is_2d(s->model) ? 2 : 3;
     std::vector<long long> ns(R);
     SCPS_CU(cudaMemcpy(ns.data(), s->st.n_saved, sizeof(long long) * R, cudaMemcpyDeviceToHost));
     std::vector<double> buf((size_t)nrep * mf);
@@ -871,7 +908,7 @@ int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames
             const int n = atoms_per_replica(s, r);
             const size_t per = (size_t)n * dims;
             std::vector<float> fb((size_t)mf * per);
-            const size_t src_off = s->model == SCPS_MODEL_TOY2D ? (size_t)r * mf * 2
+            const size_t src_off = is_2d(s->model) ? (size_t)r * mf * 2
                                                                 : (size_t)s->frame_off[r] * 3;
             SCPS_CU(cudaMemcpy(fb.data(), s->st.frames + src_off, sizeof(float) * fb.size(),
                                cudaMemcpyDeviceToHost));
@@ -892,7 +929,7 @@ int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* st
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     SCPS_CU(cudaDeviceSynchronize());
     const int R = s->d.n_replicas;
-    if (s->model == SCPS_MODEL_TOY2D) {
+    if (is_2d(s->model)) {
         if (x) SCPS_CU(cudaMemcpy(x, s->st.xy, sizeof(double2) * R, cudaMemcpyDeviceToHost));
         if (v) std::memset(v, 0, sizeof(double) * 2 * R);
     } else if (s->is_box) {  // slots are in tile order: place each atom by its id
@@ -950,7 +987,7 @@ int scps_set_state(scps_system* s, const double* x, const double* v, const doubl
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     SCPS_CU(cudaDeviceSynchronize());
     const int R = s->d.n_replicas;
-    if (s->model == SCPS_MODEL_TOY2D) {
+    if (is_2d(s->model)) {
         if (x) {
             for (int r = 0; r < 2 * R; ++r)
                 if (!std::isfinite(x[r])) return fail(SCPS_ERR_NONFINITE, "non-finite position");
@@ -1053,6 +1090,35 @@ int scps_get_info(const scps_system* s, scps_info* info) {
     info->plan = s->plan;
     info->kernels_per_step_call = 1;
     info->device_bytes = s->bytes;
+    return SCPS_OK;
+}
+
+int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, int32_t n_frames,
+                      double* out) {
+    if (!s || !replicas || !out) return fail(SCPS_ERR_INVALID_ARG, "NULL argument");
+    if (!is_2d(s->model)) return fail(SCPS_ERR_UNSUPPORTED, "path averages are built for the two-dimensional models");
+    const int R = s->d.n_replicas, mf = s->d.max_frames;
+    if (n_sel < 1 || n_frames < 1 || n_frames > mf)
+        return fail(SCPS_ERR_INVALID_ARG, "need n_sel >= 1 and 1 <= n_frames <= max_frames");
+    std::vector<long long> ns(R);
+    SCPS_CU(cudaMemcpy(ns.data(), s->st.n_saved, sizeof(long long) * R, cudaMemcpyDeviceToHost));
+    std::vector<int> sel(replicas, replicas + n_sel);
+    for (int r : sel) {
+        if (r < 0 || r >= R) return fail(SCPS_ERR_INVALID_ARG, "replica %d out of range", r);
+        if (ns[r] < n_frames || ns[r] > mf)
+            return fail(SCPS_ERR_STATE, "replica %d holds %lld frames (needs %d, at most %d kept)", r,
+                        ns[r], n_frames, mf);
+    }
+    int* d_sel = nullptr;
+    double2* d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_sel, sizeof(int) * n_sel);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double2) * n_frames);
+    if (e == cudaSuccess) e = cudaMemcpy(d_sel, sel.data(), sizeof(int) * n_sel, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_path_average_2d(s->st, mf, n_frames, d_sel, n_sel, d_out, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(double2) * n_frames, cudaMemcpyDeviceToHost);
+    cudaFree(d_sel);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return fail(SCPS_ERR_CUDA, "path average failed: %s", cudaGetErrorString(e));
     return SCPS_OK;
 }
 

@@ -63,8 +63,10 @@ struct StateDev {
     double* fe;
     double* fT;
     long long* n_saved;
-    // toy model state
+    // two-dimensional model state
     double2* xy;
+    double* sm;       // running minimum of s_lambda (tube bias)
+    double* wm;       // running minimum of w_lambda (tube bias)
 };
 
 struct RunParams {
@@ -78,9 +80,15 @@ struct RunParams {
     int save_interval, max_frames;
     long long n_steps;            // steps in this launch
     PairConst pc;
-    // toy model
+    // two-dimensional models
     double toy_dt_over_gamma, toy_sd, toy_x_ref;
     double gamma;
+    int toy_model;                // 0: double well, 1: asymmetric funnel (Eq. U, Table 1)
+    // tube variables s_lambda, w_lambda on a reference path (two-dimensional models)
+    int tube_k;                   // reference points
+    const double2* tube_ref;      // [tube_k] points of the reference path
+    const double* tube_time;      // [tube_k] their times t'
+    double tube_lambda, tube_ks, tube_kw, tube_t;  // lambda, k_s, k_w, path duration t
 };
 
 // Periodic-box state of all replicas (slot arrays are [replica][np], in tile order).
