@@ -61,7 +61,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="chain", choices=["chain", "batched", "box", "toy", "hvp"],
+    p.add_argument("--workload", default="chain", choices=["chain", "batched", "box", "toy", "hvp", "tube", "funnel"],
                    help="chain: the headline workload; the others measure the other configurations")
     return p.parse_args()
 
@@ -228,6 +228,10 @@ def timed_calls(torch, step_fn, K, W):
     return np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3, clk
 
 
+def K_calls(args):
+    return max(1, min(args.steps, 10))
+
+
 def run_extra(args):
     """The other workloads of the build target, one JSON line each."""
     import torch
@@ -302,6 +306,55 @@ def run_extra(args):
                "warmup": W, "config": {"workload": "256 replicas x 1e4 overdamped steps, FP64"},
                "clocks": clk}
         s.close()
+    elif args.workload == "tube":
+        # the headline chain workload under the contact-map tube bias (72 reference maps)
+        c = synth.make_chain(35, seed=1)
+        R, K = 64, 72
+        spc = args.md_steps_per_call
+        x0 = np.stack([c.x_unfolded] * R).reshape(-1, 3)
+        v0 = c.velocities(R, KT_300, SEED).reshape(-1, 3)
+        cu = np.array([np.linalg.norm(c.x_unfolded[j] - c.x_unfolded[i]) for i, j in c.contacts])
+        cn = np.array([np.linalg.norm(c.x_native[j] - c.x_native[i]) for i, j in c.contacts])
+        frac = np.linspace(0.0, 1.0, K)[:, None]
+        r = cu[None] + (cn - cu)[None] * frac  # synthetic reference path in distance space
+        u = (r / 0.75) ** 2
+        maps = (1 + u + u * u) / (1 + u + u * u + u ** 3 + u ** 4)
+        times = (np.arange(K) + 1) * 7.0  # a slice every 7 ps
+        s = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0,
+                       v0=v0, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002, gamma=1.0,
+                       kT=KT_300, seed=SEED, steps_per_graph=spc)
+        s.set_contact_tube_bias([c.contacts], [c.x_native], [maps], times, 13.5, 2.5, 2.5e-4,
+                                times[-1])
+        durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K=K_calls(args), W=W)
+        out = {"metric": "biased-Langevin atom-steps/s", "value": R * c.n_atoms * spc * len(durs) / durs.sum(),
+               "unit": "atom-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": len(durs), "warmup": W,
+               "config": {"workload": f"{R} replicas x {c.n_atoms}-atom chain, contact-map tube bias "
+                                      f"({K} reference maps x {len(c.contacts)} contacts, lambda 13.5, "
+                                      "k_s 2.5, k_w 2.5e-4), dt 2 fs, 300 K",
+                          "md_steps_per_call": spc},
+               "gpu_launches": int(s.info()["graph_nodes_last_call"]) * len(durs), "clocks": clk}
+        s.close()
+    elif args.workload == "funnel":
+        # the whole SCPS iteration on the funnel: rMD round + 2 tube rounds, 512 x 2000 steps each
+        from paper_1705_02180_gb300.scps import FunnelProtocol, run_funnel_scps
+        p = FunnelProtocol()
+        run_funnel_scps(FunnelProtocol(n_replicas=64, n_steps=200, save_every=20, iterations=1))
+        walls = []
+        for _ in range(K_calls(args)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = run_funnel_scps(p)
+            torch.cuda.synchronize()
+            walls.append(time.perf_counter() - t0)
+        n_rounds = len(res["rounds"])
+        out = {"metric": "particle-steps/s (whole SCPS iteration, wall clock)",
+               "value": n_rounds * p.n_replicas * p.n_steps * len(walls) / sum(walls),
+               "unit": "particle-steps/s", "ms_per_step": 1e3 * sum(walls) / len(walls),
+               "steps": len(walls), "warmup": 1,
+               "config": {"workload": f"funnel SCPS: {n_rounds} rounds x {p.n_replicas} replicas x "
+                                      f"{p.n_steps} steps, k_R {p.k_R}, lambda {p.lam}, k_s {p.k_s}, "
+                                      f"k_w {p.k_w}",
+                          "reactive_per_round": [int(len(r["reactive"])) for r in res["rounds"]]}}
     elif args.workload == "hvp":
         from paper_1705_02180_gb300.autograd import force_norm_action
         c = synth.make_chain(35, seed=1)

@@ -69,11 +69,12 @@ enum { SCPS_BIAS_NONE = 0,
        SCPS_BIAS_RMD_CONTACTS = 1,  /* chains: ratchet of Eq. (FrMD) on z(X) of Eq. (zrMD) */
        SCPS_BIAS_RMD_TOY = 2,       /* two-dimensional models: ratchet on z = (x - x_ref)^2 */
        SCPS_BIAS_RMD_RADIAL = 3,    /* two-dimensional models: ratchet on z = sqrt(x^2 + y^2) */
-       SCPS_BIAS_TUBE = 4           /* two-dimensional models: the self-consistent rMD forces
-                                       F^s and F^w of Eq. (Fs) and Eq. (Fw) on the tube
-                                       variables s_lambda and w_lambda of a reference path
-                                       (Eq. sX, Eq. wX with the average path in place of the
-                                       instantaneous one), configuration-space distance */ };
+       SCPS_BIAS_TUBE = 4           /* the self-consistent rMD forces F^s and F^w of Eq. (Fs)
+                                       and Eq. (Fw) on the tube variables s_lambda and w_lambda
+                                       of a reference path (Eq. sX, Eq. wX with the average path
+                                       in place of the instantaneous one): configuration-space
+                                       distance for the two-dimensional models, contact-map
+                                       distance for chains */ };
 enum { SCPS_ZM_FROM_X = 0, SCPS_ZM_VALUE = 1 };
 
 /* ----------------------------------------------------------------- descriptors */
@@ -155,6 +156,11 @@ typedef struct {
     const double* ref;
     const double* ref_time;
     double lambda, k_s, k_w, t_path;
+    /* SCPS_BIAS_TUBE on chains (resident form): per topology (host) the average contact maps
+       <C_p(t'_k)> over the topology's native-contact list (the pairs and x_native above),
+       n_ref x n_pairs[t], slice-major. D_k = sum_p (C_p(X) - <C_p(t'_k)>)^2 / sum_p C0_p^2
+       replaces |X - <X(t'_k)>|^2; n_ref <= 128. */
+    const double* const* ref_maps;
 } scps_bias_desc;
 
 typedef struct {
@@ -212,7 +218,7 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream);
  * `topo` (no bias force, no state change). X: device float, n_frames x
  * n_atoms x 3. U: device double, n_frames (total physical energy). F: device
  * float, n_frames x n_atoms x 3, may be NULL. z: device double, n_frames, may
- * be NULL (needs a contact bias). Stream-ordered. */
+ * be NULL (needs the contact list of a contact or tube bias). Stream-ordered. */
 int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const float* X,
                        double* U, float* F, double* z, void* stream);
 
@@ -247,11 +253,14 @@ int scps_get_status(scps_system* s, int32_t* per_replica);
 
 int scps_get_info(const scps_system* s, scps_info* info);
 
-/* Average path of selected replicas (step 3 of the SCPS iteration): for the
- * two-dimensional models, out[k] = mean over the replicas in `replicas` (host,
- * n_sel indices) of their saved frame k, k = 0 .. n_frames-1, oldest first
- * (host, n_frames x 2). Every selected replica must still hold all its frames
- * (n_saved <= max_frames) and have at least n_frames of them. Synchronous. */
+/* Average path of selected replicas (step 3 of the SCPS iteration; Eq. avCij):
+ * for the two-dimensional models, out[k] = mean over the replicas in `replicas`
+ * (host, n_sel indices) of their saved frame k, k = 0 .. n_frames-1, oldest first
+ * (host, n_frames x 2); for chains (one topology among the selected replicas, whose
+ * contact list a contact or tube bias has set), out[k * n_pairs + p] = mean of
+ * C_p of Eq. (Cij) over the selected frames k (host, n_frames x n_pairs, FP64).
+ * Every selected replica must still hold all its frames (n_saved <= max_frames)
+ * and have at least n_frames of them. Synchronous. */
 int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, int32_t n_frames,
                       double* out);
 

@@ -86,6 +86,12 @@ def lib():
         _lib.orc_run_toy.restype = C.c_int
         _lib.orc_num_threads.restype = C.c_int
         _lib.orc_hvp.argtypes = [P, P, P, P, P]
+        _lib.orc_tube_chain_vars.argtypes = [P, C.c_int, P, P, P, P, P]
+        _lib.orc_tube_chain_vars.restype = None
+        _lib.orc_run_baoab_tube.argtypes = [P, P, C.c_int, P, P, P, P, P, C.c_uint64, C.c_double,
+                                            C.c_double, C.c_double, C.c_int64, C.c_int, C.c_int,
+                                            P, P, P, P, P, P]
+        _lib.orc_run_baoab_tube.restype = C.c_int
         _lib.orc_funnel.argtypes = [C.c_double, C.c_double, P, P]
         _lib.orc_funnel.restype = None
         _lib.orc_tube_vars.argtypes = [C.c_int, P, P, C.c_double, C.c_double, C.c_double,
@@ -199,6 +205,58 @@ class BiasZ:
         g = np.zeros((n, 3)) if grad else None
         z = lib().orc_z(C.byref(self.s), n, _p(x), _p(g))
         return (z, g) if grad else z
+
+
+class Tube(C.Structure):
+    _fields_ = [("nc", C.c_int), ("pairs", C.c_void_p), ("C0", C.c_void_p), ("r0", C.c_double),
+                ("K", C.c_int), ("A", C.c_void_p), ("tref", C.c_void_p), ("lam", C.c_double),
+                ("k_s", C.c_double), ("k_w", C.c_double), ("t_path", C.c_double)]
+
+
+class TubeChain:
+    """Contact-map tube variables s_lambda, w_lambda (Eq. sX, Eq. wX with the average maps
+    A (K, n_pairs) at times tref) on the native-contact list, and their forces."""
+
+    def __init__(self, pairs, x_native, A, tref, lam, k_s, k_w, t_path, r0=0.75):
+        self.pairs = _i32(np.reshape(pairs, (-1, 2)))
+        self.C0 = np.zeros(len(self.pairs))
+        lib().orc_native_map(len(self.pairs), _p(self.pairs), r0, 0.0, _p(_f64(x_native)),
+                             _p(self.C0))
+        self.A = _f64(np.reshape(A, (-1, len(self.pairs))))
+        self.tref = _f64(tref)
+        self.s = Tube(len(self.pairs), _p(self.pairs), _p(self.C0), r0, len(self.tref), _p(self.A),
+                      _p(self.tref), lam, k_s, k_w, t_path)
+
+    def vars(self, x, grad=False):
+        x = _f64(x)
+        n = x.shape[0]
+        sv, wv = C.c_double(0.0), C.c_double(0.0)
+        gs = np.zeros((n, 3)) if grad else None
+        gw = np.zeros((n, 3)) if grad else None
+        lib().orc_tube_chain_vars(C.byref(self.s), n, _p(x), C.byref(sv), C.byref(wv), _p(gs), _p(gw))
+        return (sv.value, wv.value, gs, gw) if grad else (sv.value, wv.value)
+
+
+def run_baoab_tube(ff: ForceField, tube: TubeChain, x, v, smw, step, rep_id, seed, dt, gamma, kT,
+                   n_steps, save_every=0, max_frames=0, T_acc=None):
+    """BAOAB runs with F^s + F^w of the contact-map tube variables; smw (R, 2) running minima."""
+    x = _f64(x).copy()
+    v = _f64(v).copy()
+    R = x.shape[0]
+    smw = _f64(np.reshape(smw, (R, 2))).copy()
+    step = np.ascontiguousarray(step, np.int64).copy()
+    rep_id = _i32(rep_id)
+    T = np.zeros(R) if T_acc is None else _f64(T_acc).copy()
+    mf = max_frames if save_every > 0 else 0
+    frames = np.zeros((R, max(mf, 1), ff.n, 3))
+    fz = np.zeros((R, max(mf, 1)))
+    fzm, fT = fz.copy(), fz.copy()
+    ns = np.zeros(R, np.int32)
+    lib().orc_run_baoab_tube(C.byref(ff.s), C.byref(tube.s), R, _p(x), _p(v), _p(smw), _p(step),
+                             _p(rep_id), seed, dt, gamma, kT, n_steps, save_every, mf, _p(frames),
+                             _p(fz), _p(fzm), _p(fT), _p(ns), _p(T))
+    return dict(x=x, v=v, smw=smw, step=step, T=T, frames=frames[:, :mf], z=fz[:, :mf],
+                zmin=fzm[:, :mf], Tf=fT[:, :mf], n_saved=ns)
 
 
 def ratchet(z, zm, k_R):

@@ -587,3 +587,166 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Contact-map tube variables and the self-consistent rMD forces (chains)      */
+/* ------------------------------------------------------------------------- */
+/* Eq. (sX), Eq. (wX) with the average maps A_k = <C(t'_k)> in place of the
+ * instantaneous ones, on the native-contact list p = (i, j):
+ *   D_k = sum_p (C_p(X) - A_kp)^2 / sum_p C0_p^2,
+ *   s = 1 - (1/t) sum_k t'_k e^{-lambda D_k} / sum_k e^{-lambda D_k},
+ *   w = -(1/lambda) log sum_k e^{-lambda D_k};
+ * forces of Eq. (Fs), Eq. (Fw): F^s = -k_s grad s (s - s_m) theta(s - s_m), F^w alike. */
+typedef struct {
+    int nc;
+    const int32_t* pairs;  /* nc x 2 */
+    const double* C0;      /* nc: native map entries (for the norm) */
+    double r0;
+    int K;
+    const double* A;       /* K x nc average maps, slice-major */
+    const double* tref;    /* K times t'_k */
+    double lambda, k_s, k_w, t_path;
+} orc_tube;
+
+/* s, w and (optional, n x 3 each, overwritten) their gradients. */
+void orc_tube_chain_vars(const orc_tube* tb, int n, const double* x, double* s, double* w,
+                         double* grad_s, double* grad_w) {
+    const int nc = tb->nc, K = tb->K;
+    double n0 = 0.0;
+    for (int p = 0; p < nc; ++p) n0 += tb->C0[p] * tb->C0[p];
+    double* C = (double*)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1));
+    double* dC = (double*)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1));
+    double* D = (double*)malloc(sizeof(double) * (size_t)K);
+    for (int p = 0; p < nc; ++p) {
+        const int i = tb->pairs[2 * p], j = tb->pairs[2 * p + 1];
+        double r2 = 0.0;
+        for (int k = 0; k < 3; ++k) r2 += (x[3 * j + k] - x[3 * i + k]) * (x[3 * j + k] - x[3 * i + k]);
+        const double u = r2 / (tb->r0 * tb->r0);
+        const double num = 1.0 + u + u * u;
+        C[p] = num / (num + u * u * u + u * u * u * u);
+        dC[p] = contact_dC_du(u);
+    }
+    double dmin = INFINITY;
+    for (int k = 0; k < K; ++k) {
+        double d = 0.0;
+        for (int p = 0; p < nc; ++p) d += (C[p] - tb->A[(size_t)k * nc + p]) * (C[p] - tb->A[(size_t)k * nc + p]);
+        D[k] = d / n0;
+        if (D[k] < dmin) dmin = D[k];
+    }
+    double Z = 0.0, Zt = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double e = exp(-tb->lambda * (D[k] - dmin));
+        Z += e;
+        Zt += tb->tref[k] * e;
+    }
+    const double tbar = Zt / Z;
+    *s = 1.0 - tbar / tb->t_path;
+    *w = dmin - log(Z) / tb->lambda;
+    if (grad_s || grad_w) {
+        /* dD_k/dC_p = 2 (C_p - A_kp) / n0; ds/dD_k = (lambda/t) pi_k (t'_k - tbar); dw/dD_k = pi_k */
+        if (grad_s) memset(grad_s, 0, sizeof(double) * 3 * (size_t)n);
+        if (grad_w) memset(grad_w, 0, sizeof(double) * 3 * (size_t)n);
+        for (int p = 0; p < nc; ++p) {
+            double bs = 0.0, bw = 0.0; /* ds/dC_p, dw/dC_p */
+            for (int k = 0; k < K; ++k) {
+                const double pi = exp(-tb->lambda * (D[k] - dmin)) / Z;
+                const double dD = 2.0 * (C[p] - tb->A[(size_t)k * nc + p]) / n0;
+                bs += tb->lambda / tb->t_path * pi * (tb->tref[k] - tbar) * dD;
+                bw += pi * dD;
+            }
+            /* dC_p/dx_j = C'(u) 2 (x_j - x_i) / r0^2, x_i the negative */
+            const int i = tb->pairs[2 * p], j = tb->pairs[2 * p + 1];
+            for (int k = 0; k < 3; ++k) {
+                const double g = dC[p] * 2.0 * (x[3 * j + k] - x[3 * i + k]) / (tb->r0 * tb->r0);
+                if (grad_s) {
+                    grad_s[3 * j + k] += bs * g;
+                    grad_s[3 * i + k] -= bs * g;
+                }
+                if (grad_w) {
+                    grad_w[3 * j + k] += bw * g;
+                    grad_w[3 * i + k] -= bw * g;
+                }
+            }
+        }
+    }
+    free(C);
+    free(dC);
+    free(D);
+}
+
+/* BAOAB runs with the physical forces plus F^s + F^w (same step order, noise and
+ * outputs as orc_run_baoab). smw: R x 2 running minima (s_m, w_m), in/out; frames
+ * record s (fz) and its running minimum (fzm). */
+int orc_run_baoab_tube(const orc_ff* ff, const orc_tube* tb, int R, double* x, double* v,
+                       double* smw, int64_t* step, const int32_t* rep_id, uint64_t seed,
+                       double dt, double gamma, double kT, int64_t n_steps, int save_every,
+                       int max_frames, double* frames, double* fz, double* fzm, double* fT,
+                       int32_t* n_saved, double* T_acc) {
+    const int n = ff->n;
+    const double c1 = exp(-gamma * dt);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int r = 0; r < R; ++r) {
+        double* xr = x + (size_t)r * n * 3;
+        double* vr = v + (size_t)r * n * 3;
+        double* F = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+        double* gs = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+        double* gw = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+        int saved = 0;
+        double s = 0.0, w = 0.0, fb2 = 0.0;
+        for (int64_t it = -1; it < n_steps; ++it) {
+            if (it >= 0) { /* B A O A */
+                const uint32_t st = (uint32_t)step[r];
+                for (int i = 0; i < n; ++i) {
+                    const double im = 1.0 / ff->mass[i];
+                    double xi[4];
+                    orc_normals4(seed, (uint32_t)i, (uint32_t)rep_id[r], st, 0u, xi);
+                    const double sd = sqrt((1.0 - c1 * c1) * kT * im);
+                    for (int k = 0; k < 3; ++k) {
+                        double vv = vr[3 * i + k] + 0.5 * dt * F[3 * i + k] * im;
+                        double xx = xr[3 * i + k] + 0.5 * dt * vv;
+                        vv = c1 * vv + sd * xi[k];
+                        xx += 0.5 * dt * vv;
+                        vr[3 * i + k] = vv;
+                        xr[3 * i + k] = xx;
+                    }
+                }
+            }
+            /* forces at the new configuration */
+            double E[ORC_E_N];
+            orc_forces(ff, xr, F, E);
+            orc_tube_chain_vars(tb, n, xr, &s, &w, gs, gw);
+            const double cs = orc_ratchet(s, &smw[2 * r], tb->k_s);
+            const double cw = orc_ratchet(w, &smw[2 * r + 1], tb->k_w);
+            fb2 = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double f2 = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double fb = cs * gs[3 * i + k] + cw * gw[3 * i + k];
+                    F[3 * i + k] += fb;
+                    f2 += fb * fb;
+                }
+                fb2 += f2 / ff->mass[i];
+            }
+            if (it < 0) continue;
+            for (int i = 0; i < n; ++i) /* B */
+                for (int k = 0; k < 3; ++k) vr[3 * i + k] += 0.5 * dt * F[3 * i + k] / ff->mass[i];
+            step[r] += 1;
+            if (T_acc) T_acc[r] += dt * fb2 / gamma;
+            if (save_every > 0 && step[r] % save_every == 0 && saved < max_frames) {
+                const size_t slot = (size_t)r * max_frames + saved;
+                if (frames) memcpy(frames + slot * n * 3, xr, sizeof(double) * 3 * (size_t)n);
+                if (fz) fz[slot] = s;
+                if (fzm) fzm[slot] = smw[2 * r];
+                if (fT) fT[slot] = T_acc ? T_acc[r] : 0.0;
+                saved++;
+            }
+        }
+        if (n_saved) n_saved[r] = saved;
+        free(F);
+        free(gs);
+        free(gw);
+    }
+    return 0;
+}

@@ -52,7 +52,7 @@ class BiasDesc(C.Structure):
                 ("pairs", _P), ("x_native", _P), ("zm_init", C.c_int32),
                 ("zm_value", C.c_double), ("toy_x_ref", C.c_double), ("n_ref", C.c_int32),
                 ("ref", _P), ("ref_time", _P), ("lam", C.c_double), ("k_s", C.c_double),
-                ("k_w", C.c_double), ("t_path", C.c_double)]
+                ("k_w", C.c_double), ("t_path", C.c_double), ("ref_maps", _P)]
 
 
 class Info(C.Structure):
@@ -232,8 +232,30 @@ class System:
         pp = (_P * nt)(*[p.ctypes.data for p in pairs])
         xp = (_P * nt)(*[x.ctypes.data for x in xn])
         self._bias_keep = [pairs, xn, n_pairs, pp, xp]
+        self._n_pairs = [len(p) for p in pairs]
         b = BiasDesc(BIAS_RMD_CONTACTS, k_R, r0, _ptr(n_pairs), C.cast(pp, _P), C.cast(xp, _P),
                      zm_init, zm_value, 0.0)
+        check(load().scps_set_bias(self.h, C.byref(b)))
+
+    def set_contact_tube_bias(self, pairs_per_topology, x_native_per_topology, ref_maps_per_topology,
+                              ref_time, lam, k_s, k_w, t_path, r0=0.75, zm_init=ZM_FROM_X,
+                              zm_value=0.0):
+        """Chains: forces F^s, F^w on the contact-map tube variables of reference maps
+        <C_p(t'_k)> (per topology an array (K, n_pairs) over the contact list)."""
+        nt = len(pairs_per_topology)
+        pairs = [_i32(np.reshape(p, (-1, 2))) for p in pairs_per_topology]
+        xn = [_f64(x) for x in x_native_per_topology]
+        maps = [_f64(np.reshape(a, (len(ref_time), len(p)))) for a, p in zip(ref_maps_per_topology, pairs)]
+        tm = _f64(np.reshape(ref_time, (-1,)))
+        n_pairs = _i32([len(p) for p in pairs])
+        pp = (_P * nt)(*[p.ctypes.data for p in pairs])
+        xp = (_P * nt)(*[x.ctypes.data for x in xn])
+        mp = (_P * nt)(*[a.ctypes.data for a in maps])
+        self._bias_keep = [pairs, xn, maps, tm, n_pairs, pp, xp, mp]
+        self._n_pairs = [len(p) for p in pairs]
+        b = BiasDesc(BIAS_TUBE, 0.0, r0, _ptr(n_pairs), C.cast(pp, _P), C.cast(xp, _P), zm_init,
+                     zm_value, 0.0, len(tm), None, _ptr(tm), lam, k_s, k_w, t_path,
+                     C.cast(mp, _P))
         check(load().scps_set_bias(self.h, C.byref(b)))
 
     def set_toy_bias(self, k_R, x_ref=1.0, zm_init=ZM_FROM_X, zm_value=0.0):
@@ -258,9 +280,14 @@ class System:
         check(load().scps_set_bias(self.h, C.byref(b)))
 
     def path_average(self, replicas, n_frames):
-        """Two-dimensional models: mean of saved frames 0 .. n_frames-1 over `replicas`."""
+        """Mean of saved frames 0 .. n_frames-1 over `replicas`: positions for the
+        two-dimensional models, contact maps (n_frames, n_pairs) for chains."""
         sel = _i32(np.asarray(replicas).reshape(-1))
-        out = np.zeros((int(n_frames), 2))
+        if self.model == MODEL_CHAIN:
+            topo = int(np.asarray(self.replica_topology)[sel[0]])
+            out = np.zeros((int(n_frames), self._n_pairs[topo]))
+        else:
+            out = np.zeros((int(n_frames), 2))
         check(load().scps_path_average(self.h, len(sel), _ptr(sel), int(n_frames), _ptr(out)))
         return out
 

@@ -207,6 +207,39 @@ __global__ void k_path_average_2d(StateDev st, int max_frames, int K, const int*
     out[k] = make_double2(sx / n_sel, sy / n_sel);
 }
 
+// Average contact maps of selected chain replicas (step 3 of the SCPS iteration):
+// out[k][p] = mean over the selection of C_p (Eq. Cij, FP64 from the stored FP32
+// frame) of saved frame k, summed in selection order; one thread per (k, p).
+__global__ void k_path_average_contacts(StateDev st, const int2* __restrict__ con_ij, int nc, int n,
+                                        const long long* __restrict__ frame_off, int n_sel, int K,
+                                        double inv_r0sq, double* __restrict__ out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)K * nc) return;
+    const int k = (int)(idx / nc), p = (int)(idx % nc);
+    const int2 ij = con_ij[p];
+    double sum = 0.0;
+    for (int q = 0; q < n_sel; ++q) {
+        const float* fr = st.frames + 3 * (frame_off[q] + (long long)k * n);
+        double d2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double d = (double)fr[3 * ij.y + c] - (double)fr[3 * ij.x + c];
+            d2 += d * d;
+        }
+        const double u = d2 * inv_r0sq, num = 1.0 + u + u * u;
+        sum += num / (num + u * u * u + u * u * u * u);
+    }
+    out[idx] = sum / n_sel;
+}
+
+cudaError_t launch_path_average_contacts(const StateDev& st, const int2* con_ij, int nc, int n,
+                                         const long long* frame_off, int n_sel, int K,
+                                         double inv_r0sq, double* out, cudaStream_t stream) {
+    const long long total = (long long)K * nc;
+    k_path_average_contacts<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
+        st, con_ij, nc, n, frame_off, n_sel, K, inv_r0sq, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_path_average_2d(const StateDev& st, int max_frames, int K, const int* sel,
                                    int n_sel, double2* out, cudaStream_t stream) {
     k_path_average_2d<<<(K + 127) / 128, 128, 0, stream>>>(st, max_frames, K, sel, n_sel, out);

@@ -56,6 +56,12 @@ struct Scalars {
     double zm, z, factor, epot, T;
     long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity
     long long red_e[2][32];  // per-warp shares of the potential energy (units of 2^-20)
+    // contact-map tube bias
+    int work_next2[2];                  // counter of the second work phase, by parity
+    double sm, wm;                      // running minima of s_lambda and w_lambda
+    float gam_sum;                      // sum_k gamma_k
+    float gam[kMaxTubeK];               // gamma_k = dF/dD_k weights of the evaluated step
+    long long red_d[2][kMaxTubeK];      // this CTA's share of sum_p (C_p - A_kp)^2 (2^-40), by parity
 };
 
 __device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int ncon_max) {
@@ -362,6 +368,151 @@ __device__ __forceinline__ float box_gap2(float4 al, float4 ah, float4 bl, float
     return fmaf(gx, gx, fmaf(gy, gy, gz * gz));
 }
 
+// C(u) of Eq. (Cij) in FP32, u = (r / r0)^2 (the tube variables need no more).
+__device__ __forceinline__ float contact_C_f32(float u) {
+    const float u2 = u * u;
+    const float num = 1.0f + u + u2;
+    return num / (num + u2 * u + u2 * u2);
+}
+
+// Contact-map tube bias, first pass over one chunk of 32 native contacts: this
+// CTA's share of sum_p (C_p(X) - <C_p(t'_k)>)^2 for every reference slice k.
+// Lane l computes C of contact c0 + l; then lane l takes slices l, l + 32, ...
+// and runs over the chunk's contacts (C broadcast by shuffle).
+__device__ __forceinline__ void tube_pass1(const Shared& sm, Scalars& sc, const TopoDev& tp,
+                                           const RunParams& P, int b, int c0, int lane) {
+    const int c = c0 + lane;
+    float C = 0.f;
+    if (c < tp.n_contacts) {
+        const int2 ij = tp.con_ij[c];
+        const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
+        const float dx = q.x - a.x, dy = q.y - a.y, dz = q.z - a.z;
+        C = contact_C_f32(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq);
+    }
+    const int K = P.tube_k;
+    float acc[kMaxTubeK / 32];
+#pragma unroll
+    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) acc[blk] = 0.f;
+    const int nq = min(32, tp.n_contacts - c0);
+    for (int q = 0; q < nq; ++q) {
+        const float Cq = __shfl_sync(kFull, C, q);
+        const float* row = tp.tube_A + (size_t)(c0 + q) * K;
+#pragma unroll
+        for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+            const int kk = blk * 32 + lane;
+            if (kk < K) {
+                const float d = Cq - row[kk];
+                acc[blk] = fmaf(d, d, acc[blk]);
+            }
+        }
+    }
+#pragma unroll
+    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+        const int kk = blk * 32 + lane;
+        if (kk < K)
+            atomicAdd((unsigned long long*)&sc.red_d[b][kk],
+                      (unsigned long long)__float2ll_rn(acc[blk] * 1099511627776.0f));  // 2^40
+    }
+}
+
+// Contact-map tube bias, second pass for contact c = (i, p): with gamma_k the
+// weights of the ratchet forces on the slices (dF/dD_k), the force on the atoms
+// of the contact is beta grad C with beta = (2/N0) sum_k gamma_k (C - <C(t'_k)>);
+// h = beta C'(u) goes to G like the z gradient (F = -2/r0^2 G).
+__device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, const TopoDev& tp,
+                                           const RunParams& P, long long* G, int c) {
+    if (c >= tp.n_contacts) return;
+    const int2 ij = tp.con_ij[c];
+    const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
+    const float dx = q.x - a.x, dy = q.y - a.y, dz = q.z - a.z;
+    const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq;
+    const float C = contact_C_f32(u);
+    const int K = P.tube_k;
+    const float* row = tp.tube_A + (size_t)c * K;
+    float dot = 0.f;
+    for (int k = 0; k < K; ++k) dot = fmaf(sc.gam[k], row[k], dot);
+    const float h = 2.0f * tp.tube_inv_n0 * (C * sc.gam_sum - dot) * contact_dC_du(u);
+    const long long gx = f2fix(h * dx), gy = f2fix(h * dy), gz = f2fix(h * dz);
+    const int nta = sm.nta;
+    atomicAdd((unsigned long long*)&G[ij.x], (unsigned long long)gx);
+    atomicAdd((unsigned long long*)&G[nta + ij.x], (unsigned long long)gy);
+    atomicAdd((unsigned long long*)&G[2 * nta + ij.x], (unsigned long long)gz);
+    atomicAdd((unsigned long long*)&G[ij.y], (unsigned long long)(-gx));
+    atomicAdd((unsigned long long*)&G[nta + ij.y], (unsigned long long)(-gy));
+    atomicAdd((unsigned long long*)&G[2 * nta + ij.y], (unsigned long long)(-gz));
+}
+
+// Tube variables and their ratchets from the summed slice distances (warp 0):
+// D_k = sum_p (C_p - <C_p(t'_k)>)^2 / N0, pi_k = exp(-lambda D_k) / sum,
+// w = -(1/lambda) log sum_k exp(-lambda D_k), s = 1 - (1/t) sum_k t'_k pi_k
+// (Eq. sX, Eq. wX with the average maps); F^s, F^w of Eq. (Fs), Eq. (Fw) through
+// gamma_k = c_s ds/dD_k + c_w dw/dD_k, ds/dD_k = (lambda/t) pi_k (t'_k - <t'>),
+// dw/dD_k = pi_k. Sums over k are in a fixed order (lane order, then a fixed tree).
+template <int CL>
+__device__ void tube_decide(Scalars& sc, const TopoDev& tp, const RunParams& P, int b, int lane) {
+    const int K = P.tube_k;
+    double D[kMaxTubeK / 32];
+    double dmin = 1e300;
+#pragma unroll
+    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+        const int k = blk * 32 + lane;
+        D[blk] = 1e300;
+        if (k < K) {
+            long long t = 0;
+            for (int q = 0; q < CL; ++q) t += rank_ptr<CL>(&sc.red_d[b][0], q)[k];
+            D[blk] = (double)t * 9.094947017729282e-13 * (double)tp.tube_inv_n0;  // 2^-40
+            dmin = fmin(dmin, D[blk]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(kFull, dmin, o));
+    double e[kMaxTubeK / 32], Z = 0.0, Zt = 0.0;
+#pragma unroll
+    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+        const int k = blk * 32 + lane;
+        e[blk] = k < K ? exp(-P.tube_lambda * (D[blk] - dmin)) : 0.0;
+        Z += e[blk];
+        Zt += k < K ? e[blk] * P.tube_time[k] : 0.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Z += __shfl_down_sync(kFull, Z, o);
+        Zt += __shfl_down_sync(kFull, Zt, o);
+    }
+    Z = __shfl_sync(kFull, Z, 0);
+    Zt = __shfl_sync(kFull, Zt, 0);
+    const double tbar = Zt / Z;
+    const double sv = 1.0 - tbar / P.tube_t;
+    const double wv = dmin - log(Z) / P.tube_lambda;
+    double cs = 0.0, cw = 0.0;  // ratchets, theta(0) = 1
+    const double sm0 = sc.sm, wm0 = sc.wm;
+    if (!(sv < sm0)) cs = -P.tube_ks * (sv - sm0);
+    if (!(wv < wm0)) cw = -P.tube_kw * (wv - wm0);
+    float gsum = 0.f;
+#pragma unroll
+    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+        const int k = blk * 32 + lane;
+        if (k < K) {
+            const double pi = e[blk] / Z;
+            const double g = cs * P.tube_lambda / P.tube_t * pi * (P.tube_time[k] - tbar) + cw * pi;
+            sc.gam[k] = (float)g;
+            gsum += (float)g;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gsum += __shfl_down_sync(kFull, gsum, o);
+    __syncwarp();
+    if (lane == 0) {
+        if (sv < sm0) sc.sm = sv;
+        if (wv < wm0) sc.wm = wv;
+        sc.gam_sum = gsum;
+        sc.z = sv;  // frames record s_lambda and its running minimum
+        sc.zm = fmin(sm0, sv);
+        sc.factor = 0.5;  // the update's F = -4 factor / r0^2 G is then -2/r0^2 G
+        sc.bias_on = (cs != 0.0 || cw != 0.0) ? 1 : 0;
+    }
+}
+
 // Summed fixed-point partials (this CTA + peer) of one atom: force and bias gradient.
 struct AtomSums {
     long long f[3], g[3];
@@ -404,7 +555,7 @@ __device__ __forceinline__ void load_sums(const Shared& sm, int b, int peer, int
 // CTA also draws the Gaussian numbers of that step's O half step for all atoms
 // (each CTA of a cluster integrates every atom). On return the CTA is
 // synchronised.
-template <int ELEC, bool ENERGY, int CL>
+template <int ELEC, bool ENERGY, int CL, bool TUBE>
 __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
                          bool do_ratchet, uint32_t rep_id, long long noise_step) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -421,7 +572,8 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     // items from a counter in their own shared memory; the two halves of a tile pair
     // are listed in alternating order, so both CTAs get half of the diagonal items.
     const int n_half = 2 * ntp;
-    const int ncon = P.bias == 1 ? tp.n_contacts : 0;
+    const bool tube = TUBE && do_ratchet;  // contact-map tube bias: two work phases
+    const int ncon = (P.bias == 1 || P.bias == 5) ? tp.n_contacts : 0;  // frames: z too
     const int e_con = n_half + (ncon + kChunk - 1) / kChunk;
     const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
     const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
@@ -448,8 +600,11 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             }
             if (ENERGY) e += f2fix(ep);
         } else if (k < e_con) {
-            const int c = (k - n_half) * kChunk + lane;
-            if (c < ncon) zacc += contact_term(sm, G, tp, P, c);
+            const int c0 = (k - n_half) * kChunk;
+            if (tube)
+                tube_pass1(sm, sc, tp, P, b, c0, lane);
+            else if (c0 + lane < ncon)
+                zacc += contact_term(sm, G, tp, P, c0 + lane);
         } else if (k < e_bond) {
             const int q = (k - e_con) * kChunk + lane;
             if (q < tp.n_bonds) {
@@ -477,6 +632,8 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         sm.Fp[b ^ 1][i] = 0;
         sm.Gp[b ^ 1][i] = 0;
     }
+    if (tube)
+        for (int i = tid; i < P.tube_k; i += blockDim.x) sc.red_d[b ^ 1][i] = 0;
     // shares of z, energy and flags from every CTA of the cluster (integer sums)
     if (warp == 0) {
         long long zt = 0, et = 0;
@@ -494,10 +651,10 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             if (ENERGY) sc.epot = (double)et * 9.5367431640625e-07;  // 2^-20
             if (fl) sc.status |= SCPS_FLAG_FORCE_RANGE;
             double factor = 0.0;
-            if (P.bias == 1) {
+            if (P.bias == 1 || (P.bias == 5 && !tube)) {  // (frame evaluation: z as well)
                 const double z = (double)zt * 9.094947017729282e-13;  // 2^-40
                 sc.z = z;
-                if (do_ratchet) {  // Eq. (FrMD) with theta(0) = 1
+                if (do_ratchet && P.bias == 1) {  // Eq. (FrMD) with theta(0) = 1
                     if (z < sc.zm)
                         sc.zm = z;
                     else
@@ -508,8 +665,22 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             sc.bias_on = factor != 0.0;
             sc.work_next[b] = 0;  // every pull of this evaluation is done
         }
+        if (tube) tube_decide<CL>(sc, tp, P, b, lane);
     }
     __syncthreads();
+    if (tube) {  // second work phase: the bias force per contact, then G is complete
+        int* counter2 = &sc.work_next2[b];
+        const int n2 = (ncon + kChunk - 1) / kChunk;
+        for (;;) {
+            int m = 0;
+            if (lane == 0) m = atomicAdd(counter2, 1);
+            const int k = __shfl_sync(kFull, m, 0) * CL + rank;
+            if (k >= n2) break;
+            tube_pass2(sm, sc, tp, P, G, k * kChunk + lane);
+        }
+        cluster_barrier<CL>();  // the peer reads this CTA's G next
+        if (tid == 0) sc.work_next2[b] = 0;
+    }
 }
 
 __device__ void tile_pair_table(const Shared& sm, int nt) {
@@ -526,7 +697,7 @@ __device__ void tile_pair_table(const Shared& sm, int nt) {
 
 }  // namespace
 
-template <int ELEC, int CL>
+template <int ELEC, int CL, bool TUBE>
 __global__ void __launch_bounds__(1024, 1)
 k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, StateDev st,
            RunParams P, int nta, int ntp_max, int ncon_max) {
@@ -572,6 +743,14 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         sc.bias_on = 0;
         sc.work_next[0] = 0;
         sc.work_next[1] = 0;
+        sc.work_next2[0] = 0;
+        sc.work_next2[1] = 0;
+        sc.sm = st.sm[r];
+        sc.wm = st.wm[r];
+    }
+    for (int i = tid; i < kMaxTubeK; i += blockDim.x) {
+        sc.red_d[0][i] = 0;
+        sc.red_d[1][i] = 0;
     }
     long long step = st.step[r];
     __syncthreads();
@@ -581,7 +760,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
     const float hdt = P.half_dt;
     if (sc.status == 0 && P.n_steps > 0) {
         // the O half step that follows an evaluation uses the noise of the same step index
-        evaluate<ELEC, false, CL>(sm, sc, tp, P, (int)(step & 1), true, rep.rep_id, step);
+        evaluate<ELEC, false, CL, TUBE>(sm, sc, tp, P, (int)(step & 1), true, rep.rep_id, step);
         // position of `step` in the save cycle and ring slot of the next frame, kept as
         // counters so that the loop has no 64-bit divisions
         int save_phase = P.save_interval > 0 ? (int)(step % P.save_interval) : -1;
@@ -678,9 +857,9 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             if (save_phase >= 0) save_phase = save_phase + 1 == P.save_interval ? 0 : save_phase + 1;
             const bool save_next = save_phase == 0;
             if (save_next)
-                evaluate<ELEC, true, CL>(sm, sc, tp, P, nb, true, rep.rep_id, step);
+                evaluate<ELEC, true, CL, TUBE>(sm, sc, tp, P, nb, true, rep.rep_id, step);
             else
-                evaluate<ELEC, false, CL>(sm, sc, tp, P, nb, true, rep.rep_id, step);
+                evaluate<ELEC, false, CL, TUBE>(sm, sc, tp, P, nb, true, rep.rep_id, step);
             if (sc.status != 0) break;  // force out of range: frozen before the update
         }
     }
@@ -696,6 +875,8 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         if (tid == 0) {
             st.zm[r] = sc.zm;
             st.z[r] = sc.z;
+            st.sm[r] = sc.sm;
+            st.wm[r] = sc.wm;
             st.T[r] = sc.T;
             st.status[r] = sc.status;
             st.step[r] = step;
@@ -742,7 +923,7 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
     __syncthreads();
     all_boxes(sm, n);
     __syncthreads();
-    evaluate<ELEC, true, 1>(sm, sc, tp, P, 0, false, 0u, -1);
+    evaluate<ELEC, true, 1, false>(sm, sc, tp, P, 0, false, 0u, -1);
     if (F) {
         float* ff_out = F + f * n * 3;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -766,12 +947,12 @@ size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max) {
            sizeof(float2) * nta + sizeof(uint32_t) * ntp4;
 }
 
-template <int ELEC, int CL>
+template <int ELEC, int CL, bool TUBE>
 static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, const StateDev& st,
                                      const RunParams& P, int nta, int ntp_max, int ncon_max,
                                      int threads, cudaStream_t stream) {
     const size_t smem = resident_smem_bytes(nta, ntp_max, ncon_max);
-    auto kern = k_resident<ELEC, CL>;
+    auto kern = k_resident<ELEC, CL, TUBE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -795,11 +976,19 @@ template <int CL>
 static cudaError_t launch_resident_cl(int elec, const TopoDev* topos, const RepDev* reps,
                                       const StateDev& st, const RunParams& P, int nta, int ntp_max,
                                       int ncon_max, int threads, cudaStream_t stream) {
+    if (P.bias == 5) {  // contact-map tube bias: its own instantiation
+        switch (elec) {
+            case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+            case ELEC_RF: return launch_resident_t<ELEC_RF, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+            case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+            default: return launch_resident_t<ELEC_NONE, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+        }
+    }
     switch (elec) {
-        case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-        case ELEC_RF: return launch_resident_t<ELEC_RF, CL>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-        case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-        default: return launch_resident_t<ELEC_NONE, CL>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+        case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+        case ELEC_RF: return launch_resident_t<ELEC_RF, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+        case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+        default: return launch_resident_t<ELEC_NONE, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
     }
 }
 

@@ -25,6 +25,9 @@ cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const
                         int ncon_max, int threads, cudaStream_t stream);
 cudaError_t launch_path_average_2d(const StateDev& st, int max_frames, int K, const int* sel,
                                    int n_sel, double2* out, cudaStream_t stream);
+cudaError_t launch_path_average_contacts(const StateDev& st, const int2* con_ij, int nc, int n,
+                                         const long long* frame_off, int n_sel, int K,
+                                         double inv_r0sq, double* out, cudaStream_t stream);
 cudaError_t launch_toy(const StateDev& st, const RunParams& P, const uint32_t* rep_ids,
                        cudaStream_t stream);
 cudaError_t launch_philox(long long n, const uint32_t* ctr, uint32_t k0, uint32_t k1,
@@ -115,6 +118,7 @@ struct scps_system {
     std::vector<cudaStream_t> fork_streams;
     std::vector<cudaEvent_t> fork_events;
     int bias_kind = SCPS_BIAS_NONE;
+    double inv_r0sq = 0.0;  // 1 / r0^2 of the contact bias (FP64)
     scps_info info{};
     size_t bytes = 0;
     bool is_box = false;
@@ -492,6 +496,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     if (d->model == SCPS_MODEL_CHAIN) {
         ALLOC(st.x, off);
         ALLOC(st.v, off);
+        ALLOC(st.sm, R);
+        ALLOC(st.wm, R);
         ALLOC(s->d_topos, s->topos.size());
         ALLOC(s->d_reps, R);
         ALLOC(s->plain_f, (size_t)6 * s->max_atoms + 16384 + 64);
@@ -645,9 +651,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
         if (!is_2d(s->model)) return fail(SCPS_ERR_INVALID_ARG, "toy bias on a chain system");
         P.bias = b->kind == SCPS_BIAS_RMD_TOY ? 2 : 3;
         P.toy_x_ref = b->toy_x_ref;
-    } else if (b->kind == SCPS_BIAS_TUBE) {
-        if (!is_2d(s->model))
-            return fail(SCPS_ERR_UNSUPPORTED, "the tube bias is built for the two-dimensional models");
+    } else if (b->kind == SCPS_BIAS_TUBE && is_2d(s->model)) {
         if (b->n_ref < 1 || b->n_ref > 1000000 || !b->ref || !b->ref_time)
             return fail(SCPS_ERR_INVALID_ARG, "tube bias needs 1 <= n_ref <= 1e6, ref and ref_time");
         if (!(b->lambda > 0.0) || !(b->t_path > 0.0) || !(b->k_s >= 0.0) || !(b->k_w >= 0.0))
@@ -671,11 +675,21 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
         P.tube_ks = b->k_s;
         P.tube_kw = b->k_w;
         P.tube_t = b->t_path;
-    } else if (b->kind == SCPS_BIAS_RMD_CONTACTS) {
+    } else if (b->kind == SCPS_BIAS_RMD_CONTACTS || b->kind == SCPS_BIAS_TUBE) {
         if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_INVALID_ARG, "contact bias needs the chain model");
         if (!(b->r0 > 0.0)) return fail(SCPS_ERR_INVALID_ARG, "r0 must be > 0");
         if (!b->n_pairs || !b->pairs || !b->x_native)
             return fail(SCPS_ERR_INVALID_ARG, "contact bias needs n_pairs, pairs and x_native");
+        const bool tube = b->kind == SCPS_BIAS_TUBE;
+        if (tube) {
+            if (s->is_box || s->d.exec != SCPS_EXEC_RESIDENT)
+                return fail(SCPS_ERR_UNSUPPORTED, "the contact-map tube bias runs in the resident form of chains");
+            if (b->n_ref < 1 || b->n_ref > kMaxTubeK || !b->ref_maps || !b->ref_time)
+                return fail(SCPS_ERR_INVALID_ARG, "tube bias needs 1 <= n_ref <= %d, ref_maps and ref_time",
+                            kMaxTubeK);
+            if (!(b->lambda > 0.0) || !(b->t_path > 0.0) || !(b->k_s >= 0.0) || !(b->k_w >= 0.0))
+                return fail(SCPS_ERR_INVALID_ARG, "tube bias needs lambda > 0, t_path > 0, k_s, k_w >= 0");
+        }
         const double inv_r0sq = 1.0 / (b->r0 * b->r0);
         int ncon_max = 0;
         for (size_t t = 0; t < s->topos.size(); ++t) {
@@ -717,6 +731,33 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
             SCPS_CU(s->upload(&d_nbr, nbr));
             SCPS_CU(launch_native_map(nc, d_pairs, d_xn, inv_r0sq, d_c0, 0));
             SCPS_CU(cudaDeviceSynchronize());
+            if (tube) {  // reference maps, stored [contact][slice]; N0 = sum C0^2 (Eq. sX)
+                if (nc > 0 && !b->ref_maps[t])
+                    return fail(SCPS_ERR_INVALID_ARG, "topology %zu: NULL reference maps", t);
+                const int K = b->n_ref;
+                std::vector<float> A((size_t)std::max(nc, 1) * K, 0.f);
+                double n0 = 0.0;
+                for (int c = 0; c < nc; ++c) {
+                    double d2 = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        const double dd = xn[3 * pairs[c].y + k] - xn[3 * pairs[c].x + k];
+                        d2 += dd * dd;
+                    }
+                    const double u = d2 * inv_r0sq, num = 1.0 + u + u * u;
+                    const double c0 = num / (num + u * u * u + u * u * u * u);
+                    n0 += c0 * c0;
+                    for (int k = 0; k < K; ++k) {
+                        const double a = b->ref_maps[t][(size_t)k * nc + c];
+                        if (!std::isfinite(a))
+                            return fail(SCPS_ERR_NONFINITE, "topology %zu: non-finite reference map", t);
+                        A[(size_t)c * K + k] = (float)a;
+                    }
+                }
+                float* d_A;
+                SCPS_CU(s->upload(&d_A, A));
+                s->topos[t].dev.tube_A = d_A;
+                s->topos[t].dev.tube_inv_n0 = n0 > 0.0 ? (float)(1.0 / n0) : 0.f;
+            }
             s->topos[t].dev.n_contacts = nc;
             s->topos[t].dev.con_ij = d_pairs;
             s->topos[t].dev.con_C0 = d_c0;
@@ -746,9 +787,24 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
         int rc = sync_topos(s);
         if (rc) return rc;
         P.bias = 1;
+        s->inv_r0sq = inv_r0sq;
         P.inv_r0sq = (float)inv_r0sq;
         const float hi = (float)inv_r0sq;
         P.inv_r0sq_ff = ff{hi, (float)(inv_r0sq - (double)hi)};
+        if (tube) {
+            std::vector<double> tm(b->ref_time, b->ref_time + b->n_ref);
+            for (double v : tm)
+                if (!std::isfinite(v)) return fail(SCPS_ERR_NONFINITE, "non-finite reference time");
+            double* d_tm = nullptr;
+            SCPS_CU(s->upload(&d_tm, tm));
+            P.bias = 5;
+            P.tube_k = b->n_ref;
+            P.tube_time = d_tm;
+            P.tube_lambda = b->lambda;
+            P.tube_ks = b->k_s;
+            P.tube_kw = b->k_w;
+            P.tube_t = b->t_path;
+        }
     } else {
         return fail(SCPS_ERR_INVALID_ARG, "unknown bias kind %d", b->kind);
     }
@@ -760,7 +816,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
     std::vector<double> zero(R, 0.0);
     SCPS_CU(cudaMemcpy(s->st.zm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
     SCPS_CU(cudaMemcpy(s->st.T, zero.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
-    if (is_2d(s->model)) {  // s_m and w_m of the tube bias follow the same initial rule as z_m
+    if (s->st.sm) {  // s_m and w_m of the tube bias follow the same initial rule as z_m
         SCPS_CU(cudaMemcpy(s->st.sm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
         SCPS_CU(cudaMemcpy(s->st.wm, zm.data(), sizeof(double) * R, cudaMemcpyHostToDevice));
     }
@@ -842,7 +898,8 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
     if (n_frames < 0 || n_frames > 2147483647ll) return fail(SCPS_ERR_INVALID_ARG, "bad n_frames");
     if (n_frames == 0) return SCPS_OK;
     if (!X || !U) return fail(SCPS_ERR_INVALID_ARG, "X and U are required");
-    if (z && s->base.bias != 1) return fail(SCPS_ERR_STATE, "z needs a contact bias (scps_set_bias)");
+    if (z && s->base.bias != 1 && s->base.bias != 5)
+        return fail(SCPS_ERR_STATE, "z needs the contact list of a contact or tube bias (scps_set_bias)");
     if (s->is_box) {  // frame by frame in the evaluation slot of the box
         RunParams P = s->base;
         if (!z) P.bias = 0;
@@ -1096,7 +1153,8 @@ int scps_get_info(const scps_system* s, scps_info* info) {
 int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, int32_t n_frames,
                       double* out) {
     if (!s || !replicas || !out) return fail(SCPS_ERR_INVALID_ARG, "NULL argument");
-    if (!is_2d(s->model)) return fail(SCPS_ERR_UNSUPPORTED, "path averages are built for the two-dimensional models");
+    if (!is_2d(s->model) && (s->model != SCPS_MODEL_CHAIN || s->is_box))
+        return fail(SCPS_ERR_UNSUPPORTED, "path averages cover the two-dimensional models and chains");
     const int R = s->d.n_replicas, mf = s->d.max_frames;
     if (n_sel < 1 || n_frames < 1 || n_frames > mf)
         return fail(SCPS_ERR_INVALID_ARG, "need n_sel >= 1 and 1 <= n_frames <= max_frames");
@@ -1108,6 +1166,30 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
         if (ns[r] < n_frames || ns[r] > mf)
             return fail(SCPS_ERR_STATE, "replica %d holds %lld frames (needs %d, at most %d kept)", r,
                         ns[r], n_frames, mf);
+    }
+    if (s->model == SCPS_MODEL_CHAIN) {  // average contact maps
+        const int t = s->rep_topo[sel[0]];
+        for (int r : sel)
+            if (s->rep_topo[r] != t) return fail(SCPS_ERR_INVALID_ARG, "selected replicas differ in topology");
+        const int nc = s->topos[t].ncon, n = s->topos[t].n;
+        if (nc < 1 || !s->topos[t].dev.con_ij)
+            return fail(SCPS_ERR_STATE, "contact maps need the contact list of a contact or tube bias");
+        std::vector<long long> fo(n_sel);
+        for (int q = 0; q < n_sel; ++q) fo[q] = s->frame_off[sel[q]];
+        long long* d_fo = nullptr;
+        double* d_out = nullptr;
+        const size_t nout = (size_t)n_frames * nc;
+        cudaError_t e = cudaMalloc(&d_fo, sizeof(long long) * n_sel);
+        if (e == cudaSuccess) e = cudaMalloc(&d_out, sizeof(double) * nout);
+        if (e == cudaSuccess) e = cudaMemcpy(d_fo, fo.data(), sizeof(long long) * n_sel, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_path_average_contacts(s->st, s->topos[t].dev.con_ij, nc, n, d_fo, n_sel, n_frames,
+                                             (double)s->inv_r0sq, d_out, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost);
+        cudaFree(d_fo);
+        cudaFree(d_out);
+        if (e != cudaSuccess) return fail(SCPS_ERR_CUDA, "path average failed: %s", cudaGetErrorString(e));
+        return SCPS_OK;
     }
     int* d_sel = nullptr;
     double2* d_out = nullptr;
