@@ -393,6 +393,7 @@ def main():
     import torch
 
     import paper_1705_02180_gb300 as pkg
+    from paper_1705_02180_gb300.replicas import max_over_ranks, replica_ids
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -412,7 +413,7 @@ def main():
     n = c.n_atoms
     x0 = np.stack([c.x_unfolded] * R).reshape(-1, 3)
     v0 = c.velocities(R, KT_300, SEED).reshape(-1, 3)
-    ids = np.arange(R) + rank * R
+    ids = replica_ids(rank, world, R)
     spc = args.md_steps_per_call
     sysm = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0, v0=v0,
                       replica_id=ids, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002,
@@ -447,10 +448,7 @@ def main():
         raise RuntimeError(f"timed run failed: status {rc}")
     durs = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3  # s per call
     t_dev = float(durs.sum())
-    if dist:
-        t = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
+    t_dev = max_over_ranks(t_dev, dist, device="cuda")
     atom_steps = R * n * spc * args.steps * world
     value = atom_steps / t_dev
     paths = sysm.collect_paths(0, min(R, 4))
