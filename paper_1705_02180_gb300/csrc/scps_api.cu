@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/scps.h"
 #include "scps_internal.h"
 
@@ -147,6 +149,12 @@ struct scps_system {
 namespace {
 
 bool is_2d(int model) { return model == SCPS_MODEL_TOY2D || model == SCPS_MODEL_FUNNEL2D; }
+
+// NVTX range around every entry point (a no-op unless a profiler is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
 
 int validate_topology(const scps_topology_desc& t, int idx, int max_atoms) {
     if (t.n_atoms <= 0 || t.n_atoms > max_atoms)
@@ -383,6 +391,7 @@ extern "C" {
 const char* scps_last_error(void) { return g_err.c_str(); }
 
 int scps_create_system(const scps_system_desc* d, scps_system** out) {
+    TraceRange trace_("scps_create_system");
     if (!d || !out) return fail(SCPS_ERR_INVALID_ARG, "NULL descriptor or output pointer");
     *out = nullptr;
     if (d->model != SCPS_MODEL_CHAIN && !is_2d(d->model))
@@ -632,6 +641,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
 }
 
 int scps_destroy_system(scps_system* s) {
+    TraceRange trace_("scps_destroy_system");
     if (!s) return SCPS_OK;
     drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
@@ -643,6 +653,7 @@ int scps_destroy_system(scps_system* s) {
 }
 
 int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
+    TraceRange trace_("scps_set_bias");
     if (!s || !b) return fail(SCPS_ERR_INVALID_ARG, "NULL system or bias");
     RunParams& P = s->base;
     if (b->kind == SCPS_BIAS_NONE) {
@@ -825,6 +836,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
 }
 
 int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
+    TraceRange trace_("scps_step_replicas");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     if (n_steps < 0) return fail(SCPS_ERR_INVALID_ARG, "n_steps must be >= 0");
     if (n_steps == 0) return SCPS_OK;
@@ -892,6 +904,7 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
 
 int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const float* X, double* U,
                        float* F, double* z, void* stream) {
+    TraceRange trace_("scps_energy_forces");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
     if (topo < 0 || topo >= (int)s->topos.size()) return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
@@ -922,6 +935,7 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
 
 int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, const float* V,
              float* HV, void* stream) {
+    TraceRange trace_("scps_hvp");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
     if (topo < 0 || topo >= (int)s->topos.size()) return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
@@ -936,6 +950,7 @@ int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, con
 
 int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames, double* z,
                        double* zmin, double* epot, double* bias_T, int64_t* n_frames_out) {
+    TraceRange trace_("scps_collect_paths");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     const int R = s->d.n_replicas;
     if (rep0 < 0 || nrep < 0 || rep0 + nrep > R) return fail(SCPS_ERR_INVALID_ARG, "replica range");
@@ -983,6 +998,7 @@ int scps_collect_paths(scps_system* s, int32_t rep0, int32_t nrep, float* frames
 }
 
 int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* step, double* bias_T) {
+    TraceRange trace_("scps_get_state");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     SCPS_CU(cudaDeviceSynchronize());
     const int R = s->d.n_replicas;
@@ -1041,6 +1057,7 @@ int scps_get_state(scps_system* s, double* x, double* v, double* zm, int64_t* st
 
 int scps_set_state(scps_system* s, const double* x, const double* v, const double* zm,
                    const int64_t* step, const double* bias_T) {
+    TraceRange trace_("scps_set_state");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     SCPS_CU(cudaDeviceSynchronize());
     const int R = s->d.n_replicas;
@@ -1117,6 +1134,7 @@ int scps_set_state(scps_system* s, const double* x, const double* v, const doubl
 }
 
 int scps_get_status(scps_system* s, int32_t* per_replica) {
+    TraceRange trace_("scps_get_status");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(SCPS_ERR_CUDA, "device error: %s", cudaGetErrorString(e));
@@ -1152,6 +1170,7 @@ int scps_get_info(const scps_system* s, scps_info* info) {
 
 int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, int32_t n_frames,
                       double* out) {
+    TraceRange trace_("scps_path_average");
     if (!s || !replicas || !out) return fail(SCPS_ERR_INVALID_ARG, "NULL argument");
     if (!is_2d(s->model) && (s->model != SCPS_MODEL_CHAIN || s->is_box))
         return fail(SCPS_ERR_UNSUPPORTED, "path averages cover the two-dimensional models and chains");
@@ -1205,6 +1224,7 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
 }
 
 int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out) {
+    TraceRange trace_("scps_autotune");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     if (s->model != SCPS_MODEL_CHAIN || s->is_box || s->d.exec != SCPS_EXEC_RESIDENT)
         return fail(SCPS_ERR_UNSUPPORTED, "the tuner covers the resident form of chain replicas");
