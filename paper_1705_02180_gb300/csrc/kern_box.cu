@@ -245,8 +245,8 @@ __global__ void k_box_subsort(BoxDev B, const TopoDev* __restrict__ topo, int r0
     }
 }
 
-// Rebuild step 2: tile boxes and j-cluster boxes (one warp per tile), and which
-// tiles and clusters hold only atoms with the LJ parameters of the last atom (a
+// Rebuild step 2: boxes of the 16-slot i groups (tile halves) and of the 8-slot
+// j clusters (one warp per tile), and which groups and clusters hold only atoms with the LJ parameters of the last atom (a
 // solvent site), whose pair constants the pair kernel then computes once.
 __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) {
     const int r = blockIdx.y + r0;
@@ -263,7 +263,7 @@ __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) 
     float lx = valid ? p.x : 3.0e38f, ly = valid ? p.y : 3.0e38f, lz = valid ? p.z : 3.0e38f;
     float hx = valid ? p.x : -3.0e38f, hy = valid ? p.y : -3.0e38f, hz = valid ? p.z : -3.0e38f;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < 16; o <<= 1) {
         lx = fminf(lx, __shfl_xor_sync(kFullB, lx, o));
         ly = fminf(ly, __shfl_xor_sync(kFullB, ly, o));
         lz = fminf(lz, __shfl_xor_sync(kFullB, lz, o));
@@ -277,16 +277,21 @@ __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) 
             B.chi[c] = make_float4(hx, hy, hz, 0.f);
         }
     }
+    // lanes 0 and 16 now hold the boxes of the two 16-slot halves (the i groups)
     const int a = B.id[(size_t)r * B.np + s];
-    const bool chain = __any_sync(kFullB, a >= 0 && a < B.n_chain);
-    if (lane == 0) {
-        B.tlo[(size_t)r * B.nt + t] = make_float4(lx, ly, lz, 0.f);
-        B.thi[(size_t)r * B.nt + t] = make_float4(hx, hy, hz, 0.f);
-        B.tflag[(size_t)r * B.nt + t] = (chain ? 1 : 0) | (pure == kFullB ? 4 : 0);
+    const unsigned chain = __ballot_sync(kFullB, a >= 0 && a < B.n_chain);
+    if ((lane & 15) == 0) {
+        const int h = lane >> 4;
+        const size_t g = (size_t)r * 2 * B.nt + 2 * t + h;
+        const unsigned half = 0xffffu << (16 * h);
+        B.tlo[g] = make_float4(lx, ly, lz, 0.f);
+        B.thi[g] = make_float4(hx, hy, hz, 0.f);
+        B.tflag[g] = ((chain & half) ? 1 : 0) | ((pure & half) == half ? 4 : 0);
     }
 }
 
-// Rebuild step 3: j clusters near every i tile (one warp per i tile), in cluster order.
+// Rebuild step 3: j clusters near every i group (one warp per group), in cluster order;
+// the group's own tile comes first, then later tiles only (each pair once).
 // Each entry carries the periodic shift s (per axis -1, 0 or 1, in units of L) that
 // takes the cluster's box centre nearest to the tile's. When |d_c + s L| plus both
 // half widths plus the skin (the most two atoms can close in before the next
@@ -296,19 +301,20 @@ __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) 
 __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
-    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (t >= B.nt) return;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // i group (tile half)
+    if (g >= 2 * B.nt) return;
+    const int t = g >> 1;
     const int lane = threadIdx.x & 31;
-    const float4 al = B.tlo[(size_t)r * B.nt + t], ah = B.thi[(size_t)r * B.nt + t];
-    uint32_t* out = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
+    const size_t gi = (size_t)r * 2 * B.nt + g;
+    const float4 al = B.tlo[gi], ah = B.thi[gi];
+    uint32_t* out = B.nbr + gi * B.max_nbr;
     int count = 0;
     bool inexact = false;
     const float room = 0.5f * B.L - 2.0f * sqrtf(B.skin2_quarter);  // L/2 - skin
-    if (al.x <= ah.x) {  // the i tile holds atoms
+    if (al.x <= ah.x) {  // the i group holds atoms
         const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
         const float hx = 0.5f * (ah.x - al.x), hy = 0.5f * (ah.y - al.y), hz = 0.5f * (ah.z - al.z);
         const int ncl = 4 * B.nt;
-        // each pair once: clusters of this tile and of later tiles only
         for (int j0 = 4 * t; j0 < ncl; j0 += 32) {
             const int j = j0 + lane;
             bool hit = false, exact = true;
@@ -346,15 +352,17 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
     if (overflow) count = B.max_nbr;
     const bool any_inexact = __any_sync(kFullB, inexact);
     if (lane == 0) {
-        B.nnbr[(size_t)r * B.nt + t] = count;
-        B.tflag[(size_t)r * B.nt + t] |= any_inexact ? 2 : 0;
+        B.nnbr[gi] = count;
+        B.tflag[gi] |= any_inexact ? 2 : 0;
         if (overflow) atomicOr(&st.status[r], SCPS_FLAG_LIST_OVERFLOW);
     }
 }
 
-// The pairs of i lane `lane` with one staged group of 32 j slots: at iteration
-// u the lane takes staged slot (l + u) & 31, and the j-force accumulators
-// rotate one lane per iteration, so after 32 lane l holds staged slot l's.
+// The pairs of i lane `lane` with one staged group of 32 j slots: half-warp h
+// (lanes 16h .. 16h + 15, the group's 16 i atoms once more) takes staged slots
+// 16h .. 16h + 15; at iteration u lane l takes staged slot 16h + ((l + u) & 15) and
+// the j-force accumulators rotate one lane per iteration within the half-warp, so
+// after 16 lane l holds staged slot l's.
 // SELF: the group holds the tile's own clusters; a pair counts when its j slot
 // comes after its i slot. FAST: every i and j atom has the reference LJ
 // parameters, whose pair constants U are computed once.
@@ -364,10 +372,11 @@ __device__ __forceinline__ void group_pairs(const BoxDev& B, const RunParams& P,
                                             int si, int lane, const float4* sj, const float2* sp,
                                             const int* sid, const int* sslot, float4& fi,
                                             float& gx, float& gy, float& gz) {
-    const int src = (lane + 1) & 31;
+    const int h16 = lane & 16;
+    const int src = h16 | ((lane + 1) & 15);
 #pragma unroll 4
-    for (int u = 0; u < 32; ++u) {
-        const int k = (lane + u) & 31;
+    for (int u = 0; u < 16; ++u) {
+        const int k = h16 | ((lane + u) & 15);
         const float4 xj = sj[k];
         float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         if (MINIMG) {
@@ -418,17 +427,17 @@ __device__ __forceinline__ void group_pairs(const BoxDev& B, const RunParams& P,
 // from everything (MINIMG tests their ids instead).
 template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG>
 __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev* __restrict__ topo,
-                                                  const RunParams& P, int r, int t, int lane,
+                                                  const RunParams& P, int r, int g, int lane,
                                                   bool tile_pure, float4 (&sj)[32], float2 (&sp)[32],
                                                   int (&sid)[32], int (&sslot)[32]) {
     const size_t base = (size_t)r * B.np;
-    const int si = t * 32 + lane;
+    const int si = g * 16 + (lane & 15);  // both half-warps hold the group's 16 i slots
     const float4 xi = B.pos[base + si];
     const float2 li = B.par[base + si];
     const int idi = B.id[base + si];
     const unsigned long long em = (EXCL && idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
-    const uint32_t* lst = B.nbr + ((size_t)r * B.nt + t) * B.max_nbr;
-    const int cnt = B.nnbr[(size_t)r * B.nt + t];
+    const uint32_t* lst = B.nbr + ((size_t)r * 2 * B.nt + g) * B.max_nbr;
+    const int cnt = B.nnbr[(size_t)r * 2 * B.nt + g];
     long long* jacc = B.facc + 3 * base;
     const float2 ref = topo->lj[B.n_atoms - 1];
     const LJPair U = lj_pair(ref.x + ref.x, ref.y * ref.y, P.pc);
@@ -481,6 +490,11 @@ __device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev
         }
         __syncwarp();
     }
+    // the two half-warps' shares of each i atom
+    fi.x += __shfl_xor_sync(kFullB, fi.x, 16);
+    fi.y += __shfl_xor_sync(kFullB, fi.y, 16);
+    fi.z += __shfl_xor_sync(kFullB, fi.z, 16);
+    fi.w += __shfl_xor_sync(kFullB, fi.w, 16);
     return fi;
 }
 
@@ -494,17 +508,17 @@ __global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __re
     __shared__ int sslot[4][32];
     const int r = blockIdx.y + r0;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * 4 + w;
-    if (t >= B.nt) return;
-    const int fl = B.tflag[(size_t)r * B.nt + t];
+    const int g = blockIdx.x * 4 + w;  // i group: 16 slots, half of a tile
+    if (g >= 2 * B.nt) return;
+    const int fl = B.tflag[(size_t)r * 2 * B.nt + g];
     const bool pure = (fl & 4) != 0;
     float4 f;
     switch (fl & 3) {
-        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, t, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
-        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, t, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
-        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, t, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
+        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, g, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
+        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, g, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
+        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, g, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
     }
-    B.fnb[(size_t)r * B.np + t * 32 + lane] = f;
+    if (lane < 16) B.fnb[(size_t)r * B.np + g * 16 + lane] = f;
 }
 
 // Total non-bonded force on slot s of replica r: its i part plus its fixed-point
@@ -797,16 +811,17 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
     k_box_scan<<<nr, kSortThreads, 0, s>>>(B, r0);
     k_box_scatter<<<dim3((B.n_atoms + 255) / 256, nr), 256, 0, s>>>(B, r0);
     k_box_keyorder<<<dim3((B.ncol * B.ncol * B.nz + 255) / 256, nr), 256, 0, s>>>(B, r0);
-    const dim3 gt((B.nt + 3) / 4, nr);
+    const dim3 gt((B.nt + 3) / 4, nr);       // one warp per tile
+    const dim3 gg((2 * B.nt + 3) / 4, nr);   // one warp per i group (tile half)
     k_box_subsort<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_tiles<<<gt, 128, 0, s>>>(B, topo, r0);
-    k_box_list<<<gt, 128, 0, s>>>(B, st, r0);
+    k_box_list<<<gg, 128, 0, s>>>(B, st, r0);
 #define PAIRS(E)                                                                                \
     switch (elec) {                                                                             \
-        case ELEC_DDIEL: k_box_pairs<ELEC_DDIEL, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;  \
-        case ELEC_RF: k_box_pairs<ELEC_RF, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;        \
-        case ELEC_PLAIN: k_box_pairs<ELEC_PLAIN, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;  \
-        default: k_box_pairs<ELEC_NONE, E><<<gt, 128, 0, s>>>(B, topo, P, r0); break;           \
+        case ELEC_DDIEL: k_box_pairs<ELEC_DDIEL, E><<<gg, 128, 0, s>>>(B, topo, P, r0); break;  \
+        case ELEC_RF: k_box_pairs<ELEC_RF, E><<<gg, 128, 0, s>>>(B, topo, P, r0); break;        \
+        case ELEC_PLAIN: k_box_pairs<ELEC_PLAIN, E><<<gg, 128, 0, s>>>(B, topo, P, r0); break;  \
+        default: k_box_pairs<ELEC_NONE, E><<<gg, 128, 0, s>>>(B, topo, P, r0); break;           \
     }
     if (energy) {
         PAIRS(true)

@@ -144,6 +144,21 @@ struct scps_system {
             e = cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
         return e;
     }
+    // tables of the current bias: replaced (and freed) by the next scps_set_bias
+    std::vector<void*> bias_allocs;
+    template <class T>
+    cudaError_t bias_upload(T** p, const std::vector<T>& h) {
+        const size_t n = h.empty() ? 1 : h.size();
+        cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+        if (e != cudaSuccess) return e;
+        bias_allocs.push_back(*p);
+        if (!h.empty()) e = cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+        return e;
+    }
+    void drop_bias_tables() {
+        for (void* q : bias_allocs) cudaFree(q);
+        bias_allocs.clear();
+    }
 };
 
 namespace {
@@ -591,13 +606,13 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.colinfo, (size_t)Rs * 2 * 257);
         BALLOC(B.pos_ref, np);
         BALLOC(B.slot_of, (size_t)Rs * B.n_atoms);
-        BALLOC(B.tlo, (size_t)Rs * B.nt);
-        BALLOC(B.thi, (size_t)Rs * B.nt);
+        BALLOC(B.tlo, (size_t)Rs * 2 * B.nt);  // per i group (tile half)
+        BALLOC(B.thi, (size_t)Rs * 2 * B.nt);
         BALLOC(B.clo, (size_t)Rs * 4 * B.nt);
         BALLOC(B.chi, (size_t)Rs * 4 * B.nt);
-        BALLOC(B.nbr, (size_t)Rs * B.nt * B.max_nbr);
-        BALLOC(B.nnbr, (size_t)Rs * B.nt);
-        BALLOC(B.tflag, (size_t)Rs * B.nt);
+        BALLOC(B.nbr, (size_t)Rs * 2 * B.nt * B.max_nbr);
+        BALLOC(B.nnbr, (size_t)Rs * 2 * B.nt);
+        BALLOC(B.tflag, (size_t)Rs * 2 * B.nt);
         BALLOC(B.need, Rs);
         BALLOC(B.since, Rs);
         BALLOC(B.maxd2, Rs);
@@ -645,6 +660,7 @@ int scps_destroy_system(scps_system* s) {
     if (!s) return SCPS_OK;
     drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    s->drop_bias_tables();
     for (auto st : s->fork_streams) cudaStreamDestroy(st);
     for (auto ev : s->fork_events) cudaEventDestroy(ev);
     for (void* p : s->allocs) cudaFree(p);
@@ -656,6 +672,26 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
     TraceRange trace_("scps_set_bias");
     if (!s || !b) return fail(SCPS_ERR_INVALID_ARG, "NULL system or bias");
     RunParams& P = s->base;
+    // the previous bias goes first (its tables are freed once no enqueued work can read
+    // them); a call that fails below leaves the system without a bias
+    SCPS_CU(cudaDeviceSynchronize());
+    drop_graphs(s);
+    s->drop_bias_tables();
+    P.bias = 0;
+    P.tube_k = 0;
+    for (auto& t : s->topos) {
+        t.dev.n_contacts = 0;
+        t.dev.con_ij = nullptr;
+        t.dev.con_C0 = nullptr;
+        t.dev.con_off = nullptr;
+        t.dev.con_nbr = nullptr;
+        t.dev.tube_A = nullptr;
+        t.ncon = 0;
+    }
+    if (s->model == SCPS_MODEL_CHAIN) {
+        int rc0 = sync_topos(s);
+        if (rc0) return rc0;
+    }
     if (b->kind == SCPS_BIAS_NONE) {
         P.bias = 0;
     } else if (b->kind == SCPS_BIAS_RMD_TOY || b->kind == SCPS_BIAS_RMD_RADIAL) {
@@ -676,8 +712,8 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
         }
         double2* d_ref = nullptr;
         double* d_tm = nullptr;
-        SCPS_CU(s->upload(&d_ref, ref));
-        SCPS_CU(s->upload(&d_tm, tm));
+        SCPS_CU(s->bias_upload(&d_ref, ref));
+        SCPS_CU(s->bias_upload(&d_tm, tm));
         P.bias = 4;
         P.tube_k = b->n_ref;
         P.tube_ref = d_ref;
@@ -735,13 +771,22 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
             double* d_xn;
             int* d_off;
             int2* d_nbr;
-            SCPS_CU(s->upload(&d_pairs, pairs));
-            SCPS_CU(s->alloc(&d_c0, nc));
-            SCPS_CU(s->upload(&d_xn, xn));
-            SCPS_CU(s->upload(&d_off, off));
-            SCPS_CU(s->upload(&d_nbr, nbr));
-            SCPS_CU(launch_native_map(nc, d_pairs, d_xn, inv_r0sq, d_c0, 0));
-            SCPS_CU(cudaDeviceSynchronize());
+            SCPS_CU(s->bias_upload(&d_pairs, pairs));
+            SCPS_CU(s->bias_upload(&d_c0, std::vector<float2>(std::max(nc, 1))));
+            SCPS_CU(s->bias_upload(&d_off, off));
+            SCPS_CU(s->bias_upload(&d_nbr, nbr));
+            SCPS_CU(cudaMalloc(&d_xn, sizeof(double) * std::max<size_t>(xn.size(), 1)));
+            if (!xn.empty()) {
+                cudaError_t ex = cudaMemcpy(d_xn, xn.data(), sizeof(double) * xn.size(), cudaMemcpyHostToDevice);
+                if (ex != cudaSuccess) {
+                    cudaFree(d_xn);
+                    return fail(SCPS_ERR_CUDA, "upload of x_native failed: %s", cudaGetErrorString(ex));
+                }
+            }
+            cudaError_t em = launch_native_map(nc, d_pairs, d_xn, inv_r0sq, d_c0, 0);
+            if (em == cudaSuccess) em = cudaDeviceSynchronize();
+            cudaFree(d_xn);  // only C0 = C(X_N) is kept
+            SCPS_CU(em);
             if (tube) {  // reference maps, stored [contact][slice]; N0 = sum C0^2 (Eq. sX)
                 if (nc > 0 && !b->ref_maps[t])
                     return fail(SCPS_ERR_INVALID_ARG, "topology %zu: NULL reference maps", t);
@@ -765,7 +810,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
                     }
                 }
                 float* d_A;
-                SCPS_CU(s->upload(&d_A, A));
+                SCPS_CU(s->bias_upload(&d_A, A));
                 s->topos[t].dev.tube_A = d_A;
                 s->topos[t].dev.tube_inv_n0 = n0 > 0.0 ? (float)(1.0 / n0) : 0.f;
             }
@@ -807,7 +852,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
             for (double v : tm)
                 if (!std::isfinite(v)) return fail(SCPS_ERR_NONFINITE, "non-finite reference time");
             double* d_tm = nullptr;
-            SCPS_CU(s->upload(&d_tm, tm));
+            SCPS_CU(s->bias_upload(&d_tm, tm));
             P.bias = 5;
             P.tube_k = b->n_ref;
             P.tube_time = d_tm;

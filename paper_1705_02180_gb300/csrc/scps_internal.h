@@ -115,14 +115,14 @@ struct BoxDev {
     int* hist;        // [replica][8192] key counts, then running cursors (rebuild)
     int* colinfo;     // [replica][2][257] first compact position and first tile per column
     float4* pos_ref;  // positions at the last rebuild
-    float4* tlo;      // [replica][nt] tile boxes
+    float4* tlo;      // [replica][2 nt] boxes of the 16-slot i groups (tile halves)
     float4* thi;
     float4* clo;      // [replica][4 nt] boxes of the 8-slot j clusters (clo.w: 1 = reference LJ only)
     float4* chi;
-    uint32_t* nbr;    // [replica][nt][max_nbr]: j cluster | periodic shift << 24 (2 bits per
+    uint32_t* nbr;    // [replica][2 nt][max_nbr] per i group: j cluster | periodic shift << 24 (2 bits per
                       // axis) | 1 << 30 when the cluster holds only reference-LJ atoms
-    int* nnbr;        // [replica][nt]
-    int* tflag;       // [replica][nt]: 1 = tile holds chain atoms, 2 = a listed cluster needs
+    int* nnbr;        // [replica][2 nt]
+    int* tflag;       // [replica][2 nt] per i group: 1 = group holds chain atoms, 2 = a listed cluster needs
                       // the minimum image per pair (its shift is not the same for all pairs),
                       // 4 = all its atoms have the reference LJ parameters (the last atom's)
     int* need;        // [replica] rebuild flag

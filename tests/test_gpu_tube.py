@@ -133,3 +133,36 @@ def test_one_chain_scps_round(pkg):
     assert tube["maps"].shape == (20, len(c.contacts))
     assert np.all((tube["maps"] >= 0) & (tube["maps"] <= 1))
     assert np.all(tube["T"] >= 0)
+
+
+def test_repeated_set_bias_replaces_its_tables(pkg, path19):
+    torch = pytest.importorskip("torch")
+    c, A, t = path19
+    R = 2
+    x0 = f32(np.stack([c.x_unfolded] * R))
+    v0 = f32(c.velocities(R, KT, 25))
+
+    def make():
+        return pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R,
+                          x0=x0.reshape(-1, 3), v0=v0.reshape(-1, 3), dt=DT, gamma=1.0, kT=KT,
+                          seed=13)
+
+    s = make()
+    s.set_contact_bias([c.contacts], [c.x_native], k_R=0.01)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in range(30):  # alternate the two contact biases; the old tables are freed each time
+        s.set_contact_tube_bias([c.contacts], [c.x_native], [A], t, 13.5, 1.0, 1.0, t[-1])
+        s.set_contact_bias([c.contacts], [c.x_native], k_R=0.01)
+    torch.cuda.synchronize()
+    assert free0 - torch.cuda.mem_get_info()[0] < 4 << 20
+    s.step(40)
+    a = s.get_state()
+    s.close()
+    fresh = make()
+    fresh.set_contact_bias([c.contacts], [c.x_native], k_R=0.01)
+    fresh.step(40)
+    b = fresh.get_state()
+    fresh.close()
+    for k in ("x", "v", "zm", "T"):
+        assert np.array_equal(a[k], b[k]), k
