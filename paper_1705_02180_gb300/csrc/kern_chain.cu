@@ -394,15 +394,30 @@ __device__ __forceinline__ void tube_pass1(const Shared& sm, Scalars& sc, const 
 #pragma unroll
     for (int blk = 0; blk < kMaxTubeK / 32; ++blk) acc[blk] = 0.f;
     const int nq = min(32, tp.n_contacts - c0);
-    for (int q = 0; q < nq; ++q) {
-        const float Cq = __shfl_sync(kFull, C, q);
-        const float* row = tp.tube_A + (size_t)(c0 + q) * K;
+    // four contacts at a time: all their map entries are loaded before any is used, so
+    // the loads from L2 overlap instead of following one another
+    for (int q0 = 0; q0 < nq; q0 += 4) {
+        float a[4][kMaxTubeK / 32];
 #pragma unroll
-        for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
-            const int kk = blk * 32 + lane;
-            if (kk < K) {
-                const float d = Cq - row[kk];
-                acc[blk] = fmaf(d, d, acc[blk]);
+        for (int qq = 0; qq < 4; ++qq) {
+            const float* row = tp.tube_A + (size_t)(c0 + q0 + qq) * K;
+#pragma unroll
+            for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+                const int kk = blk * 32 + lane;
+                a[qq][blk] = (q0 + qq < nq && kk < K) ? __ldg(row + kk) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const float Cq = __shfl_sync(kFull, C, (q0 + qq) & 31);
+            if (q0 + qq < nq) {
+#pragma unroll
+                for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+                    if (blk * 32 + lane < K) {
+                        const float d = Cq - a[qq][blk];
+                        acc[blk] = fmaf(d, d, acc[blk]);
+                    }
+                }
             }
         }
     }
@@ -429,8 +444,18 @@ __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, 
     const float C = contact_C_f32(u);
     const int K = P.tube_k;
     const float* row = tp.tube_A + (size_t)c * K;
-    float dot = 0.f;
-    for (int k = 0; k < K; ++k) dot = fmaf(sc.gam[k], row[k], dot);
+    // four independent partial sums (the loads of several slices are in flight at once)
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    int k = 0;
+#pragma unroll 2
+    for (; k + 4 <= K; k += 4) {
+        d0 = fmaf(sc.gam[k], __ldg(row + k), d0);
+        d1 = fmaf(sc.gam[k + 1], __ldg(row + k + 1), d1);
+        d2 = fmaf(sc.gam[k + 2], __ldg(row + k + 2), d2);
+        d3 = fmaf(sc.gam[k + 3], __ldg(row + k + 3), d3);
+    }
+    for (; k < K; ++k) d0 = fmaf(sc.gam[k], __ldg(row + k), d0);
+    const float dot = (d0 + d1) + (d2 + d3);
     const float h = 2.0f * tp.tube_inv_n0 * (C * sc.gam_sum - dot) * contact_dC_du(u);
     const long long gx = f2fix(h * dx), gy = f2fix(h * dy), gz = f2fix(h * dz);
     const int nta = sm.nta;
