@@ -837,6 +837,22 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
     return cudaGetLastError();
 }
 
+// Dynamic shared memory k_box_chain may request on the current device: the opt-in per-block
+// limit less its static shared block; 0 when the device cannot be queried.
+size_t box_chain_smem_limit() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    size_t stat = 0;
+    for (const void* k : {(const void*)k_box_chain<true>, (const void*)k_box_chain<false>}) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
+        stat = a.sharedSizeBytes > stat ? a.sharedSizeBytes : stat;
+    }
+    return (size_t)optin > stat ? (size_t)optin - stat : 0;
+}
+
 cudaError_t box_prepare(const BoxDev& B, int n_contacts_max) {
     const size_t smem = box_chain_smem(B.n_chain, n_contacts_max);
     cudaError_t e = cudaFuncSetAttribute(k_box_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

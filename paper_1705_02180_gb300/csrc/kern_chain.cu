@@ -19,6 +19,9 @@
 // which warp or CTA took which work item.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "scps_internal.h"
 
 namespace cg = cooperative_groups;
@@ -29,6 +32,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per lane)
+constexpr int kTubeItem = 8;  // contacts per work item of the contact-map tube passes
 
 struct Shared {
     float4* xq;         // (x, y, z, qs)
@@ -57,10 +61,10 @@ struct Scalars {
     long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity
     long long red_e[2][32];  // per-warp shares of the potential energy (units of 2^-20)
     // contact-map tube bias
-    int work_next2[2];                  // counter of the second work phase, by parity
     double sm, wm;                      // running minima of s_lambda and w_lambda
     float gam_sum;                      // sum_k gamma_k
     float gam[kMaxTubeK];               // gamma_k = dF/dD_k weights of the evaluated step
+    int work_next2[2];                  // counter of the second work phase, by parity
     long long red_d[2][kMaxTubeK];      // this CTA's share of sum_p (C_p - A_kp)^2 (2^-40), by parity
 };
 
@@ -375,96 +379,102 @@ __device__ __forceinline__ float contact_C_f32(float u) {
     return num / (num + u2 * u + u2 * u2);
 }
 
-// Contact-map tube bias, first pass over one chunk of 32 native contacts: this
-// CTA's share of sum_p (C_p(X) - <C_p(t'_k)>)^2 for every reference slice k.
-// Lane l computes C of contact c0 + l; then lane l takes slices l, l + 32, ...
-// and runs over the chunk's contacts (C broadcast by shuffle).
-__device__ __forceinline__ void tube_pass1(const Shared& sm, Scalars& sc, const TopoDev& tp,
-                                           const RunParams& P, int b, int c0, int lane) {
-    const int c = c0 + lane;
+// Contact-map tube bias, first pass over one item of kTubeItem native contacts
+// (c0 .. c0 + 7): the item's share of sum_p (C_p(X) - <C_p(t'_k)>)^2 for every
+// reference slice k, added in fixed point (2^-40) to the lane's running sums dacc
+// (exact integer sums: independent of which warp takes which item). Lanes 0..7 compute C of the item's contacts; then lane l takes
+// slices l, l + 32, ... The item's rows of the reference maps are contiguous
+// (contact-major, K per row), so each load instruction reads consecutive slices,
+// and the eight rows of one slice block are loaded before any is used.
+__device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, const RunParams& P,
+                                           int c0, int lane, long long* dacc) {
+    const int nq = min(kTubeItem, tp.n_contacts - c0);
     float C = 0.f;
-    if (c < tp.n_contacts) {
-        const int2 ij = tp.con_ij[c];
+    if (lane < nq) {
+        const int2 ij = tp.con_ij[c0 + lane];
         const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
         const float dx = q.x - a.x, dy = q.y - a.y, dz = q.z - a.z;
         C = contact_C_f32(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq);
     }
     const int K = P.tube_k;
-    float acc[kMaxTubeK / 32];
-#pragma unroll
-    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) acc[blk] = 0.f;
-    const int nq = min(32, tp.n_contacts - c0);
-    // four contacts at a time: all their map entries are loaded before any is used, so
-    // the loads from L2 overlap instead of following one another
-    for (int q0 = 0; q0 < nq; q0 += 4) {
-        float a[4][kMaxTubeK / 32];
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-            const float* row = tp.tube_A + (size_t)(c0 + q0 + qq) * K;
-#pragma unroll
-            for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
-                const int kk = blk * 32 + lane;
-                a[qq][blk] = (q0 + qq < nq && kk < K) ? __ldg(row + kk) : 0.f;
-            }
-        }
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-            const float Cq = __shfl_sync(kFull, C, (q0 + qq) & 31);
-            if (q0 + qq < nq) {
-#pragma unroll
-                for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
-                    if (blk * 32 + lane < K) {
-                        const float d = Cq - a[qq][blk];
-                        acc[blk] = fmaf(d, d, acc[blk]);
-                    }
-                }
-            }
-        }
-    }
+    const float* rows = tp.tube_A + (size_t)c0 * K;
 #pragma unroll
     for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
-        const int kk = blk * 32 + lane;
-        if (kk < K)
-            atomicAdd((unsigned long long*)&sc.red_d[b][kk],
-                      (unsigned long long)__float2ll_rn(acc[blk] * 1099511627776.0f));  // 2^40
+        if (blk * 32 >= K) break;
+        const int k = blk * 32 + lane;
+        float a[kTubeItem];
+#pragma unroll
+        for (int q = 0; q < kTubeItem; ++q) a[q] = (q < nq && k < K) ? __ldg(rows + q * K + k) : 0.f;
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < kTubeItem; ++q) {
+            const float d = __shfl_sync(kFull, C, q) - a[q];
+            acc = q < nq ? fmaf(d, d, acc) : acc;
+        }
+        dacc[blk] += __float2ll_rn(acc * 1099511627776.0f);  // 2^40
     }
 }
 
-// Contact-map tube bias, second pass for contact c = (i, p): with gamma_k the
-// weights of the ratchet forces on the slices (dF/dD_k), the force on the atoms
-// of the contact is beta grad C with beta = (2/N0) sum_k gamma_k (C - <C(t'_k)>);
-// h = beta C'(u) goes to G like the z gradient (F = -2/r0^2 G).
+// Contact-map tube bias, second pass over one item of kTubeItem contacts: with
+// gamma_k the weights of the ratchet forces on the slices (dF/dD_k), the force on
+// the atoms of contact p is beta_p grad C_p with beta_p = (2/N0) sum_k gamma_k
+// (C_p - <C_p(t'_k)>); h = beta_p C'(u) goes to G like the z gradient (F = -2/r0^2 G).
+// The dots sum_k gamma_k <C_p(t'_k)> are formed with lane l on slices l, l + 32, ...
+// (coalesced rows) and reduced over the warp for the eight contacts at once: three
+// exchange steps halve the values each lane holds, two more finish the sums, so lane
+// L ends with the dot of contact (L >> 2) & 7. The order of every sum is fixed.
 __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, const TopoDev& tp,
-                                           const RunParams& P, long long* G, int c) {
-    if (c >= tp.n_contacts) return;
-    const int2 ij = tp.con_ij[c];
+                                           const RunParams& P, long long* G, int c0, int lane) {
+    const int nq = min(kTubeItem, tp.n_contacts - c0);
+    // the contact of lane l (l < nq; clamped elsewhere) is read first, so that its
+    // latency overlaps the slice loads
+    const int2 ij = tp.con_ij[c0 + min(lane, nq - 1)];
+    const int K = P.tube_k;
+    const float* rows = tp.tube_A + (size_t)c0 * K;
+    float v[kTubeItem];
+#pragma unroll
+    for (int q = 0; q < kTubeItem; ++q) v[q] = 0.f;
+#pragma unroll
+    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+        if (blk * 32 >= K) break;
+        const int k = blk * 32 + lane;
+        const float g = k < K ? sc.gam[k] : 0.f;
+#pragma unroll
+        for (int q = 0; q < kTubeItem; ++q) {
+            const float a = (q < nq && k < K) ? __ldg(rows + q * K + k) : 0.f;
+            v[q] = fmaf(g, a, v[q]);
+        }
+    }
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w4[4], w2[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        w4[q] = (b4 ? v[q + 4] : v[q]) + __shfl_xor_sync(kFull, b4 ? v[q] : v[q + 4], 16);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        w2[q] = (b3 ? w4[q + 2] : w4[q]) + __shfl_xor_sync(kFull, b3 ? w4[q] : w4[q + 2], 8);
+    float w1 = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(kFull, b2 ? w2[0] : w2[1], 4);
+    w1 += __shfl_xor_sync(kFull, w1, 2);
+    w1 += __shfl_xor_sync(kFull, w1, 1);
+    const float dot = __shfl_sync(kFull, w1, (lane & 7) * 4);
+    // every lane stays to the end (all exchanges below are full-warp); lanes >= nq
+    // hold a copy of the last contact and add nothing
+    const bool live = lane < nq;
     const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
     const float dx = q.x - a.x, dy = q.y - a.y, dz = q.z - a.z;
     const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq;
     const float C = contact_C_f32(u);
-    const int K = P.tube_k;
-    const float* row = tp.tube_A + (size_t)c * K;
-    // four independent partial sums (the loads of several slices are in flight at once)
-    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-    int k = 0;
-#pragma unroll 2
-    for (; k + 4 <= K; k += 4) {
-        d0 = fmaf(sc.gam[k], __ldg(row + k), d0);
-        d1 = fmaf(sc.gam[k + 1], __ldg(row + k + 1), d1);
-        d2 = fmaf(sc.gam[k + 2], __ldg(row + k + 2), d2);
-        d3 = fmaf(sc.gam[k + 3], __ldg(row + k + 3), d3);
-    }
-    for (; k < K; ++k) d0 = fmaf(sc.gam[k], __ldg(row + k), d0);
-    const float dot = (d0 + d1) + (d2 + d3);
-    const float h = 2.0f * tp.tube_inv_n0 * (C * sc.gam_sum - dot) * contact_dC_du(u);
+    const float h = live ? 2.0f * tp.tube_inv_n0 * (C * sc.gam_sum - dot) * contact_dC_du(u) : 0.f;
     const long long gx = f2fix(h * dx), gy = f2fix(h * dy), gz = f2fix(h * dz);
     const int nta = sm.nta;
-    atomicAdd((unsigned long long*)&G[ij.x], (unsigned long long)gx);
-    atomicAdd((unsigned long long*)&G[nta + ij.x], (unsigned long long)gy);
-    atomicAdd((unsigned long long*)&G[2 * nta + ij.x], (unsigned long long)gz);
-    atomicAdd((unsigned long long*)&G[ij.y], (unsigned long long)(-gx));
-    atomicAdd((unsigned long long*)&G[nta + ij.y], (unsigned long long)(-gy));
-    atomicAdd((unsigned long long*)&G[2 * nta + ij.y], (unsigned long long)(-gz));
+    if (live) {
+        atomicAdd((unsigned long long*)&G[ij.x], (unsigned long long)gx);
+        atomicAdd((unsigned long long*)&G[nta + ij.x], (unsigned long long)gy);
+        atomicAdd((unsigned long long*)&G[2 * nta + ij.x], (unsigned long long)gz);
+        atomicAdd((unsigned long long*)&G[ij.y], (unsigned long long)(-gx));
+        atomicAdd((unsigned long long*)&G[nta + ij.y], (unsigned long long)(-gy));
+        atomicAdd((unsigned long long*)&G[2 * nta + ij.y], (unsigned long long)(-gz));
+    }
 }
 
 // Tube variables and their ratchets from the summed slice distances (warp 0):
@@ -472,32 +482,40 @@ __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, 
 // w = -(1/lambda) log sum_k exp(-lambda D_k), s = 1 - (1/t) sum_k t'_k pi_k
 // (Eq. sX, Eq. wX with the average maps); F^s, F^w of Eq. (Fs), Eq. (Fw) through
 // gamma_k = c_s ds/dD_k + c_w dw/dD_k, ds/dD_k = (lambda/t) pi_k (t'_k - <t'>),
-// dw/dD_k = pi_k. Sums over k are in a fixed order (lane order, then a fixed tree).
+// dw/dD_k = pi_k. The D_k are exact fixed-point sums; their differences to the
+// smallest are taken in integers and the weights in FP32 (the FP64 pipe of this GPU
+// is 64 times slower); s and w are compared with their running minima in FP64.
+// Sums over k are in a fixed order (lane order, then a fixed tree).
 template <int CL>
 __device__ void tube_decide(Scalars& sc, const TopoDev& tp, const RunParams& P, int b, int lane) {
     const int K = P.tube_k;
-    double D[kMaxTubeK / 32];
-    double dmin = 1e300;
+    constexpr int NB = kMaxTubeK / 32;
+    float tk[NB];  // slice times, loaded first (their latency overlaps the exchange)
+    long long dk[NB];
+    long long dmin = LLONG_MAX;
 #pragma unroll
-    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+    for (int blk = 0; blk < NB; ++blk) {
         const int k = blk * 32 + lane;
-        D[blk] = 1e300;
+        tk[blk] = k < K ? (float)P.tube_time[k] : 0.f;
+        dk[blk] = LLONG_MAX;
         if (k < K) {
             long long t = 0;
             for (int q = 0; q < CL; ++q) t += rank_ptr<CL>(&sc.red_d[b][0], q)[k];
-            D[blk] = (double)t * 9.094947017729282e-13 * (double)tp.tube_inv_n0;  // 2^-40
-            dmin = fmin(dmin, D[blk]);
+            dk[blk] = t;
+            dmin = min(dmin, t);
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(kFull, dmin, o));
-    double e[kMaxTubeK / 32], Z = 0.0, Zt = 0.0;
+    for (int o = 16; o > 0; o >>= 1) dmin = min(dmin, __shfl_xor_sync(kFull, dmin, o));
+    const float scale = 9.094947017729282e-13f * tp.tube_inv_n0;  // 2^-40 / N0
+    const float lam = (float)P.tube_lambda;
+    float e[NB], Z = 0.f, Zt = 0.f;
 #pragma unroll
-    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+    for (int blk = 0; blk < NB; ++blk) {
         const int k = blk * 32 + lane;
-        e[blk] = k < K ? exp(-P.tube_lambda * (D[blk] - dmin)) : 0.0;
+        e[blk] = k < K ? expf(-lam * ((float)(dk[blk] - dmin) * scale)) : 0.f;
         Z += e[blk];
-        Zt += k < K ? e[blk] * P.tube_time[k] : 0.0;
+        Zt += e[blk] * tk[blk];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -506,22 +524,26 @@ __device__ void tube_decide(Scalars& sc, const TopoDev& tp, const RunParams& P, 
     }
     Z = __shfl_sync(kFull, Z, 0);
     Zt = __shfl_sync(kFull, Zt, 0);
-    const double tbar = Zt / Z;
-    const double sv = 1.0 - tbar / P.tube_t;
-    const double wv = dmin - log(Z) / P.tube_lambda;
+    const float inv_Z = 1.0f / Z;
+    const float tbar = Zt * inv_Z;
+    const float inv_t = (float)(1.0 / P.tube_t);
+    const double sv = 1.0 - (double)(tbar * inv_t);
+    const double wv = (double)dmin * 9.094947017729282e-13 * (double)tp.tube_inv_n0 -
+                      (double)(logf(Z) / lam);
     double cs = 0.0, cw = 0.0;  // ratchets, theta(0) = 1
     const double sm0 = sc.sm, wm0 = sc.wm;
     if (!(sv < sm0)) cs = -P.tube_ks * (sv - sm0);
     if (!(wv < wm0)) cw = -P.tube_kw * (wv - wm0);
+    const float cs_l = (float)cs * lam * inv_t, cw_f = (float)cw;
     float gsum = 0.f;
 #pragma unroll
-    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+    for (int blk = 0; blk < NB; ++blk) {
         const int k = blk * 32 + lane;
         if (k < K) {
-            const double pi = e[blk] / Z;
-            const double g = cs * P.tube_lambda / P.tube_t * pi * (P.tube_time[k] - tbar) + cw * pi;
-            sc.gam[k] = (float)g;
-            gsum += (float)g;
+            const float pi = e[blk] * inv_Z;
+            const float g = fmaf(cs_l * pi, tk[blk] - tbar, cw_f * pi);
+            sc.gam[k] = g;
+            gsum += g;
         }
     }
 #pragma unroll
@@ -596,23 +618,48 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     // skips it. Item k belongs to CTA k mod CL of the cluster, whose warps pull their
     // items from a counter in their own shared memory; the two halves of a tile pair
     // are listed in alternating order, so both CTAs get half of the diagonal items.
+    // Under the contact-map tube bias the contact items are first-pass items of
+    // kTubeItem contacts (loads from the reference maps in L2), interleaved two by two
+    // with the half tiles so that their memory latency overlaps arithmetic; the
+    // interleave keeps every half tile on the CTA it has without the bias.
     const int n_half = 2 * ntp;
     const bool tube = TUBE && do_ratchet;  // contact-map tube bias: two work phases
     const int ncon = (P.bias == 1 || P.bias == 5) ? tp.n_contacts : 0;  // frames: z too
-    const int e_con = n_half + (ncon + kChunk - 1) / kChunk;
+    const int n_citems = tube ? (ncon + kTubeItem - 1) / kTubeItem : (ncon + kChunk - 1) / kChunk;
+    const int m_mix = tube ? (min(n_half, n_citems) & ~1) : 0;
+    const int e_con = n_half + n_citems;
     const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
     const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
     int* counter = &sc.work_next[b];
     const int rank = cta_rank<CL>();
     long long e = 0, zacc = 0;  // fixed point: sums independent of the work order
+    long long dacc[TUBE ? kMaxTubeK / 32 : 1];  // first-pass slice sums of this lane
+#pragma unroll
+    for (int q = 0; q < (TUBE ? kMaxTubeK / 32 : 1); ++q) dacc[q] = 0;
     for (;;) {
         int m = 0;
         if (lane == 0) m = atomicAdd(counter, 1);
         const int k = __shfl_sync(kFull, m, 0) * CL + rank;
         if (k >= e_all) break;
-        if (k < n_half) {
-            const uint32_t w = sm.tpl[k >> 1];
-            const int I = (int)(w >> 16), J = (int)(w & 0xffff), h = (k ^ (k >> 1)) & 1;
+        int kp = k, kc = -1;  // half-tile index, or contact-item index when kc >= 0
+        if (k < e_con) {
+            if (k < 2 * m_mix) {
+                const int base = (k >> 2) * 2, r4 = k & 3;
+                if (r4 < 2)
+                    kc = base + r4;
+                else
+                    kp = base + r4 - 2;
+            } else {
+                const int j = k - 2 * m_mix;
+                if (j < n_half - m_mix)
+                    kp = m_mix + j;
+                else
+                    kc = m_mix + j - (n_half - m_mix);
+            }
+        }
+        if (k < e_con && kc < 0) {
+            const uint32_t w = sm.tpl[kp >> 1];
+            const int I = (int)(w >> 16), J = (int)(w & 0xffff), h = (kp ^ (kp >> 1)) & 1;
             float ep = 0.f;
             if (I == J) {
                 if (h == 0) ep = diag_tile<ELEC, ENERGY>(sm, F, tp, P.pc, I, lane);
@@ -625,11 +672,12 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             }
             if (ENERGY) e += f2fix(ep);
         } else if (k < e_con) {
-            const int c0 = (k - n_half) * kChunk;
-            if (tube)
-                tube_pass1(sm, sc, tp, P, b, c0, lane);
-            else if (c0 + lane < ncon)
-                zacc += contact_term(sm, G, tp, P, c0 + lane);
+            if (tube) {
+                if constexpr (TUBE) tube_pass1(sm, tp, P, kc * kTubeItem, lane, dacc);
+            } else {
+                const int c0 = kc * kChunk;
+                if (c0 + lane < ncon) zacc += contact_term(sm, G, tp, P, c0 + lane);
+            }
         } else if (k < e_bond) {
             const int q = (k - e_con) * kChunk + lane;
             if (q < tp.n_bonds) {
@@ -641,6 +689,16 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             if (q < tp.n_angles) {
                 const float ea = angle_term<ENERGY>(sm, F, tp, q);
                 if (ENERGY) e += f2fix(ea);
+            }
+        }
+    }
+    if constexpr (TUBE) {
+        if (tube) {  // one add per slice and warp into this CTA's share
+#pragma unroll
+            for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
+                const int kk = blk * 32 + lane;
+                if (kk < P.tube_k && dacc[blk] != 0)
+                    atomicAdd((unsigned long long*)&sc.red_d[b][kk], (unsigned long long)dacc[blk]);
             }
         }
     }
@@ -695,13 +753,13 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     __syncthreads();
     if (tube) {  // second work phase: the bias force per contact, then G is complete
         int* counter2 = &sc.work_next2[b];
-        const int n2 = (ncon + kChunk - 1) / kChunk;
+        const int n2 = (ncon + kTubeItem - 1) / kTubeItem;
         for (;;) {
             int m = 0;
             if (lane == 0) m = atomicAdd(counter2, 1);
             const int k = __shfl_sync(kFull, m, 0) * CL + rank;
             if (k >= n2) break;
-            tube_pass2(sm, sc, tp, P, G, k * kChunk + lane);
+            tube_pass2(sm, sc, tp, P, G, k * kTubeItem, lane);
         }
         cluster_barrier<CL>();  // the peer reads this CTA's G next
         if (tid == 0) sc.work_next2[b] = 0;
@@ -970,6 +1028,26 @@ size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max) {
     (void)ncon_max;  // contacts live in the topology (global memory)
     return sizeof(float4) * nta * 3 + sizeof(float4) * 6 * nt + sizeof(long long) * 12 * nta +
            sizeof(float2) * nta + sizeof(uint32_t) * ntp4;
+}
+
+// Dynamic shared memory a resident or frame-evaluation CTA may request on the current
+// device: the opt-in per-block limit less the largest static shared block of those kernels.
+// 0 when the device cannot be queried (nothing then fits).
+size_t resident_smem_limit() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    size_t stat = 0;
+    const void* kernels[] = {(const void*)k_resident<ELEC_DDIEL, 1, false>,
+                             (const void*)k_resident<ELEC_DDIEL, 2, true>,
+                             (const void*)k_eval_frames<ELEC_DDIEL>};
+    for (const void* k : kernels) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
+        stat = std::max(stat, a.sharedSizeBytes);
+    }
+    return (size_t)optin > stat ? (size_t)optin - stat : 0;
 }
 
 template <int ELEC, int CL, bool TUBE>

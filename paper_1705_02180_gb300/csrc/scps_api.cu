@@ -19,6 +19,9 @@
 
 namespace scps {
 size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max);
+size_t resident_smem_limit();
+size_t box_chain_smem_limit();
+size_t box_chain_smem(int n_chain, int n_contacts);
 cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const RepDev* reps,
                             const StateDev& st, const RunParams& P, int nta, int ntp_max,
                             int ncon_max, int threads, cudaStream_t stream);
@@ -556,6 +559,11 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         s->threads = d->threads ? d->threads : (one_cta_per_sm ? 1024 : auto_threads(s->nta));
         s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
         if (!s->is_box && d->exec == SCPS_EXEC_RESIDENT) {
+            const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, 0);
+            if (smem > resident_smem_limit())
+                return bail(fail(SCPS_ERR_UNSUPPORTED,
+                                 "%d atoms need %zu B of shared memory per CTA, above the limit; "
+                                 "use the plain execution form", s->max_atoms, smem));
             rc = set_groups(s, 0, s->cluster, s->threads);
             if (rc) return bail(rc);
         }
@@ -619,6 +627,9 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.fch, (size_t)Rs * B.n_chain);
         BALLOC(B.eb, Rs);
 #undef BALLOC
+        if (box_chain_smem(B.n_chain, 0) > box_chain_smem_limit())
+            return bail(fail(SCPS_ERR_UNSUPPORTED, "chain of %d atoms is too large for one CTA",
+                             B.n_chain));
         if (box_prepare(B, 0) != cudaSuccess) return bail(fail(SCPS_ERR_CUDA, "box set-up failed"));
     }
     rc = scps_set_state(s, d->x0, d->v0, nullptr, nullptr, nullptr);
@@ -828,13 +839,13 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
                     return fail(SCPS_ERR_INVALID_ARG, "contact %d is not between chain atoms", c);
             const size_t smem = sizeof(float4) * s->box.n_chain + sizeof(long long) * 3 * s->box.n_chain +
                                 sizeof(float) * ncon_max;
-            if (smem > 227 * 1024)
+            if (smem > box_chain_smem_limit())
                 return fail(SCPS_ERR_UNSUPPORTED, "chain of %d atoms and %d contacts is too large",
                             s->box.n_chain, ncon_max);
             SCPS_CU(box_prepare(s->box, ncon_max));
         } else {
             const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, ncon_max);
-            if (smem > 227 * 1024)
+            if (s->d.exec == SCPS_EXEC_RESIDENT && smem > resident_smem_limit())
                 return fail(SCPS_ERR_UNSUPPORTED, "shared memory %zu B exceeds the per-CTA limit", smem);
         }
         if (s->d.exec == SCPS_EXEC_PLAIN && ncon_max > 16384)
@@ -1359,6 +1370,7 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
                 std::vector<int> c{plan, cl, th};
                 if (c != cands[0]) cands.push_back(c);
             }
+    const size_t smem_limit = resident_smem_limit();
     double best = 1e300;
     std::vector<int> best_c = cands[0];
     int timed = 0;
@@ -1367,7 +1379,7 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
         if (set_groups(s, c[0], c[1], c[2]) != SCPS_OK) continue;
         bool fits = true;
         for (auto& g : s->groups)
-            fits = fits && resident_smem_bytes(g.nta, g.ntp_max, s->ncon_max) <= 227 * 1024;
+            fits = fits && resident_smem_bytes(g.nta, g.ntp_max, s->ncon_max) <= smem_limit;
         if (!fits) continue;
         // one short untimed run (first-launch set-up), then the timed probe; state restored after each
         cudaError_t le = launch_groups(s, P, std::max(1, probe_steps / 4), s->cap_stream);

@@ -414,3 +414,53 @@ def test_cluster_pair_matches_single_cta_and_oracle(pkg):
     for k in ("x", "v", "zm", "T"):
         assert np.array_equal(out[1][1][k], out[2][1][k]), k
     assert np.array_equal(out[1][2][0]["z"], out[2][2][0]["z"])
+
+
+# ------------------------------------------------------------------ size limits
+def test_largest_resident_chain_one_step_and_cta_shapes(pkg):
+    # 90 residues = 1440 atoms = 45 tiles: the largest chain whose resident state fits the
+    # shared memory of one CTA (152 B per atom slot plus boxes and the tile-pair table)
+    c = chain(90)
+    assert c.n_atoms == 1440
+    R = 2
+    x0 = f32(np.stack([c.x_unfolded] * R))
+    v0 = f32(c.velocities(R, KT, 15))
+    out = []
+    for kw in (dict(cluster_size=2), dict(cluster_size=1), dict(cluster_size=1, threads=256)):
+        s = make_system(pkg, [c], [0] * R, x0, v0, **kw)
+        s.set_contact_bias([c.contacts], [c.x_native], k_R=0.01, zm_init=pkg.ZM_VALUE,
+                           zm_value=0.0)
+        s.step(1)
+        one = s.get_state()
+        s.step(9)
+        out.append((one, s.get_state()))
+        s.close()
+    ff = oracle.ForceField.from_chain(c)
+    bz = oracle.BiasZ(c.contacts, c.x_native, k_R=0.01)
+    ref = oracle.run_baoab(ff, bz, x0, v0, [0.0] * R, [0] * R, np.arange(R), 11, DT, 1.0, KT, 1)
+    assert np.abs(out[0][0]["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-6
+    assert np.allclose(out[0][0]["T"], ref["T"], rtol=1e-4)
+    for o in out[1:]:
+        for k in ("x", "v", "zm", "T"):
+            assert np.array_equal(out[0][1][k], o[1][k]), k
+
+
+def test_chain_above_the_shared_memory_limit(pkg):
+    # 92 residues = 1472 atoms = 46 tiles no longer fit one CTA: the resident form refuses
+    # at creation with UNSUPPORTED, the plain form (state in global memory) runs it
+    c = chain(92)
+    R = 1
+    x0 = f32(np.stack([c.x_unfolded] * R))
+    v0 = f32(c.velocities(R, KT, 16))
+    with pytest.raises(pkg.ScpsError) as e:
+        make_system(pkg, [c], [0] * R, x0, v0)
+    assert e.value.code == -7
+    s = make_system(pkg, [c], [0] * R, x0, v0, exec_form=pkg.EXEC_PLAIN)
+    s.set_contact_bias([c.contacts], [c.x_native], k_R=0.01, zm_init=pkg.ZM_VALUE, zm_value=0.0)
+    s.step(1)
+    got = s.get_state()
+    s.close()
+    ff = oracle.ForceField.from_chain(c)
+    bz = oracle.BiasZ(c.contacts, c.x_native, k_R=0.01)
+    ref = oracle.run_baoab(ff, bz, x0, v0, [0.0] * R, [0] * R, np.arange(R), 11, DT, 1.0, KT, 1)
+    assert np.abs(got["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-6
