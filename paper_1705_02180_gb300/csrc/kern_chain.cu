@@ -46,7 +46,7 @@ struct Shared {
                         // without its ratchet factor, which is known only once z is complete)
     float4* blo;        // tile bounding boxes, then half-tile boxes (2 per tile)
     float4* bhi;
-    uint32_t* tpl;      // all tile pairs (I << 16 | J), I <= J
+    uint32_t* tpl;      // tile pairs at least two apart (I << 16 | J), J >= I + 2
     int* flag;          // force-range flag of the current evaluation
     int nta, nt;
 };
@@ -167,6 +167,54 @@ __device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const
     fjz += __shfl_xor_sync(kFull, fjz, 16);
     add_fix(sm, F, i, fix, fiy, fiz);
     if (lane < 16) add_fix(sm, F, jb + lane, fjx, fjy, fjz);
+    return eacc;
+}
+
+// Two quarter items side by side, one per half-warp. A quarter item is 16 i atoms
+// (half a of tile I) against 16 j atoms (half h of tile J), J >= I + 2, so no pair is
+// excluded. Lane l of half-warp g takes i = 32 I_g + 16 a_g + l and, at iteration t,
+// j slot (l + t) & 15 of its j half; the j-force accumulators rotate within the
+// half-warp, so lane l ends with slot l. Items are coded (I << 18 | J << 2 | a << 1 | h);
+// a negative code leaves its half-warp idle (it adds nothing).
+template <int ELEC, bool ENERGY>
+__device__ __forceinline__ float quarter_items(const Shared& sm, long long* F, const PairConst& pc,
+                                               int code_a, int code_b, int lane) {
+    const int code = lane < 16 ? code_a : code_b;
+    const bool valid = code >= 0;
+    const int c = valid ? code : 0;
+    const int g16 = lane & 16, l16 = lane & 15;
+    const int i = (c >> 18) * kTile + 16 * ((c >> 1) & 1) + l16;
+    const int jb = ((c >> 2) & 0xffff) * kTile + 16 * (c & 1);
+    const float4 xi = sm.xq[i];
+    const float2 li = sm.lj[i];
+    const int src = g16 | ((l16 + 1) & 15);
+    float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
+#pragma unroll 4
+    for (int t = 0; t < 16; ++t) {
+        const int j = jb + ((l16 + t) & 15);
+        const float4 xj = sm.xq[j];
+        const float2 lj = sm.lj[j];
+        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool ok = valid && r2 < pc.rc2;
+        float e = 0.f;
+        float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
+        s = ok ? s : 0.0f;
+        fix = fmaf(s, dx, fix);
+        fiy = fmaf(s, dy, fiy);
+        fiz = fmaf(s, dz, fiz);
+        fjx = fmaf(-s, dx, fjx);
+        fjy = fmaf(-s, dy, fjy);
+        fjz = fmaf(-s, dz, fjz);
+        if (ENERGY) eacc += ok ? e : 0.0f;
+        fjx = __shfl_sync(kFull, fjx, src);
+        fjy = __shfl_sync(kFull, fjy, src);
+        fjz = __shfl_sync(kFull, fjz, src);
+    }
+    if (valid) {
+        add_fix(sm, F, i, fix, fiy, fiz);
+        add_fix(sm, F, jb + l16, fjx, fjy, fjz);
+    }
     return eacc;
 }
 
@@ -606,28 +654,36 @@ template <int ELEC, bool ENERGY, int CL, bool TUBE>
 __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
                          bool do_ratchet, uint32_t rep_id, long long noise_step) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int nt = tp.n_tiles, ntp = nt * (nt + 1) / 2;
+    const int nt = tp.n_tiles;
     long long* F = sm.Fp[b];
     long long* G = sm.Gp[b];
     sm.flag = &sc.flag[b];
     if (noise_step >= 0)
         for (int q = warp; q < nt; q += nw) noise_chunk(sm, tp, P, rep_id, noise_step, q, lane);
-    // work list: half-tile candidates (two per tile pair, in tile-pair order; the tile
-    // with itself is one item), then contact, bond and angle chunks. The warp that
-    // pulls a half tile whose box is farther than the cutoff from the i tile's box
-    // skips it. Item k belongs to CTA k mod CL of the cluster, whose warps pull their
-    // items from a counter in their own shared memory; the two halves of a tile pair
-    // are listed in alternating order, so both CTAs get half of the diagonal items.
+    // Work list: the pair items, then contact, bond and angle chunks. Pair items are
+    // the tile pairs at least two tiles apart (far pairs), then each tile with itself,
+    // then the two halves (16 j atoms) of each tile's neighbour. A warp that pulls a
+    // far pair tests its four quarter items (16 x 16 atoms) by their half boxes and
+    // runs the live ones two at a time, one per half-warp; an odd one waits for the
+    // warp's next live quarter, or runs alone once the warp has pulled past the last
+    // far pair. A neighbour half whose box is beyond the cutoff from the i tile's box
+    // is skipped. Item k belongs to CTA k mod CL of the cluster, whose warps pull their
+    // items from a counter in their own shared memory.
     // Under the contact-map tube bias the contact items are first-pass items of
     // kTubeItem contacts (loads from the reference maps in L2), interleaved two by two
-    // with the half tiles so that their memory latency overlaps arithmetic; the
-    // interleave keeps every half tile on the CTA it has without the bias.
-    const int n_half = 2 * ntp;
+    // with the pair items so that their memory latency overlaps arithmetic; the
+    // interleave keeps every pair item on the CTA it has without the bias.
+    const int nfar = nt >= 3 ? (nt - 1) * (nt - 2) / 2 : 0;
+    const int n_pair = nfar + nt + 2 * (nt - 1);
     const bool tube = TUBE && do_ratchet;  // contact-map tube bias: two work phases
     const int ncon = (P.bias == 1 || P.bias == 5) ? tp.n_contacts : 0;  // frames: z too
     const int n_citems = tube ? (ncon + kTubeItem - 1) / kTubeItem : (ncon + kChunk - 1) / kChunk;
-    const int m_mix = tube ? (min(n_half, n_citems) & ~1) : 0;
-    const int e_con = n_half + n_citems;
+    const int m_mix = tube ? (min(n_pair, n_citems) & ~1) : 0;
+    const int e_con = n_pair + n_citems;
+    // one past the list position of the last far pair
+    const int k_far_end = nfar == 0 ? 0
+                          : 1 + (nfar - 1 < m_mix ? 4 * ((nfar - 1) >> 1) + 2 + ((nfar - 1) & 1)
+                                                  : m_mix + (nfar - 1));
     const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
     const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
     int* counter = &sc.work_next[b];
@@ -636,12 +692,18 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     long long dacc[TUBE ? kMaxTubeK / 32 : 1];  // first-pass slice sums of this lane
 #pragma unroll
     for (int q = 0; q < (TUBE ? kMaxTubeK / 32 : 1); ++q) dacc[q] = 0;
+    int pending = -1;  // code of a live quarter item waiting for a partner (warp-uniform)
     for (;;) {
         int m = 0;
         if (lane == 0) m = atomicAdd(counter, 1);
         const int k = __shfl_sync(kFull, m, 0) * CL + rank;
+        if (pending >= 0 && k >= k_far_end) {  // no far pair is left for this warp
+            const float ep = quarter_items<ELEC, ENERGY>(sm, F, P.pc, pending, -1, lane);
+            if (ENERGY) e += f2fix(ep);
+            pending = -1;
+        }
         if (k >= e_all) break;
-        int kp = k, kc = -1;  // half-tile index, or contact-item index when kc >= 0
+        int kp = k, kc = -1;  // pair-item index, or contact-item index when kc >= 0
         if (k < e_con) {
             if (k < 2 * m_mix) {
                 const int base = (k >> 2) * 2, r4 = k & 3;
@@ -651,24 +713,40 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
                     kp = base + r4 - 2;
             } else {
                 const int j = k - 2 * m_mix;
-                if (j < n_half - m_mix)
+                if (j < n_pair - m_mix)
                     kp = m_mix + j;
                 else
-                    kc = m_mix + j - (n_half - m_mix);
+                    kc = m_mix + j - (n_pair - m_mix);
             }
         }
         if (k < e_con && kc < 0) {
-            const uint32_t w = sm.tpl[kp >> 1];
-            const int I = (int)(w >> 16), J = (int)(w & 0xffff), h = (kp ^ (kp >> 1)) & 1;
             float ep = 0.f;
-            if (I == J) {
-                if (h == 0) ep = diag_tile<ELEC, ENERGY>(sm, F, tp, P.pc, I, lane);
-            } else if (box_gap2(sm.blo[I], sm.bhi[I], sm.blo[sm.nt + 2 * J + h],
-                                sm.bhi[sm.nt + 2 * J + h]) < P.pc.rc2) {
-                if (J == I + 1)
-                    ep = half_tile<ELEC, ENERGY, true>(sm, F, tp, P.pc, I, J, h, lane);
-                else
-                    ep = half_tile<ELEC, ENERGY, false>(sm, F, tp, P.pc, I, J, h, lane);
+            if (kp < nfar) {
+                const uint32_t w = sm.tpl[kp];
+                const int I = (int)(w >> 16), J = (int)(w & 0xffff);
+                bool live = false;  // lane q < 4 tests quarter (a, h) = (q >> 1, q & 1)
+                if (lane < 4) {
+                    const int ia = sm.nt + 2 * I + (lane >> 1), jh = sm.nt + 2 * J + (lane & 1);
+                    live = box_gap2(sm.blo[ia], sm.bhi[ia], sm.blo[jh], sm.bhi[jh]) < P.pc.rc2;
+                }
+                unsigned lm = __ballot_sync(kFull, live);
+                while (lm) {
+                    const int code = (I << 18) | (J << 2) | (__ffs(lm) - 1);
+                    lm &= lm - 1;
+                    if (pending < 0) {
+                        pending = code;
+                    } else {
+                        ep += quarter_items<ELEC, ENERGY>(sm, F, P.pc, pending, code, lane);
+                        pending = -1;
+                    }
+                }
+            } else if (kp < nfar + nt) {
+                ep = diag_tile<ELEC, ENERGY>(sm, F, tp, P.pc, kp - nfar, lane);
+            } else {
+                const int r = kp - nfar - nt, I = r >> 1, h = r & 1;
+                const int jh = sm.nt + 2 * (I + 1) + h;  // half boxes follow sm.nt tile boxes
+                if (box_gap2(sm.blo[I], sm.bhi[I], sm.blo[jh], sm.bhi[jh]) < P.pc.rc2)
+                    ep = half_tile<ELEC, ENERGY, true>(sm, F, tp, P.pc, I, I + 1, h, lane);
             }
             if (ENERGY) e += f2fix(ep);
         } else if (k < e_con) {
@@ -766,15 +844,19 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     }
 }
 
+// Tile pairs at least two tiles apart (I << 16 | J, J >= I + 2), row by row: the
+// candidates of the quarter items. Tiles with themselves and with their neighbour are
+// listed by index arithmetic.
 __device__ void tile_pair_table(const Shared& sm, int nt) {
-    for (int p = threadIdx.x; p < nt * (nt + 1) / 2; p += blockDim.x) {  // row major, I <= J
-        int I = 0, row = nt, q = p;
+    const int nfar = nt >= 3 ? (nt - 1) * (nt - 2) / 2 : 0;
+    for (int p = threadIdx.x; p < nfar; p += blockDim.x) {
+        int I = 0, row = nt - 2, q = p;
         while (q >= row) {
             q -= row;
             ++I;
             --row;
         }
-        sm.tpl[p] = ((uint32_t)I << 16) | (uint32_t)(I + q);
+        sm.tpl[p] = ((uint32_t)I << 16) | (uint32_t)(I + 2 + q);
     }
 }
 
