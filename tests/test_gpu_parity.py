@@ -102,7 +102,7 @@ def test_toy_matches_oracle(pkg):
 
 
 # ------------------------------------------------------------------ forces, energy, z
-@pytest.mark.parametrize("n_res", [1, 19, 35, 75])
+@pytest.mark.parametrize("n_res", [1, 3, 5, 19, 35, 75])  # 1, 2, 3, 10, 18, 38 tiles
 def test_energy_forces_z_match_oracle(pkg, torch_cuda, n_res):
     torch = torch_cuda
     c = chain(n_res)
@@ -464,3 +464,28 @@ def test_chain_above_the_shared_memory_limit(pkg):
     bz = oracle.BiasZ(c.contacts, c.x_native, k_R=0.01)
     ref = oracle.run_baoab(ff, bz, x0, v0, [0.0] * R, [0] * R, np.arange(R), 11, DT, 1.0, KT, 1)
     assert np.abs(got["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("n_res", [1, 3, 5])
+def test_small_chains_one_step_both_cta_shapes(pkg, n_res):
+    # 1, 2 and 3 tiles: only the tile with itself; the neighbour halves; one far tile pair
+    # (four quarter items, an odd live one runs alone)
+    c = chain(n_res)
+    pairs = c.contacts if len(c.contacts) else np.array([[0, c.n_atoms - 1]])
+    R = 3
+    x0 = f32(np.stack([c.x_unfolded] * R))
+    v0 = f32(c.velocities(R, KT, 17))
+    got = []
+    for cl in (1, 2):
+        s = make_system(pkg, [c], [0] * R, x0, v0, cluster_size=cl)
+        s.set_contact_bias([pairs], [c.x_native], k_R=0.01, zm_init=pkg.ZM_VALUE, zm_value=0.0)
+        s.step(1)
+        got.append(s.get_state())
+        s.close()
+    ff = oracle.ForceField.from_chain(c)
+    bz = oracle.BiasZ(pairs, c.x_native, k_R=0.01)
+    ref = oracle.run_baoab(ff, bz, x0, v0, [0.0] * R, [0] * R, np.arange(R), 11, DT, 1.0, KT, 1)
+    for g in got:
+        assert np.abs(g["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-6
+    for k in ("x", "v", "zm", "T"):
+        assert np.array_equal(got[0][k], got[1][k]), k
