@@ -430,10 +430,11 @@ __device__ __forceinline__ float contact_C_f32(float u) {
 // Contact-map tube bias, first pass over one item of kTubeItem native contacts
 // (c0 .. c0 + 7): the item's share of sum_p (C_p(X) - <C_p(t'_k)>)^2 for every
 // reference slice k, added in fixed point (2^-40) to the lane's running sums dacc
-// (exact integer sums: independent of which warp takes which item). Lanes 0..7 compute C of the item's contacts; then lane l takes
-// slices l, l + 32, ... The item's rows of the reference maps are contiguous
-// (contact-major, K per row), so each load instruction reads consecutive slices,
-// and the eight rows of one slice block are loaded before any is used.
+// (exact integer sums: independent of which warp takes which item). Lanes 0..7
+// compute C of the item's contacts; then lane l takes slices l, l + 32, ... The
+// item's rows of the reference maps are contiguous (contact-major, K per row), so
+// each load instruction reads consecutive slices, and the eight rows of one slice
+// block are loaded before any is used.
 __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, const RunParams& P,
                                            int c0, int lane, long long* dacc) {
     const int nq = min(kTubeItem, tp.n_contacts - c0);
