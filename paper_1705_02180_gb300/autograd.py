@@ -5,12 +5,13 @@ returns g_t * grad U(X_t) through ForceGrad, whose own backward is the
 Hessian-vector product H(X_t) v_t (scps_hvp). So second derivatives of path
 functionals work, e.g. the gradient of sum_t |grad U(X_t)|^2 (a term of the
 Onsager-Machlup action of Eq. (SOM)) is sum_t 2 H(X_t) grad U(X_t).
+ForceNormSquared computes that action per segment of frames with one force launch
+forward and one force + one HVP launch backward (force_norm_action).
 All arithmetic runs in the CUDA kernels behind the C ABI.
 """
 from __future__ import annotations
 
 import torch
-import torch.utils.checkpoint as _ckpt
 
 
 class ForceGrad(torch.autograd.Function):
@@ -57,16 +58,39 @@ def potential_energy(system, X, topo=0):
     return PotentialEnergy.apply(X, system, topo)
 
 
+class ForceNormSquared(torch.autograd.Function):
+    """sum_t |grad U(X_t)|^2 over frames X (float64 scalar). The forces are not kept:
+    the backward evaluates them again and returns g * 2 H(X_t) grad U(X_t) (one
+    force launch and one HVP launch), which is activation checkpointing over the
+    frames without the generic checkpoint machinery. First order only: for further
+    derivatives compose ForceGrad instead."""
+
+    @staticmethod
+    def forward(ctx, X, system, topo):
+        X = X.contiguous()
+        U = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        F = torch.empty_like(X)
+        system.energy_forces(topo, X, U, F)
+        ctx.save_for_backward(X)
+        ctx.system, ctx.topo = system, topo
+        return (F.double() ** 2).sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        (X,) = ctx.saved_tensors
+        U = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        F = torch.empty_like(X)
+        ctx.system.energy_forces(ctx.topo, X, U, F)
+        HV = torch.empty_like(X)
+        ctx.system.hvp(ctx.topo, X, F.mul_(-2.0), HV)  # v = 2 grad U = -2 F
+        return HV * g.to(HV.dtype), None, None
+
+
 def force_norm_action(system, X, topo=0, segment=50):
-    """sum_t |grad U(X_t)|^2 over the frames, recomputed per segment of `segment`
-    frames in the backward pass (activation checkpointing over path frames)."""
-
-    def seg(xs):
-        g = ForceGrad.apply(xs, system, topo)
-        return (g.double() ** 2).sum()
-
+    """sum_t |grad U(X_t)|^2 over the frames, evaluated per segment of `segment`
+    frames; each segment keeps only its positions and recomputes its forces in the
+    backward pass (activation checkpointing over path frames)."""
     total = X.new_zeros((), dtype=torch.float64)
     for s in range(0, X.shape[0], segment):
-        xs = X[s:s + segment]
-        total = total + _ckpt.checkpoint(seg, xs, use_reentrant=False)
+        total = total + ForceNormSquared.apply(X[s:s + segment], system, topo)
     return total

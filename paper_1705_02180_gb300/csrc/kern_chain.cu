@@ -736,8 +736,9 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
                     lm &= lm - 1;
                     if (pending < 0) {
                         pending = code;
-                    } else {
-                        ep += quarter_items<ELEC, ENERGY>(sm, F, P.pc, pending, code, lane);
+                    } else {  // each pass's energy in fixed point: the pairing is order-dependent
+                        const float eq = quarter_items<ELEC, ENERGY>(sm, F, P.pc, pending, code, lane);
+                        if (ENERGY) e += f2fix(eq);
                         pending = -1;
                     }
                 }
@@ -1052,8 +1053,11 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
     cluster_barrier<CL>();  // no CTA leaves while its shared memory may still be read
 }
 
-// Energy, forces and z of n_frames configurations (no bias, no state); one CTA per frame.
-template <int ELEC>
+// Energy, forces and z of n_frames configurations (no bias, no state); one cluster of CL
+// CTAs per frame. With CL = 2 the work list is split between the two CTAs as in the
+// resident kernel and each CTA writes half of the atoms' forces, summing its own and the
+// peer's fixed-point partials (the same integers as with one CTA).
+template <int ELEC, int CL>
 __global__ void __launch_bounds__(1024, 1)
 k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
               double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta,
@@ -1063,7 +1067,8 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
     const TopoDev tp = *topo_ptr;
     Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
     const int n = tp.n_atoms, nt = tp.n_tiles;
-    const long long f = blockIdx.x;
+    const long long f = blockIdx.x / CL;
+    const int rank = cta_rank<CL>();
     const float* xf = X + f * n * 3;
     for (int i = threadIdx.x; i < nta; i += blockDim.x) {
         if (i < n) {
@@ -1088,20 +1093,28 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
     }
     __syncthreads();
     all_boxes(sm, n);
-    __syncthreads();
-    evaluate<ELEC, true, 1, false>(sm, sc, tp, P, 0, false, 0u, -1);
-    if (F) {
+    cluster_barrier<CL>();  // every CTA of the cluster is initialised before any remote access
+    evaluate<ELEC, true, CL, false>(sm, sc, tp, P, 0, false, 0u, -1);
+    if (F) {  // evaluate ends with a cluster barrier: every partial is complete
         float* ff_out = F + f * n * 3;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            ff_out[3 * i] = fix2f(sm.Fp[0][i]);
-            ff_out[3 * i + 1] = fix2f(sm.Fp[0][nta + i]);
-            ff_out[3 * i + 2] = fix2f(sm.Fp[0][2 * nta + i]);
+        const long long* Fo = rank_ptr<CL>(sm.Fp[0], rank ^ 1);
+        for (int i = threadIdx.x + rank * blockDim.x; i < n; i += CL * blockDim.x) {
+            long long fx = sm.Fp[0][i], fy = sm.Fp[0][nta + i], fz = sm.Fp[0][2 * nta + i];
+            if (CL == 2) {
+                fx += Fo[i];
+                fy += Fo[nta + i];
+                fz += Fo[2 * nta + i];
+            }
+            ff_out[3 * i] = fix2f(fx);
+            ff_out[3 * i + 1] = fix2f(fy);
+            ff_out[3 * i + 2] = fix2f(fz);
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && rank == 0) {
         U[f] = sc.epot;
         if (Z) Z[f] = sc.z;
     }
+    cluster_barrier<CL>();  // no CTA leaves while its shared memory may still be read
 }
 
 // Shared-memory bytes of the resident kernel for tiles of nta atoms.
@@ -1124,7 +1137,8 @@ size_t resident_smem_limit() {
     size_t stat = 0;
     const void* kernels[] = {(const void*)k_resident<ELEC_DDIEL, 1, false>,
                              (const void*)k_resident<ELEC_DDIEL, 2, true>,
-                             (const void*)k_eval_frames<ELEC_DDIEL>};
+                             (const void*)k_eval_frames<ELEC_DDIEL, 1>,
+                             (const void*)k_eval_frames<ELEC_DDIEL, 2>};
     for (const void* k : kernels) {
         cudaFuncAttributes a;
         if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
@@ -1189,24 +1203,37 @@ cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const R
 template <int ELEC>
 static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const float* X,
                                  double* U, float* F, double* Z, long long n_frames, int nta,
-                                 int ntp_max, int ncon_max, int threads, cudaStream_t stream) {
+                                 int ntp_max, int ncon_max, int threads, int cl,
+                                 cudaStream_t stream) {
     const size_t smem = resident_smem_bytes(nta, ntp_max, ncon_max);
-    cudaError_t e = cudaFuncSetAttribute(k_eval_frames<ELEC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = cl == 2 ? k_eval_frames<ELEC, 2> : k_eval_frames<ELEC, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_eval_frames<ELEC><<<(unsigned)n_frames, threads, smem, stream>>>(topo, P, X, U, F, Z, nta,
-                                                                       ntp_max, ncon_max);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_frames * cl));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, topo, P, X, U, F, Z, nta, ntp_max, ncon_max);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
                         double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
-                        int ncon_max, int threads, cudaStream_t stream) {
+                        int ncon_max, int threads, int cl, cudaStream_t stream) {
     switch (elec) {
-        case ELEC_DDIEL: return launch_eval_t<ELEC_DDIEL>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, stream);
-        case ELEC_RF: return launch_eval_t<ELEC_RF>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, stream);
-        case ELEC_PLAIN: return launch_eval_t<ELEC_PLAIN>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, stream);
-        default: return launch_eval_t<ELEC_NONE>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, stream);
+        case ELEC_DDIEL: return launch_eval_t<ELEC_DDIEL>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
+        case ELEC_RF: return launch_eval_t<ELEC_RF>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
+        case ELEC_PLAIN: return launch_eval_t<ELEC_PLAIN>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
+        default: return launch_eval_t<ELEC_NONE>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
     }
 }
 

@@ -1,5 +1,6 @@
-// Hessian-vector products H(X_t) V_t of the physical potential, one CTA per
-// frame. Used by the double backward of the energy (the gradient of
+// Hessian-vector products H(X_t) V_t of the physical potential, one cluster of CL
+// CTAs per frame (CL = 2 splits the tile pairs, bonds and angles between the two
+// CTAs; each then writes half of the atoms, summing its and the peer's partials). Used by the double backward of the energy (the gradient of
 // sum_t |grad U(X_t)|^2 is sum_t 2 H(X_t) grad U(X_t); the Onsager-Machlup
 // action of Eq. (SOM) contains (grad U)^2).
 //
@@ -10,7 +11,11 @@
 //   H v = k (grad theta . v) grad theta + k (theta - theta0) D_v(grad theta),
 // D_v being the directional derivative along v, written out by hand below.
 // Sums are int64 fixed point (order-free, so results are bit-reproducible).
+#include <cooperative_groups.h>
+
 #include "scps_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace scps {
 
@@ -186,8 +191,16 @@ __device__ void hvp_angle(const HvpShared& sm, const TopoDev& tp, int q) {
 
 }  // namespace
 
-template <int ELEC>
-__global__ void __launch_bounds__(512)
+template <int CL>
+__device__ __forceinline__ void hvp_cluster_sync() {
+    if (CL == 1)
+        __syncthreads();
+    else
+        cg::this_cluster().sync();
+}
+
+template <int ELEC, int CL>
+__global__ void __launch_bounds__(1024)
 k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
              const float* __restrict__ V, float* __restrict__ HV, int nta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,7 +217,8 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
     sm.H = (long long*)p; p += sizeof(long long) * 3 * nta;
     sm.lj = (float2*)p; p += sizeof(float2) * nta;
     sm.tp = (uint32_t*)p;
-    const long long f = blockIdx.x;
+    const long long f = blockIdx.x / CL;
+    const int rank = CL == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const float* xf = X + f * n * 3;
     const float* vf = V + f * n * 3;
     for (int i = threadIdx.x; i < nta; i += blockDim.x) {
@@ -241,7 +255,7 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < ntp; q += blockDim.x) {
+    for (int q = threadIdx.x * CL + rank; q < ntp; q += blockDim.x * CL) {  // this CTA's share
         int I = 0, row = nt, r = q;
         while (r >= row) {
             r -= row;
@@ -261,15 +275,24 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
         const uint32_t w = sm.tp[k];
         hvp_tile<ELEC>(sm, tp, P.pc, (int)(w >> 16), (int)(w & 0xffff), lane);
     }
-    for (int b = threadIdx.x; b < tp.n_bonds; b += blockDim.x) hvp_bond(sm, tp, b);
-    for (int q = threadIdx.x; q < tp.n_angles; q += blockDim.x) hvp_angle(sm, tp, q);
-    __syncthreads();
+    const int t0 = threadIdx.x * CL + rank, tstep = blockDim.x * CL;
+    for (int b = t0; b < tp.n_bonds; b += tstep) hvp_bond(sm, tp, b);
+    for (int q = t0; q < tp.n_angles; q += tstep) hvp_angle(sm, tp, q);
+    hvp_cluster_sync<CL>();  // every partial of the cluster is complete
     float* out = HV + f * n * 3;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        out[3 * i] = fix2f(sm.H[i]);
-        out[3 * i + 1] = fix2f(sm.H[nta + i]);
-        out[3 * i + 2] = fix2f(sm.H[2 * nta + i]);
+    const long long* Ho = CL == 1 ? sm.H : cg::this_cluster().map_shared_rank(sm.H, (unsigned)(rank ^ 1));
+    for (int i = threadIdx.x + rank * blockDim.x; i < n; i += CL * blockDim.x) {
+        long long hx = sm.H[i], hy = sm.H[nta + i], hz = sm.H[2 * nta + i];
+        if (CL == 2) {
+            hx += Ho[i];
+            hy += Ho[nta + i];
+            hz += Ho[2 * nta + i];
+        }
+        out[3 * i] = fix2f(hx);
+        out[3 * i + 1] = fix2f(hy);
+        out[3 * i + 2] = fix2f(hz);
     }
+    hvp_cluster_sync<CL>();  // no CTA leaves while its shared memory may still be read
 }
 
 size_t hvp_smem_bytes(int nta) {
@@ -278,15 +301,36 @@ size_t hvp_smem_bytes(int nta) {
            sizeof(float2) * nta + sizeof(uint32_t) * (size_t)(nt * (nt + 1) / 2 + 4);
 }
 
+// Few frames (a checkpoint segment): a 2-CTA cluster of 1024 threads per frame, so that
+// the frames spread over the SMs; many frames: one 512-thread CTA each.
 template <int ELEC>
 static cudaError_t launch_hvp_t(const TopoDev* topo, const RunParams& P, const float* X,
                                 const float* V, float* HV, long long n_frames, int nta,
                                 cudaStream_t s) {
-    const size_t smem = hvp_smem_bytes(nta);
-    cudaError_t e = cudaFuncSetAttribute(k_hvp_frames<ELEC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, n_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    k_hvp_frames<ELEC><<<(unsigned)n_frames, 512, smem, s>>>(topo, P, X, V, HV, nta);
+    const int cl = 2 * n_frames <= n_sm ? 2 : 1;
+    const int threads = n_frames * cl <= n_sm ? 1024 : 512;
+    const size_t smem = hvp_smem_bytes(nta);
+    auto kern = cl == 2 ? k_hvp_frames<ELEC, 2> : k_hvp_frames<ELEC, 1>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_frames * cl));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, topo, P, X, V, HV, nta);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const R
                             int ncon_max, int threads, cudaStream_t stream);
 cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
                         double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
-                        int ncon_max, int threads, cudaStream_t stream);
+                        int ncon_max, int threads, int cl, cudaStream_t stream);
 cudaError_t launch_path_average_2d(const StateDev& st, int max_frames, int K, const int* sel,
                                    int n_sel, double2* out, cudaStream_t stream);
 cudaError_t launch_path_average_contacts(const StateDev& st, const int2* con_ij, int nc, int n,
@@ -984,8 +984,14 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
     const int nt = nta / kTile;
     RunParams P = s->base;
     if (!z) P.bias = 0;
+    // few frames (a checkpoint segment): a 2-CTA cluster per frame, 1024 threads per CTA,
+    // so that the frames spread over the SMs; many frames: one CTA each
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
+    const int cl = 2 * n_frames <= n_sm ? 2 : 1;
+    const int threads = n_frames * cl <= n_sm ? 1024 : auto_threads(nta);
     SCPS_CU(launch_eval(s->d.elec, s->d_topos + topo, P, X, U, F, z, n_frames, nta, nt * (nt + 1) / 2,
-                        th.ncon, auto_threads(nta), (cudaStream_t)stream));
+                        th.ncon, threads, cl, (cudaStream_t)stream));
     return SCPS_OK;
 }
 

@@ -111,3 +111,44 @@ def test_force_norm_action_gradient_with_checkpointing(torch_cuda):
     Aref = sum((ff.forces(Xn[t].astype(np.float64))[0] ** 2).sum() for t in range(T))
     assert abs(A.item() - Aref) <= 1e-4 * Aref
     s.close()
+
+
+def test_fused_action_equals_composed_double_backward(torch_cuda):
+    # the per-segment fused function and the composition through ForceGrad's own backward
+    # (the HVP as a second derivative) give the same gradient, bit for bit
+    torch = torch_cuda
+    import paper_1705_02180_gb300 as pkg
+    from paper_1705_02180_gb300.autograd import ForceGrad, force_norm_action
+    c = synth.make_chain(19, seed=1)
+    s = make(pkg, c)
+    Xn = frames_of(c, 60, 6)
+    X1 = torch.from_numpy(Xn).cuda().requires_grad_(True)
+    force_norm_action(s, X1, segment=25).backward()
+    X2 = torch.from_numpy(Xn).cuda().requires_grad_(True)
+    (ForceGrad.apply(X2, s, 0).double() ** 2).sum().backward()
+    assert torch.equal(X1.grad, X2.grad)
+    s.close()
+
+
+def test_frame_kernels_same_bits_for_every_launch_shape(torch_cuda):
+    # 200 frames run one 512-thread CTA per frame; slices of 8 frames run a 2-CTA cluster
+    # of 1024 threads per frame: energies, forces and HVPs agree bit for bit
+    torch = torch_cuda
+    import paper_1705_02180_gb300 as pkg
+    c = synth.make_chain(35, seed=1)
+    s = make(pkg, c)
+    T = 200
+    X = torch.from_numpy(frames_of(c, T, 8)).cuda()
+    V = torch.from_numpy(np.random.default_rng(9).normal(0, 1, X.shape).astype(np.float32)).cuda()
+    U1 = torch.empty(T, dtype=torch.float64, device="cuda")
+    F1, H1 = torch.empty_like(X), torch.empty_like(X)
+    s.energy_forces(0, X, U1, F1)
+    s.hvp(0, X, V, H1)
+    U2 = torch.empty_like(U1)
+    F2, H2 = torch.empty_like(X), torch.empty_like(X)
+    for a in range(0, T, 8):
+        s.energy_forces(0, X[a:a + 8], U2[a:a + 8], F2[a:a + 8])
+        s.hvp(0, X[a:a + 8], V[a:a + 8], H2[a:a + 8])
+    torch.cuda.synchronize()
+    assert torch.equal(U1, U2) and torch.equal(F1, F2) and torch.equal(H1, H2)
+    s.close()
