@@ -267,7 +267,9 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
 /* Autotuner of the resident form (chain replicas): times the launch plans
  * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} on the
  * system itself, probe_steps steps each from the current state (restored after
- * every probe; no frames are saved while probing), and keeps the fastest. The
+ * every probe; no frames are saved while probing), and keeps the fastest; a
+ * candidate replaces the current configuration (or an earlier candidate) only when
+ * it is more than 2 % faster, so timing noise does not switch shapes. The
  * choice is cached per process under (SM count, electrostatics, bias kind,
  * multiset of replica sizes); use_cache != 0 takes a cached choice without
  * probing. The plan changes only which CTA runs which replica, so trajectories

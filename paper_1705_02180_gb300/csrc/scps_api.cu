@@ -1410,7 +1410,9 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
         ++timed;
         const double us = 1e3 * ms / probe_steps;
         if (k == 0) res.us_per_step_initial = us;
-        if (us < best) {
+        // a candidate must win by more than 2 %: a shape within the timing noise of a
+        // short probe does not replace the current one (or an earlier candidate)
+        if (us < 0.98 * best) {
             best = us;
             best_c = c;
         }
