@@ -127,7 +127,8 @@ typedef struct {
     /* execution */
     int32_t exec;           /* SCPS_EXEC_* */
     int32_t cluster_size;   /* CTAs per replica in RESIDENT form: 0 = auto, 1 or 2 */
-    int32_t threads;        /* threads per CTA in RESIDENT form: 0 = auto, else 128..1024 */
+    int32_t threads;        /* threads per CTA in RESIDENT form: 0 = auto, else 128..1024
+                               (at most 768 with cluster_size 2) */
     int32_t steps_per_graph;/* device-loop steps per CUDA-graph node: 0 = auto */
     /* periodic box only */
     double skin;            /* neighbour-list buffer (nm), 0 = 0.15; a list is rebuilt when an
@@ -265,7 +266,8 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
                       double* out);
 
 /* Autotuner of the resident form (chain replicas): times the launch plans
- * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} on the
+ * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} (768 in
+ * place of 1024 for 2-CTA clusters) on the
  * system itself, probe_steps steps each from the current state (restored after
  * every probe; no frames are saved while probing), and keeps the fastest; a
  * candidate replaces the current configuration (or an earlier candidate) only when

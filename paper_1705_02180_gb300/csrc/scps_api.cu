@@ -316,6 +316,9 @@ int tile_atoms(int n) { return ((n + kTile - 1) / kTile) * kTile; }
 // group per size class (tile-rounded atom count), each with shared memory for its
 // own size. Every group gets the given cluster size and threads per CTA.
 int set_groups(scps_system* s, int plan, int cluster, int threads) {
+    if (cluster == 2 && threads > kMaxThreadsPair)
+        return fail(SCPS_ERR_INVALID_ARG, "a 2-CTA cluster takes at most %d threads per CTA",
+                    kMaxThreadsPair);
     const int R = s->d.n_replicas;
     std::vector<int> order(R);
     for (int r = 0; r < R; ++r) order[r] = r;
@@ -426,6 +429,9 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         return fail(SCPS_ERR_UNSUPPORTED, "cluster_size %d not supported (0, 1 or 2)", d->cluster_size);
     if (d->threads != 0 && (d->threads < 128 || d->threads > 1024 || d->threads % 32))
         return fail(SCPS_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 in [128, 1024]");
+    if (d->cluster_size == 2 && d->threads > kMaxThreadsPair)
+        return fail(SCPS_ERR_INVALID_ARG, "a 2-CTA cluster takes at most %d threads per CTA",
+                    kMaxThreadsPair);
     scps_system* s = new scps_system();
     s->d = *d;
     s->d.topologies = nullptr;
@@ -554,9 +560,12 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         int n_sm = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
         // a 2-CTA cluster per replica when the replicas alone leave SMs idle
-        s->cluster = d->cluster_size ? d->cluster_size : (2 * R <= n_sm ? 2 : 1);
+        s->cluster = d->cluster_size
+                         ? d->cluster_size
+                         : (2 * R <= n_sm && d->threads <= kMaxThreadsPair ? 2 : 1);
         const bool one_cta_per_sm = (long long)R * s->cluster <= n_sm;
         s->threads = d->threads ? d->threads : (one_cta_per_sm ? 1024 : auto_threads(s->nta));
+        if (s->cluster == 2 && !d->threads) s->threads = std::min(s->threads, kMaxThreadsPair);
         s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
         if (!s->is_box && d->exec == SCPS_EXEC_RESIDENT) {
             const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, 0);
@@ -1372,7 +1381,7 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
     const int n_plans = sizes.size() > 1 ? 2 : 1;
     for (int plan = 0; plan < n_plans; ++plan)
         for (int cl : {1, 2})
-            for (int th : {256, 512, 1024}) {
+            for (int th : {256, 512, cl == 2 ? kMaxThreadsPair : 1024}) {
                 std::vector<int> c{plan, cl, th};
                 if (c != cands[0]) cands.push_back(c);
             }

@@ -41,6 +41,7 @@ struct TopoDev {
 };
 
 constexpr int kMaxTubeK = 128;  // reference slices of the contact-map tube bias
+constexpr int kMaxThreadsPair = 768;  // threads per CTA of a 2-CTA cluster (80 registers each)
 
 // Per-replica addressing.
 struct RepDev {

@@ -53,3 +53,27 @@ def test_create_rejects_bad_descriptors_without_touching_the_gpu():
     d.model = pkg.MODEL_CHAIN
     d.n_replicas = 0
     assert lib.scps_create_system(C.byref(d), C.byref(h)) == -1
+
+
+def test_create_rejects_wide_ctas_in_a_cluster_on_the_host():
+    # a 2-CTA cluster runs at most 768 threads per CTA (its launch bound); the descriptor
+    # is refused before any CUDA call
+    import ctypes as C
+
+    import numpy as np
+
+    import paper_1705_02180_gb300 as pkg
+    lib = pkg.load()
+    h = C.c_void_p()
+    x0 = np.zeros((4, 3))
+    d = pkg.SystemDesc()
+    d.model = pkg.MODEL_CHAIN
+    d.n_replicas = 1
+    d.x0 = x0.ctypes.data
+    d.dt, d.gamma, d.kT = 0.002, 1.0, 2.494
+    d.cluster_size, d.threads = 2, 1024
+    assert lib.scps_create_system(C.byref(d), C.byref(h)) == -1
+    assert b"at most 768 threads" in lib.scps_last_error()
+    d.threads = 1000  # also not a multiple of 32
+    assert lib.scps_create_system(C.byref(d), C.byref(h)) == -1
+    assert b"multiple of 32" in lib.scps_last_error()
