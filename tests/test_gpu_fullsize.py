@@ -54,7 +54,7 @@ def test_chain_64x560_one_step_sampled_replicas(pkg):
     R = 64
     s, x0, v0 = _chain_system(pkg, c, R)
     info = s.info()
-    assert info["cluster_size"] == 2 and info["threads"] == 1024  # the benchmark's launch shape
+    assert info["cluster_size"] == 2 and info["threads"] == 768  # the benchmark's launch shape
     s.step(1)
     got = s.get_state()
     ff = chain_ff(c)
