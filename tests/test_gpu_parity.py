@@ -414,6 +414,8 @@ def test_cluster_pair_matches_single_cta_and_oracle(pkg):
     for k in ("x", "v", "zm", "T"):
         assert np.array_equal(out[1][1][k], out[2][1][k]), k
     assert np.array_equal(out[1][2][0]["z"], out[2][2][0]["z"])
+    for r in range(R):  # frame energies: fixed-point sums per pair pass, the same bits too
+        assert np.array_equal(out[1][2][r]["epot"], out[2][2][r]["epot"]), r
 
 
 # ------------------------------------------------------------------ size limits
