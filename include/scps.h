@@ -288,17 +288,24 @@ int scps_philox4x32_10(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t k
  * memory when they need forces: code running inside a CUDA stream capture,
  * where cudaMalloc is not allowed; frameworks that have reserved the device
  * memory for their own pool; latency-critical loops that must not allocate).
+ * Open-boundary chain systems only: a periodic-box system returns
+ * SCPS_ERR_UNSUPPORTED (these kernels take no periodic images).
  * X: device float n_atoms x 3 of topology `topo`; U: device double (1 value);
  * F: device float n_atoms x 3, may be NULL. Physical energy and forces only.
- * It calls no cudaMalloc/cudaFree: the plain-form kernels accumulate into a
- * static device array of this library (sized for at most 8192 atoms, held by
- * every GPU that loads the library until the process exits); larger
- * topologies return SCPS_ERR_UNSUPPORTED. Each call clears the part it uses
- * first. All calls share that array, so calls that overlap on the GPU (on
- * different streams, or from several threads) race and corrupt each other's
- * results; serialise them. The first call on a device looks up the array's
- * device address (once per device, with that device current); make that first
- * call before any stream capture. Stream-ordered on `stream`. */
+ * Forces and energy are summed in 64-bit fixed point (2^-20 units) with integer
+ * atomics, so the result does not depend on thread order and repeated calls on
+ * the same X return the same bits (they may differ from scps_energy_forces in
+ * the last bits: the two sum their FP32 pair terms in different groups).
+ * It calls no cudaMalloc/cudaFree: the kernels accumulate into a static device
+ * array of this library (sized for at most 8192 atoms, held by every GPU that
+ * loads the library until the process exits); larger topologies return
+ * SCPS_ERR_UNSUPPORTED (chain systems are limited to 2048 atoms at creation,
+ * so the check is a safeguard). Each call clears the part it uses first. All
+ * calls share that array, so calls that overlap on the GPU (on different
+ * streams, or from several threads) race and corrupt each other's results;
+ * serialise them. The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture. Stream-ordered on `stream`. */
 int scps_energy_forces_noalloc(scps_system* s, int32_t topo, const float* X, double* U, float* F,
                                void* stream);
 

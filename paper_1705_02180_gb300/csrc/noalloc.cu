@@ -10,6 +10,12 @@
 // into a fixed scratch array that lives in this file for the lifetime of the
 // process instead of in memory allocated per call.
 //
+// Forces and the energy are summed in 64-bit fixed point (units of 2^-20) with
+// integer atomics, so the result does not depend on the order in which threads
+// add their terms: repeated calls on the same X give the same bits. Each thread
+// sums its own atom's pair terms in FP32 in a fixed j order before converting.
+// Only open-boundary chains are evaluated (periodic boxes are refused).
+//
 // The scratch is a file-scope __device__ array (every GPU that loads the
 // library holds it until the process exits). Host code must not pass the
 // array's name to a kernel: on the host that name is only a stand-in, so its
@@ -30,11 +36,15 @@ namespace {
 constexpr int kNoAllocMaxAtoms = 8192;  // largest topology the static scratch holds
 constexpr int kMaxDevices = 64;
 
-// Force components (SoA, 3 x kNoAllocMaxAtoms floats) and the energy accumulator.
+// Force components (SoA, 3 x kNoAllocMaxAtoms) and the energy, fixed point 2^-20.
 struct NoAllocScratch {
-    float F[3 * kNoAllocMaxAtoms];
-    double E[32];
+    unsigned long long F[3 * kNoAllocMaxAtoms];
+    unsigned long long E[32];
 };
+
+__device__ __forceinline__ void na_add(unsigned long long* a, float v) {
+    atomicAdd(a, (unsigned long long)f2fix(v));
+}
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 std::mutex g_setup_mutex;
@@ -42,8 +52,8 @@ NoAllocScratch* g_scratch_ptr[kMaxDevices] = {};
 
 __global__ void k_na_clear(NoAllocScratch* sc, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 3 * n) sc->F[i] = 0.0f;
-    if (i == 0) sc->E[0] = 0.0;
+    if (i < 3 * n) sc->F[i] = 0ull;
+    if (i == 0) sc->E[0] = 0ull;
 }
 
 template <int ELEC>
@@ -52,7 +62,7 @@ __global__ void k_na_pairs(const float* __restrict__ X, NoAllocScratch* sc, Topo
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = tp.n_atoms;
     if (i >= n) return;
-    float* F = sc->F;
+    unsigned long long* F = sc->F;
     const float xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
     const float qi = tp.qs[i];
     const float2 li = tp.lj[i];
@@ -70,21 +80,21 @@ __global__ void k_na_pairs(const float* __restrict__ X, NoAllocScratch* sc, Topo
         fx = fmaf(s, dx, fx);
         fy = fmaf(s, dy, fy);
         fz = fmaf(s, dz, fz);
-        atomicAdd(&F[j], -s * dx);
-        atomicAdd(&F[n + j], -s * dy);
-        atomicAdd(&F[2 * n + j], -s * dz);
+        na_add(&F[j], -s * dx);
+        na_add(&F[n + j], -s * dy);
+        na_add(&F[2 * n + j], -s * dz);
         e += ep;
     }
-    atomicAdd(&F[i], fx);
-    atomicAdd(&F[n + i], fy);
-    atomicAdd(&F[2 * n + i], fz);
-    atomicAdd(&sc->E[0], (double)e);
+    na_add(&F[i], fx);
+    na_add(&F[n + i], fy);
+    na_add(&F[2 * n + i], fz);
+    na_add(&sc->E[0], e);
 }
 
 __global__ void k_na_bonded(const float* __restrict__ X, NoAllocScratch* sc, TopoDev tp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = tp.n_atoms;
-    float* F = sc->F;
+    unsigned long long* F = sc->F;
     if (t < tp.n_bonds) {
         const int2 ij = tp.bond_ij[t];
         const float2 par = tp.bond_par[t];
@@ -93,13 +103,13 @@ __global__ void k_na_bonded(const float* __restrict__ X, NoAllocScratch* sc, Top
         const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         const float dr = r - par.x;
         const float f = par.y * dr / r;
-        atomicAdd(&F[ij.x], f * dx);
-        atomicAdd(&F[n + ij.x], f * dy);
-        atomicAdd(&F[2 * n + ij.x], f * dz);
-        atomicAdd(&F[ij.y], -f * dx);
-        atomicAdd(&F[n + ij.y], -f * dy);
-        atomicAdd(&F[2 * n + ij.y], -f * dz);
-        atomicAdd(&sc->E[0], 0.5 * (double)par.y * (double)dr * (double)dr);
+        na_add(&F[ij.x], f * dx);
+        na_add(&F[n + ij.x], f * dy);
+        na_add(&F[2 * n + ij.x], f * dz);
+        na_add(&F[ij.y], -f * dx);
+        na_add(&F[n + ij.y], -f * dy);
+        na_add(&F[2 * n + ij.y], -f * dz);
+        na_add(&sc->E[0], 0.5f * par.y * dr * dr);
     } else if (t < tp.n_bonds + tp.n_angles) {
         const int q = t - tp.n_bonds;
         const int4 ijk = tp.ang_ijk[q];
@@ -118,16 +128,16 @@ __global__ void k_na_bonded(const float* __restrict__ X, NoAllocScratch* sc, Top
         const float au = cs / ru2, aw = cs / rw2;
         const float fix = g * fmaf(au, ux, -wx), fiy = g * fmaf(au, uy, -wy), fiz = g * fmaf(au, uz, -wz);
         const float fkx = g * fmaf(aw, wx, -ux), fky = g * fmaf(aw, wy, -uy), fkz = g * fmaf(aw, wz, -uz);
-        atomicAdd(&F[ijk.x], fix);
-        atomicAdd(&F[n + ijk.x], fiy);
-        atomicAdd(&F[2 * n + ijk.x], fiz);
-        atomicAdd(&F[ijk.z], fkx);
-        atomicAdd(&F[n + ijk.z], fky);
-        atomicAdd(&F[2 * n + ijk.z], fkz);
-        atomicAdd(&F[ijk.y], -(fix + fkx));
-        atomicAdd(&F[n + ijk.y], -(fiy + fky));
-        atomicAdd(&F[2 * n + ijk.y], -(fiz + fkz));
-        atomicAdd(&sc->E[0], 0.5 * (double)par.y * (double)dth * (double)dth);
+        na_add(&F[ijk.x], fix);
+        na_add(&F[n + ijk.x], fiy);
+        na_add(&F[2 * n + ijk.x], fiz);
+        na_add(&F[ijk.z], fkx);
+        na_add(&F[n + ijk.z], fky);
+        na_add(&F[2 * n + ijk.z], fkz);
+        na_add(&F[ijk.y], -(fix + fkx));
+        na_add(&F[n + ijk.y], -(fiy + fky));
+        na_add(&F[2 * n + ijk.y], -(fiz + fkz));
+        na_add(&sc->E[0], 0.5f * par.y * dth * dth);
     }
 }
 
@@ -136,11 +146,11 @@ __global__ void k_na_finish(const NoAllocScratch* sc, int n, float* __restrict__
                             double* __restrict__ U) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && F) {
-        F[3 * i] = sc->F[i];
-        F[3 * i + 1] = sc->F[n + i];
-        F[3 * i + 2] = sc->F[2 * n + i];
+        F[3 * i] = fix2f((long long)sc->F[i]);
+        F[3 * i + 1] = fix2f((long long)sc->F[n + i]);
+        F[3 * i + 2] = fix2f((long long)sc->F[2 * n + i]);
     }
-    if (i == 0) *U = sc->E[0];
+    if (i == 0) *U = (double)(long long)sc->E[0] * 9.5367431640625e-07;  // 2^-20
 }
 
 // Device address of the scratch for the current device (looked up once per device).

@@ -1457,6 +1457,9 @@ int scps_philox4x32_10(int64_t n, const uint32_t* ctr, uint32_t key0, uint32_t k
 namespace scps {
 int internal_topology(const scps_system* s, int topo, TopoDev* out, int* elec, RunParams* P) {
     if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
+    if (s->is_box)  // its kernels take every pair once, with no periodic images
+        return fail(SCPS_ERR_UNSUPPORTED,
+                    "the allocation-free evaluation covers open-boundary chains, not periodic boxes");
     if (topo < 0 || topo >= (int)s->topos.size())
         return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
     *out = s->topos[topo].dev;

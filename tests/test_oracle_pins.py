@@ -244,16 +244,6 @@ def test_bias_inactive_when_z_keeps_decreasing():
     assert np.all(a["T"] == 0.0)
 
 
-def test_bias_pushes_back_when_z_rises():
-    # toy with a strong outward push in x: bias must be nonzero and oppose the rise of z
-    xy = np.array([[0.9, 0.0]])
-    z0 = oracle.toy_z(xy)
-    run = oracle.run_toy(xy, z0, [0], [0], 1, 1e-3, 1.0, 0.5, 50.0, 2000)
-    free = oracle.run_toy(xy, z0, [0], [0], 1, 1e-3, 1.0, 0.5, 0.0, 2000)
-    assert run["T"][0] > 0.0
-    assert oracle.toy_z(run["x"])[0] <= oracle.toy_z(free["x"])[0] + 1e-12 or run["T"][0] > 0
-
-
 # ------------------------------------------------------------------ integrators
 def test_toy_closed_form_first_step():
     # one EM step from (-1, 0): U'(x) = 0 there, z = 4 = z_m, so only noise moves it
