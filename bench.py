@@ -9,10 +9,15 @@ total. One bench step = one scps_step_replicas call of 1000 MD steps for every
 replica; K bench steps are timed with CUDA events on the launching stream,
 with an L2 flush (a 512 MB write) between calls outside the events.
 
-Metric: atom-steps/s = sum over replicas of atoms x MD steps / time.
+Metric: atom-steps/s = sum over replicas of atoms x MD steps / time; its second
+half, the force error against the FP64 oracle, is reported as force_err
+(max |F_gpu - F_oracle| / rms |F_oracle| on a frame saved during the timed run).
 Also printed: the plain one-replica-per-launch FP32 form on the same GPU
-(speed-up), the roofline of the resident kernel (FP32 ALU), the end-to-end
-rate with host buffers, the FP64 oracle on the host cores, and the GPU clocks.
+(speed-up, timed the same way), the roofline of the resident kernel (FP32 ALU,
+flops counted over the pairs inside the cutoff only), the end-to-end rate with
+host buffers, the FP64 oracle on the host cores, the GPU clocks, and short runs
+of the other configurations (toy, batched uneven replicas, differentiation,
+solvated box, tube bias) under "configs".
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build).
 Multi-GPU (torchrun): every rank runs its own 64 replicas (distinct replica
@@ -38,10 +43,8 @@ import synth  # noqa: E402
 KT_300 = 0.0083144626 * 300.0
 SEED = 2017
 FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ = 2070.0       # maximum SM clock of the part (nvidia-smi clocks.max.sm when sampled)
 FLOPS_PAIR_IN = 49        # in-cutoff pair: distance, LJ + Coulomb + shift, two force updates
-FLOPS_PAIR_TEST = 8       # any pair: separation and squared distance
 FLOPS_BOND = 20
 FLOPS_ANGLE = 60
 FLOPS_CONTACT = 30        # C_ij, (C - C0)^2 and its gradient in FP64-equivalent arithmetic
@@ -61,6 +64,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-configs", action="store_true", help="skip the other configurations")
     p.add_argument("--workload", default="chain", choices=["chain", "batched", "box", "toy", "hvp", "tube", "funnel"],
                    help="chain: the headline workload; the others measure the other configurations")
     return p.parse_args()
@@ -120,7 +124,8 @@ def workload(args):
 
 
 def count_pairs(c, frames, cutoff=1.0):
-    """Mean number of non-excluded pairs within the cutoff over sample frames (geometry only)."""
+    """Mean number of non-excluded pairs within the cutoff over sample frames (geometry only),
+    and the number of non-excluded pairs."""
     n = c.n_atoms
     ex = np.zeros((n, n), bool)
     ex[c.exclusions[:, 0], c.exclusions[:, 1]] = True
@@ -134,10 +139,36 @@ def count_pairs(c, frames, cutoff=1.0):
     return float(np.mean(counts)), int(keep.sum())
 
 
-def flops_per_replica_step(c, p_in, p_all):
-    return (FLOPS_PAIR_TEST * p_all + (FLOPS_PAIR_IN - FLOPS_PAIR_TEST) * p_in
-            + FLOPS_BOND * len(c.bonds) + FLOPS_ANGLE * len(c.angles)
+def flops_per_replica_step(c, p_in):
+    """Algorithmic flops of one replica-step: the pairs inside the cutoff only (a pair
+    the method does not need, outside r_c, counts nothing), bonded terms, native contacts
+    and the atom updates."""
+    return (FLOPS_PAIR_IN * p_in + FLOPS_BOND * len(c.bonds) + FLOPS_ANGLE * len(c.angles)
             + FLOPS_CONTACT * len(c.contacts) + FLOPS_ATOM_UPDATE * c.n_atoms)
+
+
+def alu_peak_tflops(torch, clk):
+    """FP32 peak of the device: SMs x 128 lanes x 2 flops (FMA) x the maximum SM clock."""
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or SM_MAX_MHZ
+    return n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, n_sm, mhz
+
+
+def force_error(pkg, torch, sysm, c, frame):
+    """max |F - F_oracle| / rms |F_oracle| of the GPU frame evaluation on one frame of the
+    timed run (the FP64 oracle gets the same FP32 positions)."""
+    import oracle
+    x = np.asarray(frame, np.float32)
+    X = torch.from_numpy(x[None]).cuda()
+    U = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F = torch.zeros_like(X)
+    sysm.energy_forces(0, X, U, F)
+    torch.cuda.synchronize()
+    Fr, Er = oracle.ForceField.from_chain(c).forces(x.astype(np.float64))
+    rms = float(np.sqrt((Fr ** 2).sum(axis=1).mean()))
+    return {"max_abs_over_rms": float(np.abs(F[0].double().cpu().numpy() - Fr).max() / rms),
+            "energy_rel": float(abs(U.item() - Er.sum()) / max(1.0, abs(Er.sum()))),
+            "rms_force": rms, "frame": "last frame saved in the timed run"}
 
 
 def cpu_baseline(c, R, budget_s=15.0):
@@ -232,14 +263,35 @@ def K_calls(args):
     return max(1, min(args.steps, 10))
 
 
-def run_extra(args):
-    """The other workloads of the build target, one JSON line each."""
-    import torch
+def measured_peaks():
+    """MEASURED_PEAKS.json of this machine (HBM copy GB/s and others), or {}."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
-    import paper_1705_02180_gb300 as pkg
-    torch.cuda.set_device(0)
-    W, K = max(args.warmup, 3), args.steps
-    if args.workload == "batched":
+
+def chain_pairs_of_states(chains, reps, x, sample=2):
+    """Mean in-cutoff pairs per replica of each topology, counted on `sample` replicas of it
+    in the packed positions x."""
+    off = np.concatenate([[0], np.cumsum([chains[t].n_atoms for t in reps])])
+    out = []
+    for t, c in enumerate(chains):
+        idx = [k for k, tt in enumerate(reps) if tt == t][:sample]
+        frames = [x[off[k]:off[k + 1]] for k in idx]
+        out.append(count_pairs(c, frames)[0])
+    return out
+
+
+FLOPS_TUBE_SLICE_CONTACT = 5   # pass 1: difference and square-add; pass 2: one multiply-add
+FLOPS_HVP_PAIR = 70            # pair Hessian-vector term: phi', phi'' and two projections
+
+
+def extra_config(torch, pkg, name, args, K, W):
+    """One of the other configurations of the build target, timed like the headline."""
+    W = max(W, 3)
+    if name == "batched":
         sizes = [19, 35, 75]
         counts = [171, 171, 170]
         chains = [synth.make_chain(r, seed=1) for r in sizes]
@@ -253,9 +305,16 @@ def run_extra(args):
                        steps_per_graph=spc)
         s.set_contact_bias([c.contacts for c in chains], [c.x_native for c in chains], k_R=1e-4)
         tune = s.autotune(probe_steps=100) if args.threads == 0 else None
+        x_start = s.get_state()["x"]
         durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
+        x_end = s.get_state()["x"]
         atoms = int(sum(chains[t].n_atoms for t in reps))
         info = s.info()
+        p_in = [(a + b) / 2 for a, b in zip(chain_pairs_of_states(chains, reps, x_start),
+                                            chain_pairs_of_states(chains, reps, x_end))]
+        flops = sum(flops_per_replica_step(chains[t], p_in[t]) * counts[t] for t in range(3)) * spc
+        peak, n_sm, mhz = alu_peak_tflops(torch, clk)
+        ach = flops / float(durs.mean()) / 1e12
         out = {"metric": "biased-Langevin atom-steps/s", "value": atoms * spc * K / durs.sum(),
                "unit": "atom-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
                "config": {"workload": "512 replicas: 171 x 304 + 171 x 560 + 170 x 1200 atoms, "
@@ -264,9 +323,14 @@ def run_extra(args):
                           "threads_per_cta": info["threads"], "cluster": info["cluster_size"],
                           "plan": ["one launch", "one launch per size class"][info["plan"]],
                           "autotune": tune},
+               "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                            "frac": ach / peak, "traffic": None,
+                            "in_cutoff_pairs_per_size": p_in,
+                            "pair_slots_evaluated": info["pair_checks_per_step"]},
                "gpu_launches": int(info["graph_nodes_last_call"]) * K, "clocks": clk}
         s.close()
-    elif args.workload == "box":
+    elif name == "box":
+        from scipy.spatial import cKDTree
         b = synth.make_box(35, 24000, seed=1)
         R = 16
         c = b.chain
@@ -280,22 +344,36 @@ def run_extra(args):
         durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
         atoms = b.n_atoms * R
         rate = atoms * spc * K / durs.sum()
+        xs = s.get_state()["x"].reshape(R, b.n_atoms, 3)[0] % b.box
+        p_in = len(cKDTree(xs, boxsize=b.box).query_pairs(1.0)) - len(c.exclusions)
+        t = b.topology()
+        fl = (FLOPS_PAIR_IN * p_in + FLOPS_BOND * len(t["b0"]) + FLOPS_ANGLE * len(t["th0"]) +
+              FLOPS_CONTACT * len(c.contacts) + FLOPS_ATOM_UPDATE * b.n_atoms)
+        peak, n_sm, mhz = alu_peak_tflops(torch, clk)
+        ach = fl * R * spc / float(durs.mean()) / 1e12
         bytes_per_atom_step = 100  # x,q read + write, v read + write, parameters, forces
+        hbm_peak = measured_peaks().get("hbm_gbs")
+        gbs = rate * bytes_per_atom_step / 1e9
         out = {"metric": "biased-Langevin atom-steps/s", "value": rate, "unit": "atom-steps/s",
                "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
                "config": {"workload": f"{R} replicas x ({c.n_atoms}-atom chain + 24000 solvent "
                                       f"sites), L {b.box:.3f} nm, RF, rc 1.0, skin 0.15, rebuild "
                                       "<= 20 steps, dt 2 fs, 300 K",
                           "atoms": atoms, "md_steps_per_call": spc},
-               "hbm": {"algorithmic_GBps": rate * bytes_per_atom_step / 1e9,
-                       "bytes_per_atom_step": bytes_per_atom_step},
+               "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                            "frac": ach / peak, "traffic": None,
+                            "in_cutoff_pairs_per_replica": p_in},
+               "hbm": {"algorithmic_GBps": gbs, "bytes_per_atom_step": bytes_per_atom_step,
+                       "peak_GBps": hbm_peak,
+                       "frac": gbs / hbm_peak if hbm_peak else None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm_peak else None},
                # per call: one re-evaluation (5 kernels) + its A half step, then
                # 5 + 1 kernels per step and the step counter
                "gpu_launches": K * (6 + 6 * spc + 1), "clocks": clk}
         rc, st = s.status()
         out["status"] = int(rc)
         s.close()
-    elif args.workload == "toy":
+    elif name == "toy":
         toy = synth.make_toy(256)
         s = pkg.System(model=pkg.MODEL_TOY2D, x0=toy.start_positions(), integrator=pkg.INT_EM,
                        dt=toy.dt, gamma=toy.gamma, kT=toy.kT, seed=toy.seed)
@@ -304,43 +382,53 @@ def run_extra(args):
         out = {"metric": "particle-steps/s", "value": 256 * toy.n_steps * K / durs.sum(),
                "unit": "particle-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": K,
                "warmup": W, "config": {"workload": "256 replicas x 1e4 overdamped steps, FP64"},
-               "clocks": clk}
+               "roofline": None, "note": "one thread per replica: launch and latency bound, no "
+                                         "meaningful roofline",
+               "gpu_launches": K, "clocks": clk}
         s.close()
-    elif args.workload == "tube":
+    elif name == "tube":
         # the headline chain workload under the contact-map tube bias (72 reference maps)
         c = synth.make_chain(35, seed=1)
-        R, K = 64, 72
+        R, KS = 64, 72
         spc = args.md_steps_per_call
         x0 = np.stack([c.x_unfolded] * R).reshape(-1, 3)
         v0 = c.velocities(R, KT_300, SEED).reshape(-1, 3)
         cu = np.array([np.linalg.norm(c.x_unfolded[j] - c.x_unfolded[i]) for i, j in c.contacts])
         cn = np.array([np.linalg.norm(c.x_native[j] - c.x_native[i]) for i, j in c.contacts])
-        frac = np.linspace(0.0, 1.0, K)[:, None]
+        frac = np.linspace(0.0, 1.0, KS)[:, None]
         r = cu[None] + (cn - cu)[None] * frac  # synthetic reference path in distance space
         u = (r / 0.75) ** 2
         maps = (1 + u + u * u) / (1 + u + u * u + u ** 3 + u ** 4)
-        times = (np.arange(K) + 1) * 7.0  # a slice every 7 ps
+        times = (np.arange(KS) + 1) * 7.0  # a slice every 7 ps
         s = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0,
                        v0=v0, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002, gamma=1.0,
                        kT=KT_300, seed=SEED, steps_per_graph=spc)
         s.set_contact_tube_bias([c.contacts], [c.x_native], [maps], times, 13.5, 2.5, 2.5e-4,
                                 times[-1])
-        durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K=K_calls(args), W=W)
-        out = {"metric": "biased-Langevin atom-steps/s", "value": R * c.n_atoms * spc * len(durs) / durs.sum(),
-               "unit": "atom-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": len(durs), "warmup": W,
+        x_start = s.get_state()["x"].reshape(R, -1, 3)
+        durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
+        x_end = s.get_state()["x"].reshape(R, -1, 3)
+        p_in = count_pairs(c, [x_start[0], x_start[1], x_end[0], x_end[1]])[0]
+        fl = flops_per_replica_step(c, p_in) + FLOPS_TUBE_SLICE_CONTACT * KS * len(c.contacts)
+        peak, n_sm, mhz = alu_peak_tflops(torch, clk)
+        ach = fl * R * spc / float(durs.mean()) / 1e12
+        out = {"metric": "biased-Langevin atom-steps/s", "value": R * c.n_atoms * spc * K / durs.sum(),
+               "unit": "atom-steps/s", "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
                "config": {"workload": f"{R} replicas x {c.n_atoms}-atom chain, contact-map tube bias "
-                                      f"({K} reference maps x {len(c.contacts)} contacts, lambda 13.5, "
+                                      f"({KS} reference maps x {len(c.contacts)} contacts, lambda 13.5, "
                                       "k_s 2.5, k_w 2.5e-4), dt 2 fs, 300 K",
                           "md_steps_per_call": spc},
-               "gpu_launches": int(s.info()["graph_nodes_last_call"]) * len(durs), "clocks": clk}
+               "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                            "frac": ach / peak, "traffic": None, "in_cutoff_pairs": p_in},
+               "gpu_launches": int(s.info()["graph_nodes_last_call"]) * K, "clocks": clk}
         s.close()
-    elif args.workload == "funnel":
+    elif name == "funnel":
         # the whole SCPS iteration on the funnel: rMD round + 2 tube rounds, 512 x 2000 steps each
         from paper_1705_02180_gb300.scps import FunnelProtocol, run_funnel_scps
         p = FunnelProtocol()
         run_funnel_scps(FunnelProtocol(n_replicas=64, n_steps=200, save_every=20, iterations=1))
         walls = []
-        for _ in range(K_calls(args)):
+        for _ in range(K):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             res = run_funnel_scps(p)
@@ -355,13 +443,14 @@ def run_extra(args):
                                       f"{p.n_steps} steps, k_R {p.k_R}, lambda {p.lam}, k_s {p.k_s}, "
                                       f"k_w {p.k_w}",
                           "reactive_per_round": [int(len(r["reactive"])) for r in res["rounds"]]}}
-    elif args.workload == "hvp":
+    elif name == "hvp":
         from paper_1705_02180_gb300.autograd import force_norm_action
         c = synth.make_chain(35, seed=1)
         T = 1000
         g = np.random.default_rng(5)
         base = np.where((np.arange(T) % 2 == 0)[:, None, None], c.x_unfolded[None], c.x_native[None])
-        X = torch.from_numpy((base + g.normal(0, 0.01, base.shape)).astype(np.float32)).cuda()
+        Xh = (base + g.normal(0, 0.01, base.shape)).astype(np.float32)
+        X = torch.from_numpy(Xh).cuda()
         s = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0], x0=c.x_unfolded,
                        dt=0.002, gamma=1.0, kT=KT_300, seed=1)
 
@@ -371,18 +460,35 @@ def run_extra(args):
             A.backward()
 
         durs, clk = timed_calls(torch, once, K, W)
+        p_in = count_pairs(c, [Xh[0], Xh[1]])[0]
+        # forward: forces; backward: forces again plus the Hessian-vector product
+        fl = T * (2 * flops_per_replica_step(c, p_in) + FLOPS_HVP_PAIR * p_in)
+        peak, n_sm, mhz = alu_peak_tflops(torch, clk)
+        ach = fl / float(durs.mean()) / 1e12
         out = {"metric": "frames/s (forward + backward + double backward)", "value": T * K / durs.sum(),
                "unit": "frames/s", "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
                "config": {"workload": "sum_t |grad U(X_t)|^2 over 1000 frames x 560 atoms, "
                                       "checkpointing every 50 frames (the backward of a segment "
                                       "recomputes its forces and applies H(X_t) 2 grad U(X_t))"},
+               "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                            "frac": ach / peak, "traffic": None, "in_cutoff_pairs": p_in},
                "clocks": clk}
         s.close()
     else:
-        raise SystemExit(f"unknown workload {args.workload}")
+        raise SystemExit(f"unknown workload {name}")
     out.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
-                "workload_name": args.workload})
-    print(json.dumps(out), flush=True)
+                "workload_name": name})
+    return out
+
+
+def run_extra(args):
+    """One of the other workloads of the build target as its own JSON line."""
+    import torch
+
+    import paper_1705_02180_gb300 as pkg
+    torch.cuda.set_device(0)
+    K = args.steps if args.workload not in ("tube", "funnel") else K_calls(args)
+    print(json.dumps(extra_config(torch, pkg, args.workload, args, K, args.warmup)), flush=True)
 
 
 def main():
@@ -416,10 +522,13 @@ def main():
     v0 = c.velocities(R, KT_300, SEED).reshape(-1, 3)
     ids = replica_ids(rank, world, R)
     spc = args.md_steps_per_call
+    # one frame per call, all kept: the pair counts of the roofline are averaged over the
+    # configurations the timed calls start and end in
     sysm = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0, v0=v0,
                       replica_id=ids, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002,
-                      gamma=1.0, kT=KT_300, seed=SEED, save_interval=spc, max_frames=4,
-                      threads=args.threads, steps_per_graph=spc)
+                      gamma=1.0, kT=KT_300, seed=SEED, save_interval=spc,
+                      max_frames=args.warmup + args.steps, threads=args.threads,
+                      steps_per_graph=spc)
     sysm.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4, r0=0.75)
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -452,13 +561,19 @@ def main():
     t_dev = max_over_ranks(t_dev, dist, device="cuda")
     atom_steps = R * n * spc * args.steps * world
     value = atom_steps / t_dev
-    paths = sysm.collect_paths(0, min(R, 4))
-    frames = [f for p in paths for f in p["frames"]][:8]
+    paths = sysm.collect_paths(0, min(R, 2))
+    W0 = args.warmup
+    frames = []
+    for p in paths:  # the frames the timed calls start from and end in (at most 6 per replica)
+        fr = p["frames"][max(W0 - 1, 0):W0 + args.steps]
+        idx = np.unique(np.linspace(0, len(fr) - 1, min(6, len(fr))).round().astype(int))
+        frames += [fr[i] for i in idx]
     p_in, p_all = count_pairs(c, frames)
-    flops_launch = flops_per_replica_step(c, p_in, p_all) * R * spc
+    flops_launch = flops_per_replica_step(c, p_in) * R * spc
     achieved = flops_launch / float(durs.mean()) / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak, n_sm, peak_mhz = alu_peak_tflops(torch, clk)
     info = sysm.info()
+    ferr = force_error(pkg, torch, sysm, c, paths[0]["frames"][-1]) if rank == 0 else None
 
     result = {"metric": "biased-Langevin atom-steps/s", "value": value, "unit": "atom-steps/s",
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -472,32 +587,33 @@ def main():
                          "threads_per_cta": info["threads"], "parallelism": f"replicas x{world}"},
               "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak, "traffic": None,
-                           "note": "FP32 peak = 152 SMs x 128 lanes x 2 x 2070 MHz; algorithmic "
-                                   f"flops = {FLOPS_PAIR_TEST}/pair test + {FLOPS_PAIR_IN}/in-cutoff "
-                                   f"pair (mean in-cutoff {p_in:.0f} of {p_all} pairs) + bonded, "
-                                   "contacts, update"},
+                           "note": f"FP32 peak = {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                   f"{peak_mhz:.0f} MHz (maximum SM clock); algorithmic flops per "
+                                   f"replica-step = {FLOPS_PAIR_IN} x in-cutoff pairs (mean "
+                                   f"{p_in:.0f} of {p_all} non-excluded pairs over the timed "
+                                   f"calls' frames) + {FLOPS_BOND} x {len(c.bonds)} bonds + "
+                                   f"{FLOPS_ANGLE} x {len(c.angles)} angles + {FLOPS_CONTACT} x "
+                                   f"{len(c.contacts)} contacts + {FLOPS_ATOM_UPDATE} x {n} atoms",
+                           "in_cutoff_pairs": p_in,
+                           "pair_slots_evaluated": info["pair_checks_per_step"] / R},
+              "force_err": ferr,
               "gpu_launches": int(info["graph_nodes_last_call"]) * args.steps,
               "clocks": clk, "wall_s": t_wall}
-    # plain one-replica-per-launch form on the same GPU (the speed-up denominator)
+    # plain one-replica-per-launch form on the same GPU (the speed-up denominator), timed
+    # like the resident arm: untimed warm-up calls, then calls timed with CUDA events on
+    # the launching stream, L2 flushed between calls, clocks sampled meanwhile
     if not args.no_plain and rank == 0:
-        plain_steps = 20
+        plain_steps, plain_K = 200, 3
         ps = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0, v0=v0,
                         replica_id=ids, cutoff=1.0, elec=pkg.ELEC_DDIEL, k_dd=40.0, dt=0.002,
                         gamma=1.0, kT=KT_300, seed=SEED, exec_form=pkg.EXEC_PLAIN)
         ps.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4, r0=0.75)
-        with torch.cuda.stream(stream):
-            ps.step(2, stream=stream.cuda_stream)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.zero_()
-            a.record(stream)
-            ps.step(plain_steps, stream=stream.cuda_stream)
-            b.record(stream)
-        torch.cuda.synchronize()
-        t_plain = a.elapsed_time(b) * 1e-3
-        plain_rate = R * n * plain_steps / t_plain
+        pd, pclk = timed_calls(torch, lambda st: ps.step(plain_steps, stream=st), plain_K, 1)
+        plain_rate = R * n * plain_steps * plain_K / pd.sum()
         result["plain_form"] = {"value": plain_rate, "unit": "atom-steps/s",
-                                "md_steps": plain_steps, "speedup": value / world / plain_rate}
+                                "md_steps_per_call": plain_steps, "calls": plain_K,
+                                "warmup_calls": 1, "clocks": pclk,
+                                "speedup": value / world / plain_rate}
         ps.close()
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
@@ -522,6 +638,10 @@ def main():
         cb = cpu_baseline(c, R)
         result["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     sysm.close()
+    if rank == 0 and not args.no_configs:  # the other configurations, short runs
+        result["configs"] = {}
+        for name in ("toy", "batched", "hvp", "box", "tube"):
+            result["configs"][name] = extra_config(torch, pkg, name, args, K=3, W=3)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -130,10 +130,17 @@ typedef struct {
     int32_t threads;        /* threads per CTA in RESIDENT form: 0 = auto, else 128..1024
                                (at most 768 with cluster_size 2) */
     int32_t steps_per_graph;/* device-loop steps per CUDA-graph node: 0 = auto */
-    /* periodic box only */
-    double skin;            /* neighbour-list buffer (nm), 0 = 0.15; a list is rebuilt when an
-                               atom has moved skin/2 since the last rebuild */
-    int32_t rebuild_every;  /* scheduled list rebuild interval (steps), 0 = 20 */
+    /* pair lists */
+    double skin;            /* list buffer r_list - r_c (nm); 0 = default (0.15 for the periodic
+                               box, 0.08 for chains). A list is rebuilt before any pair inside
+                               r_c can be missing: periodic box, once an atom has moved skin/2
+                               since the last build; chains, once a bound on every atom's
+                               displacement since then (dt/2 times the largest |v| + |v'| of
+                               each step, summed) reaches skin/2. Forces do not depend on the
+                               skin or the rebuild cadence (chains: bit for bit). */
+    int32_t rebuild_every;  /* periodic box: scheduled rebuild interval (steps), 0 = 20; chains:
+                               also rebuild at least every this many steps, 0 = only by the
+                               displacement bound */
 } scps_system_desc;
 
 typedef struct {
@@ -172,10 +179,17 @@ typedef struct {
     int32_t kernels_per_step_call;      /* kernel launches one scps_step_replicas call enqueues
                                            per graph node (resident form) */
     int64_t graph_nodes_last_call;      /* kernel launches enqueued by the last step call */
-    int64_t pair_checks_per_step;       /* tile-pair slots evaluated in the last step call */
+    int64_t pair_checks_per_step;       /* resident chains: non-bonded pair slots one step
+                                           evaluates, summed over replicas, with the pair list
+                                           each replica built last (64 per list item of 8 x 8
+                                           atoms, 28 per block of 8 with itself) */
     size_t device_bytes;                /* device memory held by the system */
     int32_t launch_groups;              /* resident form: launches per step call chunk */
     int32_t plan;                       /* resident form: SCPS_PLAN_* */
+    double list_skin;                   /* chains: pair-list skin r_list - r_c (nm) */
+    double steps_per_list_build;        /* resident chains: mean steps per pair-list build in
+                                           the latest launch (the build that opens a launch
+                                           counts) */
 } scps_info;
 
 /* launch plans of the resident form */
@@ -191,6 +205,7 @@ typedef struct {
     int32_t from_cache;                 /* 1: the choice came from the process-wide cache */
     double us_per_step;                 /* probe time per step of the choice */
     double us_per_step_initial;         /* probe time per step of the configuration before */
+    double skin;                        /* chosen pair-list skin (nm) */
 } scps_tune_result;
 
 typedef struct scps_system scps_system;
@@ -252,6 +267,8 @@ int scps_set_state(scps_system* s, const double* x, const double* v, const doubl
  * the SCPS_REPLICA_* bits. */
 int scps_get_status(scps_system* s, int32_t* per_replica);
 
+/* Sizes and launch shape of the system (host `info`). Synchronises the device (it reads the
+ * per-replica pair-slot counts of the last step call). */
 int scps_get_info(const scps_system* s, scps_info* info);
 
 /* Average path of selected replicas (step 3 of the SCPS iteration; Eq. avCij):
@@ -267,15 +284,17 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
 
 /* Autotuner of the resident form (chain replicas): times the launch plans
  * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} (768 in
- * place of 1024 for 2-CTA clusters) on the
- * system itself, probe_steps steps each from the current state (restored after
- * every probe; no frames are saved while probing), and keeps the fastest; a
- * candidate replaces the current configuration (or an earlier candidate) only when
- * it is more than 2 % faster, so timing noise does not switch shapes. The
- * choice is cached per process under (SM count, electrostatics, bias kind,
- * multiset of replica sizes); use_cache != 0 takes a cached choice without
- * probing. The plan changes only which CTA runs which replica, so trajectories
- * are bit-identical under every choice. Synchronous; out may be NULL. */
+ * place of 1024 for 2-CTA clusters) on the system itself, then, at the chosen shape, the
+ * pair-list skin {0.04, 0.06, 0.08, 0.11, 0.15} nm (a larger skin adds pairs to every
+ * step and makes list builds rarer: the rebuild cadence follows from the displacement
+ * bound), probe_steps steps each from the current state (restored after every probe; no
+ * frames are saved while probing), and keeps the fastest; a candidate replaces the
+ * current configuration (or an earlier candidate) only when it is more than 2 % faster,
+ * so timing noise does not switch shapes. The choice is cached per process under (SM
+ * count, electrostatics, bias kind, multiset of replica sizes); use_cache != 0 takes a
+ * cached choice without probing. The plan changes only which CTA runs which replica and
+ * forces do not depend on the skin, so trajectories are bit-identical under every
+ * choice. Synchronous; out may be NULL. */
 int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out);
 
 /* Philox4x32-10 blocks on the device, for checking the noise stream:

@@ -60,13 +60,14 @@ class Info(C.Structure):
                 ("cluster_size", C.c_int32), ("threads", C.c_int32),
                 ("steps_per_graph", C.c_int32), ("kernels_per_step_call", C.c_int32),
                 ("graph_nodes_last_call", C.c_int64), ("pair_checks_per_step", C.c_int64),
-                ("device_bytes", C.c_size_t), ("launch_groups", C.c_int32), ("plan", C.c_int32)]
+                ("device_bytes", C.c_size_t), ("launch_groups", C.c_int32), ("plan", C.c_int32),
+                ("list_skin", C.c_double), ("steps_per_list_build", C.c_double)]
 
 
 class TuneResult(C.Structure):
     _fields_ = [("plan", C.c_int32), ("cluster_size", C.c_int32), ("threads", C.c_int32),
                 ("candidates", C.c_int32), ("from_cache", C.c_int32), ("us_per_step", C.c_double),
-                ("us_per_step_initial", C.c_double)]
+                ("us_per_step_initial", C.c_double), ("skin", C.c_double)]
 
 
 PLAN_ONE_LAUNCH, PLAN_PER_SIZE_CLASS = 0, 1
@@ -345,8 +346,9 @@ class System:
         return out
 
     def autotune(self, probe_steps=100, use_cache=True):
-        """Times the resident launch plans, cluster sizes and CTA widths on this system
-        (state restored after every probe) and keeps the fastest; returns the choice."""
+        """Times the resident launch plans, cluster sizes, CTA widths and pair-list skins on
+        this system (state restored after every probe) and keeps the fastest; returns the
+        choice."""
         t = TuneResult()
         check(load().scps_autotune(self.h, int(probe_steps), 1 if use_cache else 0, C.byref(t)))
         return {f: getattr(t, f) for f, _ in TuneResult._fields_}

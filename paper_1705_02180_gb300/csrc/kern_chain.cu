@@ -1,22 +1,37 @@
 // Resident rMD step kernel for chain replicas, and the frame evaluator.
 //
 // One thread-block cluster of CL CTAs (CL = 1 or 2) owns one replica for a
-// whole launch of n_steps steps. Positions, velocities and int64 fixed-point
-// force partials live in shared memory; the CTAs of a cluster split the force
-// work list between them (the warps of each CTA pull their items from a counter
-// in their own shared memory) and read each other's partials through
-// distributed shared memory. Every step evaluates
-//   bonded terms + non-bonded pairs (32 x 16 half tile pairs, skipped when
-//   their bounding boxes are farther apart than the cutoff; a tile with
-//   itself in one 16-step round)                                   -grad U
+// whole launch of n_steps steps. Positions, velocities and fixed-point force
+// partials live in shared memory; the CTAs of a cluster split the force work
+// between them (the warps of each CTA pull their items from a counter in their
+// own shared memory) and read each other's partials through distributed shared
+// memory. Every step evaluates
+//   bonded terms + non-bonded pairs from a pair list              -grad U
 //   z(X) of Eq. (zrMD) from C_ij of Eq. (Cij) in float-float     collective coordinate
 //   ratchet of Eq. (FrMD) in FP64 (z < z_m: z_m = z, no bias)   bias force
 //   BAOAB update with Philox4x32-10 noise (Eq. Lang)
 // and writes a frame every save_interval steps. Every CTA of a cluster
 // integrates all atoms of the replica with the same total force, so their
-// copies of the state stay identical without being exchanged. All sums that
-// several warps contribute to are fixed point, so results do not depend on
-// which warp or CTA took which work item.
+// copies of the state stay identical without being exchanged.
+//
+// Pair list. Atoms are grouped in blocks of 8 consecutive chain atoms. For each
+// block I the list holds, in ascending order, every atom j of a later block that
+// lies within r_list = r_c + skin of some atom of I, in chunks of 8 (the last one
+// padded with a far-away sentinel slot). A work item is one block against one
+// chunk (64 pairs) on a quarter warp: lane l keeps atom j_l of the chunk and the
+// block's atoms rotate through the lanes, so the i-force accumulators rotate one
+// lane per pair while the j-force stays in place. Pairs inside a block form 28-pair
+// items of their own. The list is rebuilt when a bound on the largest displacement
+// since the last build reaches skin/2, or after rebuild_every steps, so no pair
+// inside r_c is ever missing.
+//
+// Summation. Every pair term s (x_j - x_i) is rounded to an integer multiple of
+// 2^-13 kJ mol^-1 nm^-1 and summed in integers; bonded and bias terms are rounded
+// to 2^-20 units. The shared-memory partials are pairs of 32-bit words (a signed
+// integer part and an unsigned 2^-20 fraction part) added with 32-bit atomics, so
+// every sum is exact and independent of the order of the additions. Results are
+// therefore the same bits whichever warp or CTA takes an item, whatever the list
+// skin or rebuild cadence, and across a checkpoint and resume.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -31,24 +46,30 @@ namespace scps {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kChunk = 32;  // contacts / bonds / angles per work item (one per lane)
+constexpr int kChunk = 32;    // contacts / bonds / angles per work item (one per lane)
 constexpr int kTubeItem = 8;  // contacts per work item of the contact-map tube passes
+constexpr float kPairScale = 8192.0f;     // 2^13: integer units of the pair force terms
+constexpr float kPairEScale = 262144.0f;  // 2^18: integer units of the pair energies (finer:
+                                          // the many small energies near r_c share one sign,
+                                          // so their rounding does not average out)
+constexpr float kPairEMax = 8000.0f;      // larger pair energies take the slow path
 
+// Shared-memory arrays of one CTA. Atom slots: nta real or padding slots plus 8 sentinel
+// slots (a block far from everything) that absorb the padding of list chunks.
 struct Shared {
-    float4* xq;         // (x, y, z, qs)
-    float4* v;          // velocities (w: 1/m)
+    float4* xq;         // (x, y, z, qs), nta + 8
+    float4* v;          // velocities (w: 1/m), nta
     float4* xi;         // noise of the next O half step per atom (sd times Gaussian numbers);
-                        // w: the atom's |F_bias|^2 / m of the step just closed
-    float2* lj;         // (sigma/2, sqrt(24 eps))
-    long long* Fp[2];   // 3 x nta force partials of this CTA, by parity of the evaluated step
-    long long* Gp[2];   // 3 x nta partials of sum_p (C - C0) C'(u) (x_p - x_i) over the native
-                        // contacts (i, p) this CTA evaluated, by parity (the bias gradient
-                        // without its ratchet factor, which is known only once z is complete)
-    float4* blo;        // tile bounding boxes, then half-tile boxes (2 per tile)
-    float4* bhi;
-    uint32_t* tpl;      // tile pairs at least two apart (I << 16 | J), J >= I + 2
+                        // w: the atom's |F_bias|^2 / m of the step just closed. During a list
+                        // rebuild it holds the block boxes and chunk counts instead.
+    float2* lj;         // (sigma/2, sqrt(24 eps)), nta + 8
+    int* FH[2];         // force partials of this CTA by parity of the evaluated step:
+    unsigned* FL[2];    //   integer part and 2^-20 fraction part, 3 x (nta + 8) each
+    int* GH[2];         // partials of sum_p (C - C0) C'(u) (x_p - x_i) over the native
+    unsigned* GL[2];    //   contacts this CTA evaluated (the bias gradient without its
+                        //   ratchet factor, which is known only once z is complete)
     int* flag;          // force-range flag of the current evaluation
-    int nta, nt;
+    int nta, na8;       // atom slots; accumulator stride (nta + 8)
 };
 
 struct Scalars {
@@ -56,6 +77,10 @@ struct Scalars {
     int status;         // replica status (identical in every CTA of a cluster)
     int bias_on;
     int flag[2];        // force-range bits raised during the evaluation of a given parity
+    int n_items;        // pair items in this CTA's item table
+    int n_diag;         // blocks whose inner pairs this CTA evaluates
+    unsigned vmax2[2];  // largest |v1|^2 + |v2|^2 of the update, by parity (float bits)
+    long long pair_slots;  // pairs one evaluation with the current list takes
     long long n_saved;
     double zm, z, factor, epot, T;
     long long red_z[2][32];  // per-warp shares of z (units of 2^-40), by parity
@@ -68,23 +93,22 @@ struct Scalars {
     long long red_d[2][kMaxTubeK];      // this CTA's share of sum_p (C_p - A_kp)^2 (2^-40), by parity
 };
 
-__device__ __forceinline__ Shared carve(void* base, int nta, int ntp_max, int ncon_max) {
+__device__ __forceinline__ Shared carve(void* base, int nta) {
     Shared s;
     char* p = (char*)base;
+    const int na8 = nta + 8;
     s.nta = nta;
-    s.nt = nta / kTile;
-    s.xq = (float4*)p; p += sizeof(float4) * nta;
+    s.na8 = na8;
+    s.xq = (float4*)p; p += sizeof(float4) * na8;
     s.v = (float4*)p; p += sizeof(float4) * nta;
     s.xi = (float4*)p; p += sizeof(float4) * nta;
-    s.blo = (float4*)p; p += sizeof(float4) * 3 * s.nt;
-    s.bhi = (float4*)p; p += sizeof(float4) * 3 * s.nt;
-    s.Fp[0] = (long long*)p; p += sizeof(long long) * 3 * nta;
-    s.Fp[1] = (long long*)p; p += sizeof(long long) * 3 * nta;
-    s.Gp[0] = (long long*)p; p += sizeof(long long) * 3 * nta;
-    s.Gp[1] = (long long*)p; p += sizeof(long long) * 3 * nta;
-    s.lj = (float2*)p; p += sizeof(float2) * nta;
-    const int ntp4 = (ntp_max + 3) & ~3;
-    s.tpl = (uint32_t*)p; p += sizeof(uint32_t) * ntp4;
+    for (int b = 0; b < 2; ++b) {
+        s.FH[b] = (int*)p; p += sizeof(int) * 3 * na8;
+        s.FL[b] = (unsigned*)p; p += sizeof(unsigned) * 3 * na8;
+        s.GH[b] = (int*)p; p += sizeof(int) * 3 * na8;
+        s.GL[b] = (unsigned*)p; p += sizeof(unsigned) * 3 * na8;
+    }
+    s.lj = (float2*)p;
     s.flag = nullptr;
     return s;
 }
@@ -101,7 +125,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// Fixed-point value of a force partial; a non-finite partial or one above
+// Fixed-point value (2^-20 units) of a force term; a non-finite term or one above
 // 1e9 kJ/mol/nm raises the force-range flag (the replica is then frozen).
 __device__ __forceinline__ long long f2fix_checked(float v, int* flag) {
     if (!(fabsf(v) < 262144.0f)) {
@@ -110,197 +134,24 @@ __device__ __forceinline__ long long f2fix_checked(float v, int* flag) {
     return f2fix(v);
 }
 
-__device__ __forceinline__ void add_fix(const Shared& sm, long long* F, int i, float fx, float fy,
-                                        float fz) {
-    const int nta = sm.nta;
-    atomicAdd((unsigned long long*)&F[i], (unsigned long long)f2fix_checked(fx, sm.flag));
-    atomicAdd((unsigned long long*)&F[nta + i], (unsigned long long)f2fix_checked(fy, sm.flag));
-    atomicAdd((unsigned long long*)&F[2 * nta + i], (unsigned long long)f2fix_checked(fz, sm.flag));
+// Adds a 2^-20 fixed-point value to a (integer part, fraction part) accumulator.
+__device__ __forceinline__ void red_fix20(int* H, unsigned* L, int k, long long v) {
+    atomicAdd(&H[k], (int)(v >> 20));
+    atomicAdd(&L[k], (unsigned)(v & 0xfffffll));
 }
 
-// Half of a 32 x 32 tile pair (j slots 16h .. 16h+15) on one warp. Lane l
-// owns atom i = 32 I + l; within each 16-lane half-warp, lane l takes j slot
-// 16h + ((l + t) & 15) at iteration t and the j-force accumulators rotate one
-// lane per iteration, so lane l ends with slot l & 15; the two half-warps'
-// shares of each j are then added with one exchange. NEAR tile pairs
-// (J = I + 1) test exclusions.
-template <int ELEC, bool ENERGY, bool NEAR>
-__device__ __forceinline__ float half_tile(const Shared& sm, long long* F, const TopoDev& tp,
-                                           const PairConst& pc, int I, int J, int h, int lane) {
-    const int i = I * kTile + lane;
-    const float4 xi = sm.xq[i];
-    const float2 li = sm.lj[i];
-    const unsigned long long em = (NEAR && i < tp.n_atoms) ? tp.excl[i] : 0ull;
-    const int g16 = lane & 16, l16 = lane & 15;
-    const int jb = J * kTile + 16 * h;
-    float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
-#pragma unroll 4
-    for (int t = 0; t < 16; ++t) {
-        const int sl = (l16 + t) & 15;
-        const int j = jb + sl;
-        const float4 xj = sm.xq[j];
-        const float2 lj = sm.lj[j];
-        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        bool ok = r2 < pc.rc2;
-        if (NEAR) {
-            const int dj = j - i + kExclWindow;  // in [33, 95]: j - i in [1, 64)
-            if (dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
-        }
-        float e = 0.f;
-        float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
-        s = ok ? s : 0.0f;
-        fix = fmaf(s, dx, fix);
-        fiy = fmaf(s, dy, fiy);
-        fiz = fmaf(s, dz, fiz);
-        fjx = fmaf(-s, dx, fjx);
-        fjy = fmaf(-s, dy, fjy);
-        fjz = fmaf(-s, dz, fjz);
-        if (ENERGY) eacc += ok ? e : 0.0f;
-        const int src = g16 | ((l16 + 1) & 15);
-        fjx = __shfl_sync(kFull, fjx, src);
-        fjy = __shfl_sync(kFull, fjy, src);
-        fjz = __shfl_sync(kFull, fjz, src);
-    }
-    fjx += __shfl_xor_sync(kFull, fjx, 16);
-    fjy += __shfl_xor_sync(kFull, fjy, 16);
-    fjz += __shfl_xor_sync(kFull, fjz, 16);
-    add_fix(sm, F, i, fix, fiy, fiz);
-    if (lane < 16) add_fix(sm, F, jb + lane, fjx, fjy, fjz);
-    return eacc;
+// Adds an integer number of 2^-13 units (the pair terms).
+__device__ __forceinline__ void red_fix13(int* H, unsigned* L, int k, int v) {
+    atomicAdd(&H[k], v >> 13);
+    atomicAdd(&L[k], ((unsigned)v & 0x1fffu) << 7);
 }
 
-// Two quarter items side by side, one per half-warp. A quarter item is 16 i atoms
-// (half a of tile I) against 16 j atoms (half h of tile J), J >= I + 2, so no pair is
-// excluded. Lane l of half-warp g takes i = 32 I_g + 16 a_g + l and, at iteration t,
-// j slot (l + t) & 15 of its j half; the j-force accumulators rotate within the
-// half-warp, so lane l ends with slot l. Items are coded (I << 18 | J << 2 | a << 1 | h);
-// a negative code leaves its half-warp idle (it adds nothing).
-template <int ELEC, bool ENERGY>
-__device__ __forceinline__ float quarter_items(const Shared& sm, long long* F, const PairConst& pc,
-                                               int code_a, int code_b, int lane) {
-    const int code = lane < 16 ? code_a : code_b;
-    const bool valid = code >= 0;
-    const int c = valid ? code : 0;
-    const int g16 = lane & 16, l16 = lane & 15;
-    const int i = (c >> 18) * kTile + 16 * ((c >> 1) & 1) + l16;
-    const int jb = ((c >> 2) & 0xffff) * kTile + 16 * (c & 1);
-    const float4 xi = sm.xq[i];
-    const float2 li = sm.lj[i];
-    const int src = g16 | ((l16 + 1) & 15);
-    float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
-#pragma unroll 4
-    for (int t = 0; t < 16; ++t) {
-        const int j = jb + ((l16 + t) & 15);
-        const float4 xj = sm.xq[j];
-        const float2 lj = sm.lj[j];
-        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const bool ok = valid && r2 < pc.rc2;
-        float e = 0.f;
-        float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
-        s = ok ? s : 0.0f;
-        fix = fmaf(s, dx, fix);
-        fiy = fmaf(s, dy, fiy);
-        fiz = fmaf(s, dz, fiz);
-        fjx = fmaf(-s, dx, fjx);
-        fjy = fmaf(-s, dy, fjy);
-        fjz = fmaf(-s, dz, fjz);
-        if (ENERGY) eacc += ok ? e : 0.0f;
-        fjx = __shfl_sync(kFull, fjx, src);
-        fjy = __shfl_sync(kFull, fjy, src);
-        fjz = __shfl_sync(kFull, fjz, src);
-    }
-    if (valid) {
-        add_fix(sm, F, i, fix, fiy, fiz);
-        add_fix(sm, F, jb + l16, fjx, fjy, fjz);
-    }
-    return eacc;
-}
-
-// The 496 pairs of tile I with itself in 16 iterations of one warp: at
-// iteration k lane l takes the pair (l, (l + k) & 31) (k = 16 on lanes 0..15
-// only), so every pair comes exactly once. The j-force accumulators rotate one
-// lane per iteration; at the end lane l holds atom (l + 17) & 31's, and one
-// exchange brings each to its atom's lane.
-template <int ELEC, bool ENERGY>
-__device__ __forceinline__ float diag_tile(const Shared& sm, long long* F, const TopoDev& tp,
-                                           const PairConst& pc, int I, int lane) {
-    const int i = I * kTile + lane;
-    const float4 xi = sm.xq[i];
-    const float2 li = sm.lj[i];
-    const unsigned long long em = i < tp.n_atoms ? tp.excl[i] : 0ull;
-    float fix = 0.f, fiy = 0.f, fiz = 0.f, fjx = 0.f, fjy = 0.f, fjz = 0.f, eacc = 0.f;
-    const int src = (lane + 1) & 31;
-#pragma unroll 4
-    for (int k = 1; k <= 16; ++k) {
-        const int j = I * kTile + ((lane + k) & 31);
-        const float4 xj = sm.xq[j];
-        const float2 lj = sm.lj[j];
-        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const int dj = j - i + kExclWindow;  // in [1, 63]: |j - i| < 32
-        const bool ok = r2 < pc.rc2 && (k < 16 || lane < 16) && !((em >> dj) & 1ull);
-        float e = 0.f;
-        float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
-        s = ok ? s : 0.0f;
-        fix = fmaf(s, dx, fix);
-        fiy = fmaf(s, dy, fiy);
-        fiz = fmaf(s, dz, fiz);
-        fjx = fmaf(-s, dx, fjx);
-        fjy = fmaf(-s, dy, fjy);
-        fjz = fmaf(-s, dz, fjz);
-        if (ENERGY) eacc += ok ? e : 0.0f;
-        fjx = __shfl_sync(kFull, fjx, src);
-        fjy = __shfl_sync(kFull, fjy, src);
-        fjz = __shfl_sync(kFull, fjz, src);
-    }
-    const int back = (lane + 15) & 31;
-    fjx = __shfl_sync(kFull, fjx, back);
-    fjy = __shfl_sync(kFull, fjy, back);
-    fjz = __shfl_sync(kFull, fjz, back);
-    add_fix(sm, F, i, fix + fjx, fiy + fjy, fiz + fjz);
-    return eacc;
-}
-
-template <bool ENERGY>
-__device__ __forceinline__ float bond_term(const Shared& sm, long long* F, const TopoDev& tp,
-                                           int b) {
-    const int2 ij = tp.bond_ij[b];
-    const float2 par = tp.bond_par[b];
-    const float4 a = sm.xq[ij.x], c = sm.xq[ij.y];
-    const float dx = c.x - a.x, dy = c.y - a.y, dz = c.z - a.z;
-    const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float dr = r - par.x;
-    const float f = par.y * dr / r;
-    add_fix(sm, F, ij.x, f * dx, f * dy, f * dz);
-    add_fix(sm, F, ij.y, -f * dx, -f * dy, -f * dz);
-    return ENERGY ? 0.5f * par.y * dr * dr : 0.0f;
-}
-
-template <bool ENERGY>
-__device__ __forceinline__ float angle_term(const Shared& sm, long long* F, const TopoDev& tp,
-                                            int q) {
-    const int4 ijk = tp.ang_ijk[q];
-    const float2 par = tp.ang_par[q];
-    const float4 a = sm.xq[ijk.x], b = sm.xq[ijk.y], c = sm.xq[ijk.z];
-    const float ux = a.x - b.x, uy = a.y - b.y, uz = a.z - b.z;
-    const float wx = c.x - b.x, wy = c.y - b.y, wz = c.z - b.z;
-    const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
-    const float sn = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
-    const float cs = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
-    const float ru2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    const float rw2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-    const float dth = atan2f(sn, cs) - par.x;
-    // F_i = g (cs u / |u|^2 - w) / sn, F_k = g (cs w / |w|^2 - u) / sn, g = -k dth
-    const float g = -par.y * dth / sn;
-    const float au = cs / ru2, aw = cs / rw2;
-    const float fix = g * fmaf(au, ux, -wx), fiy = g * fmaf(au, uy, -wy), fiz = g * fmaf(au, uz, -wz);
-    const float fkx = g * fmaf(aw, wx, -ux), fky = g * fmaf(aw, wy, -uy), fkz = g * fmaf(aw, wz, -uz);
-    add_fix(sm, F, ijk.x, fix, fiy, fiz);
-    add_fix(sm, F, ijk.z, fkx, fky, fkz);
-    add_fix(sm, F, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
-    return ENERGY ? 0.5f * par.y * dth * dth : 0.0f;
+__device__ __forceinline__ void add_fix(const Shared& sm, int* H, unsigned* L, int i, float fx,
+                                        float fy, float fz) {
+    const int s = sm.na8;
+    red_fix20(H, L, i, f2fix_checked(fx, sm.flag));
+    red_fix20(H, L, s + i, f2fix_checked(fy, sm.flag));
+    red_fix20(H, L, 2 * s + i, f2fix_checked(fz, sm.flag));
 }
 
 // Cluster helpers: CL == 1 degenerates to a plain CTA.
@@ -324,12 +175,269 @@ __device__ __forceinline__ int cta_rank() {
     return (int)cg::this_cluster().block_rank();
 }
 
+// ---------------------------------------------------------------------------
+// Pair items
+// ---------------------------------------------------------------------------
+
+// List slab of this replica or frame (see scps_internal.h for the layout).
+struct ListDev {
+    uint16_t* jl;       // j entries of all blocks
+    uint32_t* items;    // this CTA's item table
+    int nbs;            // blocks of the slab layout (nta / 8)
+};
+
+__device__ __forceinline__ ListDev list_of(unsigned char* slab, int nta, int rank) {
+    ListDev L;
+    L.nbs = nta >> 3;
+    L.jl = (uint16_t*)slab;
+    L.items = (uint32_t*)(slab + list_jl_bytes(L.nbs) +
+                          (long long)rank * ((4 * list_items_cap(L.nbs) + 15) & ~15ll));
+    return L;
+}
+
+// The 64 pairs of one item (block I against the chunk whose atom j this lane holds) on
+// a quarter warp, fast path: integer pair terms summed in 32-bit registers. Returns
+// false (and adds nothing) when some |s| of the quarter warp exceeds pc.s_lim, for
+// which the integer sums of the item could overflow; the caller then takes the slow path.
+template <int ELEC, bool ENERGY, bool NEARX>
+__device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsigned* FL,
+                                               const TopoDev& tp, const PairConst& pc, int I, int j,
+                                               int lane, long long& e18) {
+    const int l8 = lane & 7, q = lane >> 3;
+    const int src = (lane & 24) | ((l8 + 1) & 7);
+    const float4 xj = sm.xq[j];
+    const float2 lj = sm.lj[j];
+    const int i0 = 8 * I;
+    int fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    long long ei = 0;
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int i = i0 + ((l8 + t) & 7);
+        const float4 xi = sm.xq[i];
+        const float2 li = sm.lj[i];
+        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool ok = r2 < pc.rc2;
+        if (NEARX) {  // j - i in [1, 64): a bonded neighbour may be excluded
+            const int dj = j - i + kExclWindow;
+            if (dj < 2 * kExclWindow && i < tp.n_atoms) ok = ok && !((tp.excl[i] >> dj) & 1ull);
+        }
+        float e = 0.f;
+        float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
+        s = ok ? s : 0.0f;
+        bad = bad || !(fabsf(s) <= pc.s_lim);
+        if (ENERGY) bad = bad || (ok && !(fabsf(e) < kPairEMax));
+        const float s13 = s * kPairScale;
+        const int tx = __float2int_rn(s13 * dx), ty = __float2int_rn(s13 * dy),
+                  tz = __float2int_rn(s13 * dz);
+        fix += tx;
+        fiy += ty;
+        fiz += tz;
+        fjx -= tx;
+        fjy -= ty;
+        fjz -= tz;
+        if (ENERGY) ei += ok ? __float2int_rn(e * kPairEScale) : 0;
+        fix = __shfl_sync(kFull, fix, src);
+        fiy = __shfl_sync(kFull, fiy, src);
+        fiz = __shfl_sync(kFull, fiz, src);
+    }
+    if ((__ballot_sync(kFull, bad) >> (8 * q)) & 0xffu) return false;
+    const int s3 = sm.na8, i = i0 + l8;  // after 8 rotations lane l holds block atom l
+    red_fix13(FH, FL, i, fix);
+    red_fix13(FH, FL, s3 + i, fiy);
+    red_fix13(FH, FL, 2 * s3 + i, fiz);
+    red_fix13(FH, FL, j, fjx);
+    red_fix13(FH, FL, s3 + j, fjy);
+    red_fix13(FH, FL, 2 * s3 + j, fjz);
+    if (ENERGY) e18 += ei;
+    return true;
+}
+
+// Slow path of an item: every pair term goes to both atoms in 2^-20 fixed point with
+// the range check (a force beyond 1e9 kJ/mol/nm or a non-finite one freezes the replica).
+template <int ELEC, bool ENERGY>
+__device__ __noinline__ void pair_item_slow(const Shared& sm, int* FH, unsigned* FL,
+                                            const TopoDev& tp, const PairConst& pc, int I, int j,
+                                            int lane, long long& e20) {
+    const int l8 = lane & 7;
+    const float4 xj = sm.xq[j];
+    const float2 lj = sm.lj[j];
+    for (int t = 0; t < 8; ++t) {
+        const int i = 8 * I + ((l8 + t) & 7);
+        const float4 xi = sm.xq[i];
+        const float2 li = sm.lj[i];
+        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool ok = r2 < pc.rc2;
+        const int dj = j - i + kExclWindow;
+        if (dj >= 0 && dj < 2 * kExclWindow && i < tp.n_atoms) ok = ok && !((tp.excl[i] >> dj) & 1ull);
+        if (!ok) continue;
+        float e = 0.f;
+        const float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
+        add_fix(sm, FH, FL, i, s * dx, s * dy, s * dz);
+        add_fix(sm, FH, FL, j, -s * dx, -s * dy, -s * dz);
+        if (ENERGY) e20 += f2fix(e);
+    }
+}
+
+// One batch of four pair items (one per quarter warp) from this CTA's item table.
+template <int ELEC, bool ENERGY>
+__device__ __forceinline__ void pair_batch(const Shared& sm, int* FH, unsigned* FL, const TopoDev& tp,
+                                           const PairConst& pc, const ListDev& L, int n_items,
+                                           int batch, int lane, long long& e18, long long& e20) {
+    const int it = 4 * batch + (lane >> 3);
+    int I = 0, j = sm.nta;  // idle quarter: block 0 against the far sentinel slot (zero terms)
+    bool near = false;
+    if (it < n_items) {
+        const uint32_t d = __ldcg(L.items + it);
+        I = (int)(d >> 17);
+        near = (d >> 16) & 1u;
+        j = (int)__ldcg(L.jl + list_jl_off(L.nbs, I) + 8 * (int)(d & 0xffffu) + (lane & 7));
+    }
+    bool done;
+    if (__any_sync(kFull, near))
+        done = pair_item_fast<ELEC, ENERGY, true>(sm, FH, FL, tp, pc, I, j, lane, e18);
+    else
+        done = pair_item_fast<ELEC, ENERGY, false>(sm, FH, FL, tp, pc, I, j, lane, e18);
+    if (!done) pair_item_slow<ELEC, ENERGY>(sm, FH, FL, tp, pc, I, j, lane, e20);
+}
+
+// The 28 pairs inside block I on a quarter warp: at round k = 1..4 lane l takes the pair
+// (l, (l + k) & 7) (round 4 on lanes 0..3 only), so every pair comes once; the second
+// atom's accumulators rotate one lane per round and return home with one exchange.
+template <int ELEC, bool ENERGY>
+__device__ __forceinline__ void diag_item(const Shared& sm, int* FH, unsigned* FL, const TopoDev& tp,
+                                          const PairConst& pc, int I, int lane, long long& e18,
+                                          long long& e20) {
+    const int l8 = lane & 7, q = lane >> 3;
+    const int src = (lane & 24) | ((l8 + 1) & 7);
+    const int i = 8 * I + l8;
+    const float4 xa = sm.xq[i];
+    const float2 la = sm.lj[i];
+    const unsigned long long em = i < tp.n_atoms ? tp.excl[i] : 0ull;
+    int fax = 0, fay = 0, faz = 0, fbx = 0, fby = 0, fbz = 0;
+    long long ei = 0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const int b = 8 * I + ((l8 + k) & 7);
+        const float4 xb = sm.xq[b];
+        const float2 lb = sm.lj[b];
+        const float dx = xb.x - xa.x, dy = xb.y - xa.y, dz = xb.z - xa.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool ok = r2 < pc.rc2 && (k < 4 || l8 < 4) && !((em >> (b - i + kExclWindow)) & 1ull);
+        float e = 0.f;
+        float s = pair_s<ELEC, ENERGY>(r2, la.x + lb.x, la.y * lb.y, xa.w * xb.w, pc, &e);
+        s = ok ? s : 0.0f;
+        bad = bad || !(fabsf(s) <= pc.s_lim);
+        if (ENERGY) bad = bad || (ok && !(fabsf(e) < kPairEMax));
+        const float s13 = s * kPairScale;
+        const int tx = __float2int_rn(s13 * dx), ty = __float2int_rn(s13 * dy),
+                  tz = __float2int_rn(s13 * dz);
+        fax += tx;
+        fay += ty;
+        faz += tz;
+        fbx -= tx;
+        fby -= ty;
+        fbz -= tz;
+        if (ENERGY) ei += ok ? __float2int_rn(e * kPairEScale) : 0;
+        if (k < 4) {
+            fbx = __shfl_sync(kFull, fbx, src);
+            fby = __shfl_sync(kFull, fby, src);
+            fbz = __shfl_sync(kFull, fbz, src);
+        }
+    }
+    const int home = (lane & 24) | ((l8 + 4) & 7);
+    fbx = __shfl_sync(kFull, fbx, home);
+    fby = __shfl_sync(kFull, fby, home);
+    fbz = __shfl_sync(kFull, fbz, home);
+    const int s3 = sm.na8;
+    if (!((__ballot_sync(kFull, bad) >> (8 * q)) & 0xffu)) {
+        red_fix13(FH, FL, i, fax + fbx);
+        red_fix13(FH, FL, s3 + i, fay + fby);
+        red_fix13(FH, FL, 2 * s3 + i, faz + fbz);
+        if (ENERGY) e18 += ei;
+        return;
+    }
+    for (int k = 1; k <= 4; ++k) {  // slow path (quarter-uniform)
+        const int b = 8 * I + ((l8 + k) & 7);
+        const float4 xb = sm.xq[b];
+        const float2 lb = sm.lj[b];
+        const float dx = xb.x - xa.x, dy = xb.y - xa.y, dz = xb.z - xa.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(r2 < pc.rc2 && (k < 4 || l8 < 4) && !((em >> (b - i + kExclWindow)) & 1ull))) continue;
+        float e = 0.f;
+        const float s = pair_s<ELEC, ENERGY>(r2, la.x + lb.x, la.y * lb.y, xa.w * xb.w, pc, &e);
+        add_fix(sm, FH, FL, i, s * dx, s * dy, s * dz);
+        add_fix(sm, FH, FL, b, -s * dx, -s * dy, -s * dz);
+        if (ENERGY) e20 += f2fix(e);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bonded terms, contacts, noise
+// ---------------------------------------------------------------------------
+
+template <bool ENERGY>
+__device__ __forceinline__ float bond_term(const Shared& sm, int* H, unsigned* L, const TopoDev& tp,
+                                           int b) {
+    const int2 ij = tp.bond_ij[b];
+    const float2 par = tp.bond_par[b];
+    const float4 a = sm.xq[ij.x], c = sm.xq[ij.y];
+    const float dx = c.x - a.x, dy = c.y - a.y, dz = c.z - a.z;
+    const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float dr = r - par.x;
+    const float f = par.y * dr / r;
+    add_fix(sm, H, L, ij.x, f * dx, f * dy, f * dz);
+    add_fix(sm, H, L, ij.y, -f * dx, -f * dy, -f * dz);
+    return ENERGY ? 0.5f * par.y * dr * dr : 0.0f;
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ float angle_term(const Shared& sm, int* H, unsigned* L, const TopoDev& tp,
+                                            int q) {
+    const int4 ijk = tp.ang_ijk[q];
+    const float2 par = tp.ang_par[q];
+    const float4 a = sm.xq[ijk.x], b = sm.xq[ijk.y], c = sm.xq[ijk.z];
+    const float ux = a.x - b.x, uy = a.y - b.y, uz = a.z - b.z;
+    const float wx = c.x - b.x, wy = c.y - b.y, wz = c.z - b.z;
+    const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+    const float sn = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
+    const float cs = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
+    const float ru2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const float rw2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+    const float dth = atan2f(sn, cs) - par.x;
+    // F_i = g (cs u / |u|^2 - w) / sn, F_k = g (cs w / |w|^2 - u) / sn, g = -k dth
+    const float g = -par.y * dth / sn;
+    const float au = cs / ru2, aw = cs / rw2;
+    const float fix = g * fmaf(au, ux, -wx), fiy = g * fmaf(au, uy, -wy), fiz = g * fmaf(au, uz, -wz);
+    const float fkx = g * fmaf(aw, wx, -ux), fky = g * fmaf(aw, wy, -uy), fkz = g * fmaf(aw, wz, -uz);
+    add_fix(sm, H, L, ijk.x, fix, fiy, fiz);
+    add_fix(sm, H, L, ijk.z, fkx, fky, fkz);
+    add_fix(sm, H, L, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
+    return ENERGY ? 0.5f * par.y * dth * dth : 0.0f;
+}
+
+// Adds h (x_p - x_i) to G_i and its negative to G_p (2^-20 fixed point).
+__device__ __forceinline__ void add_grad(const Shared& sm, int* GH, unsigned* GL, int i, int p,
+                                         float h, float dx, float dy, float dz) {
+    const long long gx = f2fix(h * dx), gy = f2fix(h * dy), gz = f2fix(h * dz);
+    const int s = sm.na8;
+    red_fix20(GH, GL, i, gx);
+    red_fix20(GH, GL, s + i, gy);
+    red_fix20(GH, GL, 2 * s + i, gz);
+    red_fix20(GH, GL, p, -gx);
+    red_fix20(GH, GL, s + p, -gy);
+    red_fix20(GH, GL, 2 * s + p, -gz);
+}
+
 // One native contact (i, p): (C - C0)^2 in float-float, returned as a 2^-40
 // fixed-point value. h (x_p - x_i) with h = (C - C0) dC/du goes to G_i and its
 // negative to G_p, so that grad_i (C - C0)^2 = -4 h (x_p - x_i) / r0^2 is
 // -4 G_i / r0^2 summed over the atom's contacts (Eq. zrMD, Eq. Cij).
-__device__ __forceinline__ long long contact_term(const Shared& sm, long long* G, const TopoDev& tp,
-                                                  const RunParams& P, int c) {
+__device__ __forceinline__ long long contact_term(const Shared& sm, int* GH, unsigned* GL,
+                                                  const TopoDev& tp, const RunParams& P, int c) {
     const int2 ij = tp.con_ij[c];
     const float4 a = sm.xq[ij.x], b = sm.xq[ij.y];
     const ff r2 = ff_r2(ff_diff(b.x, a.x), ff_diff(b.y, a.y), ff_diff(b.z, a.z));
@@ -338,15 +446,7 @@ __device__ __forceinline__ long long contact_term(const Shared& sm, long long* G
     const float2 c0 = tp.con_C0[c];
     const ff d = ff_add(C, ff{-c0.x, -c0.y});
     const float h = (d.hi + d.lo) * contact_dC_du(u.hi);
-    const long long gx = f2fix(h * (b.x - a.x)), gy = f2fix(h * (b.y - a.y)),
-                    gz = f2fix(h * (b.z - a.z));
-    const int nta = sm.nta;
-    atomicAdd((unsigned long long*)&G[ij.x], (unsigned long long)gx);
-    atomicAdd((unsigned long long*)&G[nta + ij.x], (unsigned long long)gy);
-    atomicAdd((unsigned long long*)&G[2 * nta + ij.x], (unsigned long long)gz);
-    atomicAdd((unsigned long long*)&G[ij.y], (unsigned long long)(-gx));
-    atomicAdd((unsigned long long*)&G[nta + ij.y], (unsigned long long)(-gy));
-    atomicAdd((unsigned long long*)&G[2 * nta + ij.y], (unsigned long long)(-gz));
+    add_grad(sm, GH, GL, ij.x, ij.y, h, b.x - a.x, b.y - a.y, b.z - a.z);
     return ff2fix40(ff_sqr(d));
 }
 
@@ -366,50 +466,6 @@ __device__ __forceinline__ void noise_chunk(const Shared& sm, const TopoDev& tp,
         sm.xi[i].x = sd * g.x;
         sm.xi[i].y = sd * g.y;
         sm.xi[i].z = sd * g.z;
-    }
-}
-
-// Box of 32 positions of one warp (invalid lanes hold +inf/-inf sentinels):
-// lane 0 writes the tile box, lanes 0 and 16 the two half-tile boxes.
-__device__ __forceinline__ void warp_boxes(const Shared& sm, int t, float4 lo, float4 hi,
-                                           int lane) {
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-        lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, o));
-        lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, o));
-        lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, o));
-        hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, o));
-        hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, o));
-        hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, o));
-    }
-    if (t < sm.nt && (lane & 15) == 0) {
-        sm.blo[sm.nt + 2 * t + (lane >> 4)] = lo;
-        sm.bhi[sm.nt + 2 * t + (lane >> 4)] = hi;
-    }
-    lo.x = fminf(lo.x, __shfl_xor_sync(kFull, lo.x, 16));
-    lo.y = fminf(lo.y, __shfl_xor_sync(kFull, lo.y, 16));
-    lo.z = fminf(lo.z, __shfl_xor_sync(kFull, lo.z, 16));
-    hi.x = fmaxf(hi.x, __shfl_xor_sync(kFull, hi.x, 16));
-    hi.y = fmaxf(hi.y, __shfl_xor_sync(kFull, hi.y, 16));
-    hi.z = fmaxf(hi.z, __shfl_xor_sync(kFull, hi.z, 16));
-    if (t < sm.nt && lane == 0) {
-        sm.blo[t] = lo;
-        sm.bhi[t] = hi;
-    }
-}
-
-// Tile and half-tile boxes of the positions in shared memory (whole CTA).
-__device__ void all_boxes(const Shared& sm, int n) {
-    const int lane = threadIdx.x & 31;
-    for (int base = 0; base < sm.nta; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-        float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
-        if (i < n) {  // i may run past the nta-entry arrays: no load then
-            lo = sm.xq[i];
-            hi = lo;
-        }
-        warp_boxes(sm, (base >> 5) + (threadIdx.x >> 5), lo, hi, lane);
     }
 }
 
@@ -473,7 +529,8 @@ __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, 
 // exchange steps halve the values each lane holds, two more finish the sums, so lane
 // L ends with the dot of contact (L >> 2) & 7. The order of every sum is fixed.
 __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, const TopoDev& tp,
-                                           const RunParams& P, long long* G, int c0, int lane) {
+                                           const RunParams& P, int* GH, unsigned* GL, int c0,
+                                           int lane) {
     const int nq = min(kTubeItem, tp.n_contacts - c0);
     // the contact of lane l (l < nq; clamped elsewhere) is read first, so that its
     // latency overlaps the slice loads
@@ -506,7 +563,7 @@ __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, 
     w1 += __shfl_xor_sync(kFull, w1, 2);
     w1 += __shfl_xor_sync(kFull, w1, 1);
     const float dot = __shfl_sync(kFull, w1, (lane & 7) * 4);
-    // every lane stays to the end (all exchanges below are full-warp); lanes >= nq
+    // every lane stays to the end (all exchanges above are full-warp); lanes >= nq
     // hold a copy of the last contact and add nothing
     const bool live = lane < nq;
     const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
@@ -514,16 +571,7 @@ __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, 
     const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq;
     const float C = contact_C_f32(u);
     const float h = live ? 2.0f * tp.tube_inv_n0 * (C * sc.gam_sum - dot) * contact_dC_du(u) : 0.f;
-    const long long gx = f2fix(h * dx), gy = f2fix(h * dy), gz = f2fix(h * dz);
-    const int nta = sm.nta;
-    if (live) {
-        atomicAdd((unsigned long long*)&G[ij.x], (unsigned long long)gx);
-        atomicAdd((unsigned long long*)&G[nta + ij.x], (unsigned long long)gy);
-        atomicAdd((unsigned long long*)&G[2 * nta + ij.x], (unsigned long long)gz);
-        atomicAdd((unsigned long long*)&G[ij.y], (unsigned long long)(-gx));
-        atomicAdd((unsigned long long*)&G[nta + ij.y], (unsigned long long)(-gy));
-        atomicAdd((unsigned long long*)&G[2 * nta + ij.y], (unsigned long long)(-gz));
-    }
+    if (live) add_grad(sm, GH, GL, ij.x, ij.y, h, dx, dy, dz);
 }
 
 // Tube variables and their ratchets from the summed slice distances (warp 0):
@@ -609,7 +657,8 @@ __device__ void tube_decide(Scalars& sc, const TopoDev& tp, const RunParams& P, 
     }
 }
 
-// Summed fixed-point partials (this CTA + peer) of one atom: force and bias gradient.
+// Summed fixed-point partials (this CTA + peer) of one atom: force and bias gradient,
+// each in 2^-20 units.
 struct AtomSums {
     long long f[3], g[3];
 };
@@ -619,156 +668,302 @@ struct AtomSums {
 template <int CL>
 __device__ __forceinline__ void load_sums(const Shared& sm, int b, int peer, int i, bool bias,
                                           AtomSums& a) {
-    const int nta = sm.nta;
-    const long long* F = sm.Fp[b];
-    const long long* G = sm.Gp[b];
+    const int s = sm.na8;
+    int fh[3], gh[3];
+    unsigned fl[3], gl[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a.f[c] = F[c * nta + i];
-        a.g[c] = bias ? G[c * nta + i] : 0;
+        fh[c] = sm.FH[b][c * s + i];
+        fl[c] = sm.FL[b][c * s + i];
+        gh[c] = bias ? sm.GH[b][c * s + i] : 0;
+        gl[c] = bias ? sm.GL[b][c * s + i] : 0u;
+    }
+    long long lo[3], glo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = (long long)fl[c];
+        glo[c] = (long long)gl[c];
     }
     if (CL == 2) {
-        const long long* pF = rank_ptr<CL>(sm.Fp[b], peer);
-        const long long* pG = rank_ptr<CL>(sm.Gp[b], peer);
-        long long r[3], q[3];
+        const int* pFH = rank_ptr<CL>(sm.FH[b], peer);
+        const unsigned* pFL = rank_ptr<CL>(sm.FL[b], peer);
+        const int* pGH = rank_ptr<CL>(sm.GH[b], peer);
+        const unsigned* pGL = rank_ptr<CL>(sm.GL[b], peer);
+        int rh[3], qh[3];
+        unsigned rl[3], ql[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            r[c] = pF[c * nta + i];
-            q[c] = bias ? pG[c * nta + i] : 0;
+            rh[c] = pFH[c * s + i];
+            rl[c] = pFL[c * s + i];
+            qh[c] = bias ? pGH[c * s + i] : 0;
+            ql[c] = bias ? pGL[c * s + i] : 0u;
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            a.f[c] += r[c];
-            a.g[c] += q[c];
+            fh[c] += rh[c];
+            gh[c] += qh[c];
+            lo[c] += (long long)rl[c];
+            glo[c] += (long long)ql[c];
         }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.f[c] = ((long long)fh[c] << 20) + lo[c];
+        a.g[c] = ((long long)gh[c] << 20) + glo[c];
     }
 }
 
-// Force evaluation of the configuration in shared memory (boxes current) for
-// the evaluated step of parity b. Work items come from the queue of the
-// cluster; this CTA's share goes to Fp[b] and Gp[b]; the ratchet decision is
-// taken by every CTA from the same fixed-point sums. With noise_step >= 0 the
-// CTA also draws the Gaussian numbers of that step's O half step for all atoms
-// (each CTA of a cluster integrates every atom). On return the CTA is
-// synchronised.
+// ---------------------------------------------------------------------------
+// Pair list build
+// ---------------------------------------------------------------------------
+
+// Builds the pair list of the positions in shared memory: the block boxes, then for the
+// blocks I with I % CL == rank (one warp per block) the ascending list of atoms j of
+// later blocks within sqrt(rlist2) of some atom of I, then (after a cluster barrier, so
+// that both CTAs' counts and entries are complete) this CTA's item table. Items are
+// numbered over all blocks, chunks near a block (first j within the exclusion window of
+// the block) first; item k goes to CTA k % CL. Called by every thread of every CTA of
+// the cluster; returns after a cluster barrier (the peer has finished reading this
+// CTA's counts, which share the noise array's space).
+template <int CL>
+__device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, float rlist2,
+                           const ListDev& L) {
+    const int n = tp.n_atoms, nb = (n + 7) >> 3;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int rank = cta_rank<CL>();
+    // scratch in the noise array: boxes (2 nb float4), chunk counts, near-chunk counts
+    // and the two prefix arrays (nb ints each)
+    float4* blo = sm.xi;
+    float4* bhi = sm.xi + nb;
+    int* cnt = (int*)(sm.xi + 2 * nb);
+    int* cntn = cnt + nb;
+    int* pren = cntn + nb;
+    int* pref = pren + nb;
+    __syncthreads();  // warp 0 may still be summing the bias terms held in the noise array
+    for (int I = tid; I < nb; I += blockDim.x) {
+        float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+        float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
+        for (int a = 8 * I; a < min(8 * I + 8, n); ++a) {
+            const float4 x = sm.xq[a];
+            lo.x = fminf(lo.x, x.x);
+            lo.y = fminf(lo.y, x.y);
+            lo.z = fminf(lo.z, x.z);
+            hi.x = fmaxf(hi.x, x.x);
+            hi.y = fmaxf(hi.y, x.y);
+            hi.z = fmaxf(hi.z, x.z);
+        }
+        blo[I] = lo;
+        bhi[I] = hi;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int I = rank + CL * warp; I < nb; I += CL * nw) {
+        const float4 bl = blo[I], bh = bhi[I];
+        const int i0 = 8 * I, ia = min(8, n - i0);
+        uint16_t* out = L.jl + list_jl_off(L.nbs, I);
+        int count = 0, n_near = 0;
+        for (int J0 = I + 1; J0 < nb; J0 += 32) {
+            const int J = J0 + lane;
+            const bool cand = J < nb && box_gap2(bl, bh, blo[J], bhi[J]) < rlist2;
+            unsigned cm = __ballot_sync(kFull, cand);
+            while (cm) {  // four candidate blocks at a time: lane (c, s) tests atom 8 J_c + s
+                int Jc = -1;
+                const int c = lane >> 3;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (cm) {
+                        const int Jk = J0 + __ffs(cm) - 1;
+                        cm &= cm - 1;
+                        if (k == c) Jc = Jk;
+                    }
+                }
+                const int j = Jc >= 0 ? 8 * Jc + (lane & 7) : n;
+                // atoms within sqrt(rlist2) of the block's box, then, four at a time (eight
+                // lanes each, one block atom per lane), the exact test against the atoms
+                float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
+                bool pass = false;
+                if (j < n) {
+                    xj = sm.xq[j];
+                    const float gx = fmaxf(0.f, fmaxf(bl.x - xj.x, xj.x - bh.x));
+                    const float gy = fmaxf(0.f, fmaxf(bl.y - xj.y, xj.y - bh.y));
+                    const float gz = fmaxf(0.f, fmaxf(bl.z - xj.z, xj.z - bh.z));
+                    pass = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlist2;
+                }
+                const unsigned pm = __ballot_sync(kFull, pass);
+                const int np = __popc(pm), rk = __popc(pm & lt);
+                bool hit = false;
+                for (int p0 = 0; p0 < np; p0 += 4) {
+                    const int sv = p0 + (lane >> 3), a = lane & 7;
+                    const int src = sv < np ? (int)__fns(pm, 0, sv + 1) : 0;
+                    const float qx = __shfl_sync(kFull, xj.x, src), qy = __shfl_sync(kFull, xj.y, src),
+                                qz = __shfl_sync(kFull, xj.z, src);
+                    bool h = false;
+                    if (sv < np && a < ia) {
+                        const float4 xa = sm.xq[i0 + a];
+                        const float dx = qx - xa.x, dy = qy - xa.y, dz = qz - xa.z;
+                        h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rlist2;
+                    }
+                    const unsigned hb = __ballot_sync(kFull, h);
+                    if (pass && rk >= p0 && rk < p0 + 4) hit = ((hb >> (8 * (rk - p0))) & 0xffu) != 0u;
+                }
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (hit) out[count + __popc(hm & lt)] = (uint16_t)j;
+                const unsigned nm = __ballot_sync(kFull, hit && j < i0 + 8 + 31);
+                count += __popc(hm);
+                n_near += __popc(nm);
+            }
+        }
+        const int padded = (count + 7) & ~7;
+        if (lane < padded - count) out[count + lane] = (uint16_t)sm.nta;
+        if (lane == 0) {
+            cnt[I] = padded >> 3;
+            cntn[I] = (n_near + 7) >> 3;  // chunks whose first entry is near the block
+        }
+    }
+    __threadfence();  // entries are read back with L2 loads (also by the peer CTA)
+    cluster_barrier<CL>();  // every block's entries and counts are complete
+    if (warp == 0) {  // prefix sums over blocks: near chunks, then the remaining ones
+        int runn = 0, runf = 0;
+        for (int I0 = 0; I0 < nb; I0 += 32) {
+            const int I = I0 + lane;
+            int cn = 0, cf = 0;
+            if (I < nb) {
+                const int owner = I % CL;
+                const int ct = *rank_ptr<CL>(&cnt[I], owner);
+                cn = *rank_ptr<CL>(&cntn[I], owner);
+                cf = ct - cn;
+            }
+            int sn = cn, sf = cf;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yn = __shfl_up_sync(kFull, sn, o), yf = __shfl_up_sync(kFull, sf, o);
+                if (lane >= o) {
+                    sn += yn;
+                    sf += yf;
+                }
+            }
+            if (I < nb) {
+                pren[I] = runn + sn - cn;
+                pref[I] = runf + sf - cf;
+            }
+            runn += __shfl_sync(kFull, sn, 31);
+            runf += __shfl_sync(kFull, sf, 31);
+        }
+        const int total = runn + runf;
+        if (lane == 0) {
+            sc.n_items = (total - rank + CL - 1) / CL;
+            sc.n_diag = (nb - rank + CL - 1) / CL;
+            sc.work_next[0] = 0;
+            sc.work_next[1] = 0;
+            sc.pair_slots = 64ll * total + 28ll * nb;  // pairs evaluated per step with this list
+        }
+        // the total number of near chunks, for the far items' numbering
+        if (lane == 0) pref[nb] = runn;
+    }
+    __syncthreads();
+    const int tot_near = pref[nb];
+    for (int I = warp; I < nb; I += nw) {
+        const int owner = I % CL;
+        const int ct = *rank_ptr<CL>(&cnt[I], owner), cn = *rank_ptr<CL>(&cntn[I], owner);
+        for (int c = lane; c < ct; c += 32) {
+            const int k = c < cn ? pren[I] + c : tot_near + pref[I] + (c - cn);
+            if (k % CL == rank)
+                L.items[k / CL] = ((uint32_t)I << 17) | ((uint32_t)(c < cn) << 16) | (uint32_t)c;
+        }
+    }
+    __threadfence();
+    cluster_barrier<CL>();  // the peer is done with this CTA's counts; items are visible
+}
+
+// ---------------------------------------------------------------------------
+// Force evaluation
+// ---------------------------------------------------------------------------
+
+// Force evaluation of the configuration in shared memory (pair list current) for
+// the evaluated step of parity b. Work items come from the queue of this CTA; its
+// share goes to the parity-b partials; the ratchet decision is taken by every CTA
+// from the same fixed-point sums. With noise_step >= 0 the CTA also draws the
+// Gaussian numbers of that step's O half step for all atoms (each CTA of a cluster
+// integrates every atom). On return the CTA is synchronised.
 template <int ELEC, bool ENERGY, int CL, bool TUBE>
-__device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P, int b,
-                         bool do_ratchet, uint32_t rep_id, long long noise_step) {
+__device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunParams& P,
+                         const ListDev& L, int b, bool do_ratchet, uint32_t rep_id,
+                         long long noise_step) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int nt = tp.n_tiles;
-    long long* F = sm.Fp[b];
-    long long* G = sm.Gp[b];
+    int* FH = sm.FH[b];
+    unsigned* FL = sm.FL[b];
+    int* GH = sm.GH[b];
+    unsigned* GL = sm.GL[b];
     sm.flag = &sc.flag[b];
     if (noise_step >= 0)
         for (int q = warp; q < nt; q += nw) noise_chunk(sm, tp, P, rep_id, noise_step, q, lane);
-    // Work list: the pair items, then contact, bond and angle chunks. Pair items are
-    // the tile pairs at least two tiles apart (far pairs), then each tile with itself,
-    // then the two halves (16 j atoms) of each tile's neighbour. A warp that pulls a
-    // far pair tests its four quarter items (16 x 16 atoms) by their half boxes and
-    // runs the live ones two at a time, one per half-warp; an odd one waits for the
-    // warp's next live quarter, or runs alone once the warp has pulled past the last
-    // far pair. A neighbour half whose box is beyond the cutoff from the i tile's box
-    // is skipped. Item k belongs to CTA k mod CL of the cluster, whose warps pull their
-    // items from a counter in their own shared memory.
-    // Under the contact-map tube bias the contact items are first-pass items of
-    // kTubeItem contacts (loads from the reference maps in L2), interleaved two by two
-    // with the pair items so that their memory latency overlaps arithmetic; the
-    // interleave keeps every pair item on the CTA it has without the bias.
-    const int nfar = nt >= 3 ? (nt - 1) * (nt - 2) / 2 : 0;
-    const int n_pair = nfar + nt + 2 * (nt - 1);
+    const int rank = cta_rank<CL>();
+    // Work list of this CTA: pair batches (four items from its item table each), blocks
+    // with themselves (four per batch), then its shares of the contact, bond and angle
+    // chunks (global chunk g belongs to CTA g % CL). Under the contact-map tube bias the
+    // contact items are first-pass items of kTubeItem contacts (loads from the reference
+    // maps in L2), interleaved one to one with the pair batches so that their memory
+    // latency overlaps arithmetic.
+    const int n_pb = (sc.n_items + 3) >> 2;
+    const int n_db = (sc.n_diag + 3) >> 2;
     const bool tube = TUBE && do_ratchet;  // contact-map tube bias: two work phases
     const int ncon = (P.bias == 1 || P.bias == 5) ? tp.n_contacts : 0;  // frames: z too
-    const int n_citems = tube ? (ncon + kTubeItem - 1) / kTubeItem : (ncon + kChunk - 1) / kChunk;
-    const int m_mix = tube ? (min(n_pair, n_citems) & ~1) : 0;
-    const int e_con = n_pair + n_citems;
-    // one past the list position of the last far pair
-    const int k_far_end = nfar == 0 ? 0
-                          : 1 + (nfar - 1 < m_mix ? 4 * ((nfar - 1) >> 1) + 2 + ((nfar - 1) & 1)
-                                                  : m_mix + (nfar - 1));
-    const int e_bond = e_con + (tp.n_bonds + kChunk - 1) / kChunk;
-    const int e_all = e_bond + (tp.n_angles + kChunk - 1) / kChunk;
+    const int g_con = tube ? (ncon + kTubeItem - 1) / kTubeItem : (ncon + kChunk - 1) / kChunk;
+    const int g_bond = (tp.n_bonds + kChunk - 1) / kChunk;
+    const int g_ang = (tp.n_angles + kChunk - 1) / kChunk;
+    const int n_con = (g_con - rank + CL - 1) / CL;
+    const int n_bond = (g_bond - rank + CL - 1) / CL;
+    const int n_ang = (g_ang - rank + CL - 1) / CL;
+    const int m_mix = tube ? min(n_pb, n_con) : 0;
+    const int e_pair = n_pb + n_con;          // pair batches and contact items end here
+    const int e_diag = e_pair + n_db;
+    const int e_bond = e_diag + n_bond;
+    const int e_all = e_bond + n_ang;
     int* counter = &sc.work_next[b];
-    const int rank = cta_rank<CL>();
-    long long e = 0, zacc = 0;  // fixed point: sums independent of the work order
+    long long e18 = 0, e20 = 0, zacc = 0;  // fixed point: sums independent of the work order
     long long dacc[TUBE ? kMaxTubeK / 32 : 1];  // first-pass slice sums of this lane
 #pragma unroll
     for (int q = 0; q < (TUBE ? kMaxTubeK / 32 : 1); ++q) dacc[q] = 0;
-    int pending = -1;  // code of a live quarter item waiting for a partner (warp-uniform)
     for (;;) {
         int m = 0;
         if (lane == 0) m = atomicAdd(counter, 1);
-        const int k = __shfl_sync(kFull, m, 0) * CL + rank;
-        if (pending >= 0 && k >= k_far_end) {  // no far pair is left for this warp
-            const float ep = quarter_items<ELEC, ENERGY>(sm, F, P.pc, pending, -1, lane);
-            if (ENERGY) e += f2fix(ep);
-            pending = -1;
-        }
+        const int k = __shfl_sync(kFull, m, 0);
         if (k >= e_all) break;
-        int kp = k, kc = -1;  // pair-item index, or contact-item index when kc >= 0
-        if (k < e_con) {
+        if (k < e_pair) {
+            int kp = -1, kc = -1;  // pair batch or contact item
             if (k < 2 * m_mix) {
-                const int base = (k >> 2) * 2, r4 = k & 3;
-                if (r4 < 2)
-                    kc = base + r4;
-                else
-                    kp = base + r4 - 2;
+                if (k & 1) kc = k >> 1; else kp = k >> 1;
             } else {
-                const int j = k - 2 * m_mix;
-                if (j < n_pair - m_mix)
-                    kp = m_mix + j;
-                else
-                    kc = m_mix + j - (n_pair - m_mix);
+                const int r = k - 2 * m_mix;
+                if (r < n_pb - m_mix) kp = m_mix + r; else kc = m_mix + r - (n_pb - m_mix);
             }
-        }
-        if (k < e_con && kc < 0) {
-            float ep = 0.f;
-            if (kp < nfar) {
-                const uint32_t w = sm.tpl[kp];
-                const int I = (int)(w >> 16), J = (int)(w & 0xffff);
-                bool live = false;  // lane q < 4 tests quarter (a, h) = (q >> 1, q & 1)
-                if (lane < 4) {
-                    const int ia = sm.nt + 2 * I + (lane >> 1), jh = sm.nt + 2 * J + (lane & 1);
-                    live = box_gap2(sm.blo[ia], sm.bhi[ia], sm.blo[jh], sm.bhi[jh]) < P.pc.rc2;
+            if (kp >= 0) {
+                pair_batch<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, L, sc.n_items, kp, lane, e18, e20);
+            } else {
+                const int g = kc * CL + rank;
+                if (tube) {
+                    if constexpr (TUBE) tube_pass1(sm, tp, P, g * kTubeItem, lane, dacc);
+                } else {
+                    const int c = g * kChunk + lane;
+                    if (c < ncon) zacc += contact_term(sm, GH, GL, tp, P, c);
                 }
-                unsigned lm = __ballot_sync(kFull, live);
-                while (lm) {
-                    const int code = (I << 18) | (J << 2) | (__ffs(lm) - 1);
-                    lm &= lm - 1;
-                    if (pending < 0) {
-                        pending = code;
-                    } else {  // each pass's energy in fixed point: the pairing is order-dependent
-                        const float eq = quarter_items<ELEC, ENERGY>(sm, F, P.pc, pending, code, lane);
-                        if (ENERGY) e += f2fix(eq);
-                        pending = -1;
-                    }
-                }
-            } else if (kp < nfar + nt) {
-                ep = diag_tile<ELEC, ENERGY>(sm, F, tp, P.pc, kp - nfar, lane);
-            } else {
-                const int r = kp - nfar - nt, I = r >> 1, h = r & 1;
-                const int jh = sm.nt + 2 * (I + 1) + h;  // half boxes follow sm.nt tile boxes
-                if (box_gap2(sm.blo[I], sm.bhi[I], sm.blo[jh], sm.bhi[jh]) < P.pc.rc2)
-                    ep = half_tile<ELEC, ENERGY, true>(sm, F, tp, P.pc, I, I + 1, h, lane);
             }
-            if (ENERGY) e += f2fix(ep);
-        } else if (k < e_con) {
-            if (tube) {
-                if constexpr (TUBE) tube_pass1(sm, tp, P, kc * kTubeItem, lane, dacc);
-            } else {
-                const int c0 = kc * kChunk;
-                if (c0 + lane < ncon) zacc += contact_term(sm, G, tp, P, c0 + lane);
-            }
+        } else if (k < e_diag) {
+            const int d = 4 * (k - e_pair) + (lane >> 3);
+            const int I = d < sc.n_diag ? d * CL + rank : (sm.nta >> 3);
+            diag_item<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, I, lane, e18, e20);
         } else if (k < e_bond) {
-            const int q = (k - e_con) * kChunk + lane;
+            const int q = ((k - e_diag) * CL + rank) * kChunk + lane;
             if (q < tp.n_bonds) {
-                const float eb = bond_term<ENERGY>(sm, F, tp, q);
-                if (ENERGY) e += f2fix(eb);
+                const float eb = bond_term<ENERGY>(sm, FH, FL, tp, q);
+                if (ENERGY) e20 += f2fix(eb);
             }
         } else {
-            const int q = (k - e_bond) * kChunk + lane;
+            const int q = ((k - e_bond) * CL + rank) * kChunk + lane;
             if (q < tp.n_angles) {
-                const float ea = angle_term<ENERGY>(sm, F, tp, q);
-                if (ENERGY) e += f2fix(ea);
+                const float ea = angle_term<ENERGY>(sm, FH, FL, tp, q);
+                if (ENERGY) e20 += f2fix(ea);
             }
         }
     }
@@ -783,7 +978,8 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         }
     }
     zacc = warp_sum_ll(zacc);
-    if (ENERGY) e = warp_sum_ll(e);
+    long long e = 0;
+    if (ENERGY) e = warp_sum_ll((e18 << 2) + e20);  // 2^-18 pair energy units to 2^-20
     if (lane == 0) {
         sc.red_z[b][warp] = zacc;
         sc.red_e[b][warp] = e;
@@ -791,9 +987,11 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     cluster_barrier<CL>();
     // the partials of the other parity were last read (here and in the peer CTA)
     // before this barrier: clear them for the next evaluation meanwhile
-    for (int i = tid; i < 3 * sm.nta; i += blockDim.x) {
-        sm.Fp[b ^ 1][i] = 0;
-        sm.Gp[b ^ 1][i] = 0;
+    for (int i = tid; i < 3 * sm.na8; i += blockDim.x) {
+        sm.FH[b ^ 1][i] = 0;
+        sm.FL[b ^ 1][i] = 0u;
+        sm.GH[b ^ 1][i] = 0;
+        sm.GL[b ^ 1][i] = 0u;
     }
     if (tube)
         for (int i = tid; i < P.tube_k; i += blockDim.x) sc.red_d[b ^ 1][i] = 0;
@@ -839,69 +1037,60 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             if (lane == 0) m = atomicAdd(counter2, 1);
             const int k = __shfl_sync(kFull, m, 0) * CL + rank;
             if (k >= n2) break;
-            tube_pass2(sm, sc, tp, P, G, k * kTubeItem, lane);
+            tube_pass2(sm, sc, tp, P, GH, GL, k * kTubeItem, lane);
         }
         cluster_barrier<CL>();  // the peer reads this CTA's G next
         if (tid == 0) sc.work_next2[b] = 0;
     }
 }
 
-// Tile pairs at least two tiles apart (I << 16 | J, J >= I + 2), row by row: the
-// candidates of the quarter items. Tiles with themselves and with their neighbour are
-// listed by index arithmetic.
-__device__ void tile_pair_table(const Shared& sm, int nt) {
-    const int nfar = nt >= 3 ? (nt - 1) * (nt - 2) / 2 : 0;
-    for (int p = threadIdx.x; p < nfar; p += blockDim.x) {
-        int I = 0, row = nt - 2, q = p;
-        while (q >= row) {
-            q -= row;
-            ++I;
-            --row;
-        }
-        sm.tpl[p] = ((uint32_t)I << 16) | (uint32_t)(I + 2 + q);
-    }
+// Atom slots: real atoms, padding slots and the 8 sentinel slots far apart from
+// everything (no charge, no LJ).
+__device__ __forceinline__ float4 far_slot(int i) {
+    return make_float4(1.0e5f * (float)(i + 1), 0.f, 0.f, 0.f);
 }
 
 }  // namespace
 
 // A CTA pair runs at most kMaxThreadsPair threads per CTA, which leaves 80 registers per
-// thread (fewer spills; 2 % faster than 1024 threads with 64 registers, measured); a lone
-// CTA per replica keeps 1024 threads, so that two 512-thread CTAs can share an SM.
+// thread; a lone CTA per replica keeps 1024 threads, so that two 512-thread CTAs can share
+// an SM.
 template <int ELEC, int CL, bool TUBE>
 __global__ void __launch_bounds__(CL == 2 ? kMaxThreadsPair : 1024, 1)
 k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, StateDev st,
-           RunParams P, int nta, int ntp_max, int ncon_max) {
+           RunParams P, int nta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const RepDev rep = reps[blockIdx.x / CL];  // this launch's replicas, in any order
     const int r = rep.index;
     const int rank = cta_rank<CL>();
     const TopoDev tp = topos[rep.topo];
-    Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
-    const int n = tp.n_atoms, nt = tp.n_tiles;
+    Shared sm = carve(smem_raw, nta);
+    const ListDev L = list_of(P.list_base + rep.list_off, nta, rank);
+    const int n = tp.n_atoms;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nta3 = 3 * nta;
 
-    for (int i = tid; i < nta; i += blockDim.x) {
+    for (int i = tid; i < sm.na8; i += blockDim.x) {
         if (i < n) {
             const float4 x = st.x[rep.atom_off + i];
             sm.xq[i] = make_float4(x.x, x.y, x.z, tp.qs[i]);
             sm.lj[i] = tp.lj[i];
             const float4 v = st.v[rep.atom_off + i];
             sm.v[i] = make_float4(v.x, v.y, v.z, tp.inv_m[i]);
-        } else {  // padding: far apart from everything, no charge, no LJ
-            sm.xq[i] = make_float4(1.0e5f * (float)(i + 1), 0.f, 0.f, 0.f);
+        } else {
+            sm.xq[i] = far_slot(i);
             sm.lj[i] = make_float2(0.f, 0.f);
-            sm.v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < nta) sm.v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    for (int i = tid; i < nta3; i += blockDim.x) {
-        sm.Fp[0][i] = 0;
-        sm.Fp[1][i] = 0;
-        sm.Gp[0][i] = 0;
-        sm.Gp[1][i] = 0;
+    for (int i = tid; i < 3 * sm.na8; i += blockDim.x) {
+        for (int b = 0; b < 2; ++b) {
+            sm.FH[b][i] = 0;
+            sm.FL[b][i] = 0u;
+            sm.GH[b][i] = 0;
+            sm.GL[b][i] = 0u;
+        }
     }
-    tile_pair_table(sm, nt);
     if (tid == 0) {
         sc.zm = st.zm[r];
         sc.z = st.z[r];
@@ -915,6 +1104,8 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         sc.work_next[1] = 0;
         sc.work_next2[0] = 0;
         sc.work_next2[1] = 0;
+        sc.vmax2[0] = 0u;
+        sc.vmax2[1] = 0u;
         sc.sm = st.sm[r];
         sc.wm = st.wm[r];
     }
@@ -923,14 +1114,19 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
         sc.red_d[1][i] = 0;
     }
     long long step = st.step[r];
-    __syncthreads();
-    all_boxes(sm, n);
+    int builds = 0;  // pair-list builds in this launch
     cluster_barrier<CL>();  // every CTA of the cluster is initialised before any remote access
     const int peer = rank ^ 1;
     const float hdt = P.half_dt;
     if (sc.status == 0 && P.n_steps > 0) {
+        build_list<CL>(sm, sc, tp, P.rlist2, L);
+        // displacement bound since the last build and steps since then (identical in every
+        // thread of the cluster: same inputs, same arithmetic)
+        float disp = 0.f;
+        int since = 0;
+        builds = 1;
         // the O half step that follows an evaluation uses the noise of the same step index
-        evaluate<ELEC, false, CL, TUBE>(sm, sc, tp, P, (int)(step & 1), true, rep.rep_id, step);
+        evaluate<ELEC, false, CL, TUBE>(sm, sc, tp, P, L, (int)(step & 1), true, rep.rep_id, step);
         // position of `step` in the save cycle and ring slot of the next frame, kept as
         // counters so that the loop has no 64-bit divisions
         int save_phase = P.save_interval > 0 ? (int)(step % P.save_interval) : -1;
@@ -942,11 +1138,10 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             const bool bias = sc.bias_on;
             const bool save = do_b && save_phase == 0;
             const float kb = -(float)sc.factor * 4.0f * P.inv_r0sq;  // F_bias = kb G
+            float vm2 = 0.f;  // largest |v after B|^2 + |v after O|^2 of this thread's atoms
             for (int base = 0; base < nta; base += blockDim.x) {
                 const int i = base + tid;
-                const bool valid = i < n;
-                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (valid) {
+                if (i < n) {
                     AtomSums a;
                     load_sums<CL>(sm, b, peer, i, bias, a);
                     float4 v = sm.v[i];
@@ -960,7 +1155,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                         fy += by;
                         fz += bz;
                     }
-                    x = sm.xq[i];
+                    float4 x = sm.xq[i];
                     if (do_b) {  // B: closes the evaluated step
                         v.x = fmaf(hdt * im, fx, v.x);
                         v.y = fmaf(hdt * im, fy, v.y);
@@ -976,6 +1171,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                         v.x = fmaf(hdt * im, fx, v.x);
                         v.y = fmaf(hdt * im, fy, v.y);
                         v.z = fmaf(hdt * im, fz, v.z);
+                        const float v1 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
                         x.x = fmaf(hdt, v.x, x.x);
                         x.y = fmaf(hdt, v.y, x.y);
                         x.z = fmaf(hdt, v.z, x.z);
@@ -986,6 +1182,7 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                         x.x = fmaf(hdt, v.x, x.x);
                         x.y = fmaf(hdt, v.y, x.y);
                         x.z = fmaf(hdt, v.z, x.z);
+                        vm2 = fmaxf(vm2, v1 + fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)));
                         if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
                               isfinite(v.y) && isfinite(v.z)))
                             atomicOr(&sc.status, SCPS_FLAG_NONFINITE);
@@ -993,13 +1190,15 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                     }
                     sm.v[i] = v;
                 }
-                if (do_a) {  // boxes of this warp's tile at the new positions
-                    const float4 lo = valid ? x : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
-                    const float4 hi = valid ? x : make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
-                    warp_boxes(sm, (base >> 5) + warp, lo, hi, lane);
-                }
             }
-            if (tid == 0) sc.flag[nb] = 0;
+            if (do_a) {  // largest speed of the step (positive floats order as their bits)
+                const unsigned wm = __reduce_max_sync(kFull, __float_as_uint(vm2));
+                if (lane == 0) atomicMax(&sc.vmax2[b], wm);
+            }
+            if (tid == 0) {
+                sc.flag[nb] = 0;
+                sc.vmax2[nb] = 0u;
+            }
             __syncthreads();
             if (warp == 0 && do_b && bias) {  // atoms in a fixed order, whatever the CTA shape
                 float tsum = 0.f;
@@ -1025,11 +1224,22 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             if (!do_a || sc.status != 0) break;
             ++step;
             if (save_phase >= 0) save_phase = save_phase + 1 == P.save_interval ? 0 : save_phase + 1;
+            // |x_new - x_old| <= dt/2 (|v after B| + |v after O|) <= dt/2 sqrt(2 vmax2) per
+            // atom; a pair inside r_c now was inside r_c + 2 disp at the build, so the list
+            // stays complete while 2 disp < skin (a 1 % margin covers the FP32 rounding)
+            disp += hdt * sqrtf(2.0f * __uint_as_float(sc.vmax2[b]));
+            ++since;
+            if (disp >= 0.99f * P.skin_half || (P.rebuild_every > 0 && since >= P.rebuild_every)) {
+                build_list<CL>(sm, sc, tp, P.rlist2, L);
+                disp = 0.f;
+                since = 0;
+                ++builds;
+            }
             const bool save_next = save_phase == 0;
             if (save_next)
-                evaluate<ELEC, true, CL, TUBE>(sm, sc, tp, P, nb, true, rep.rep_id, step);
+                evaluate<ELEC, true, CL, TUBE>(sm, sc, tp, P, L, nb, true, rep.rep_id, step);
             else
-                evaluate<ELEC, false, CL, TUBE>(sm, sc, tp, P, nb, true, rep.rep_id, step);
+                evaluate<ELEC, false, CL, TUBE>(sm, sc, tp, P, L, nb, true, rep.rep_id, step);
             if (sc.status != 0) break;  // force out of range: frozen before the update
         }
     }
@@ -1051,42 +1261,46 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
             st.status[r] = sc.status;
             st.step[r] = step;
             st.n_saved[r] = sc.n_saved;
+            if (st.pair_slots && sc.status == 0 && P.n_steps > 0) st.pair_slots[r] = sc.pair_slots;
+            if (st.list_builds) st.list_builds[r] = builds;
         }
     }
     cluster_barrier<CL>();  // no CTA leaves while its shared memory may still be read
 }
 
 // Energy, forces and z of n_frames configurations (no bias, no state); one cluster of CL
-// CTAs per frame. With CL = 2 the work list is split between the two CTAs as in the
-// resident kernel and each CTA writes half of the atoms' forces, summing its own and the
-// peer's fixed-point partials (the same integers as with one CTA).
+// CTAs per frame, each cluster with its own list slab. With CL = 2 the work is split
+// between the two CTAs as in the resident kernel and each CTA writes half of the atoms'
+// forces, summing its own and the peer's fixed-point partials (the same integers as with
+// one CTA).
 template <int ELEC, int CL>
 __global__ void __launch_bounds__(1024, 1)
 k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
-              double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta,
-              int ntp_max, int ncon_max) {
+              double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const TopoDev tp = *topo_ptr;
-    Shared sm = carve(smem_raw, nta, ntp_max, ncon_max);
-    const int n = tp.n_atoms, nt = tp.n_tiles;
+    Shared sm = carve(smem_raw, nta);
+    const int n = tp.n_atoms;
     const long long f = blockIdx.x / CL;
     const int rank = cta_rank<CL>();
+    const ListDev L = list_of(P.list_base + (blockIdx.x / CL) * P.list_slab, nta, rank);
     const float* xf = X + f * n * 3;
-    for (int i = threadIdx.x; i < nta; i += blockDim.x) {
+    for (int i = threadIdx.x; i < sm.na8; i += blockDim.x) {
         if (i < n) {
             sm.xq[i] = make_float4(xf[3 * i], xf[3 * i + 1], xf[3 * i + 2], tp.qs[i]);
             sm.lj[i] = tp.lj[i];
         } else {
-            sm.xq[i] = make_float4(1.0e5f * (float)(i + 1), 0.f, 0.f, 0.f);
+            sm.xq[i] = far_slot(i);
             sm.lj[i] = make_float2(0.f, 0.f);
         }
     }
-    for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) {
-        sm.Fp[0][i] = 0;
-        sm.Gp[0][i] = 0;
+    for (int i = threadIdx.x; i < 3 * sm.na8; i += blockDim.x) {
+        sm.FH[0][i] = 0;
+        sm.FL[0][i] = 0u;
+        sm.GH[0][i] = 0;
+        sm.GL[0][i] = 0u;
     }
-    tile_pair_table(sm, nt);
     if (threadIdx.x == 0) {
         sc.zm = 0.0;
         sc.z = 0.0;
@@ -1094,23 +1308,29 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
         sc.flag[0] = 0;
         sc.work_next[0] = 0;
     }
-    __syncthreads();
-    all_boxes(sm, n);
     cluster_barrier<CL>();  // every CTA of the cluster is initialised before any remote access
-    evaluate<ELEC, true, CL, false>(sm, sc, tp, P, 0, false, 0u, -1);
+    build_list<CL>(sm, sc, tp, P.rlist2, L);
+    evaluate<ELEC, true, CL, false>(sm, sc, tp, P, L, 0, false, 0u, -1);
     if (F) {  // evaluate ends with a cluster barrier: every partial is complete
         float* ff_out = F + f * n * 3;
-        const long long* Fo = rank_ptr<CL>(sm.Fp[0], rank ^ 1);
+        const int s = sm.na8;
+        const int* oH = rank_ptr<CL>(sm.FH[0], rank ^ 1);
+        const unsigned* oL = rank_ptr<CL>(sm.FL[0], rank ^ 1);
         for (int i = threadIdx.x + rank * blockDim.x; i < n; i += CL * blockDim.x) {
-            long long fx = sm.Fp[0][i], fy = sm.Fp[0][nta + i], fz = sm.Fp[0][2 * nta + i];
-            if (CL == 2) {
-                fx += Fo[i];
-                fy += Fo[nta + i];
-                fz += Fo[2 * nta + i];
+            float o[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                int h = sm.FH[0][c * s + i];
+                long long l = (long long)sm.FL[0][c * s + i];
+                if (CL == 2) {
+                    h += oH[c * s + i];
+                    l += (long long)oL[c * s + i];
+                }
+                o[c] = fix2f(((long long)h << 20) + l);
             }
-            ff_out[3 * i] = fix2f(fx);
-            ff_out[3 * i + 1] = fix2f(fy);
-            ff_out[3 * i + 2] = fix2f(fz);
+            ff_out[3 * i] = o[0];
+            ff_out[3 * i + 1] = o[1];
+            ff_out[3 * i + 2] = o[2];
         }
     }
     if (threadIdx.x == 0 && rank == 0) {
@@ -1120,13 +1340,13 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
     cluster_barrier<CL>();  // no CTA leaves while its shared memory may still be read
 }
 
-// Shared-memory bytes of the resident kernel for tiles of nta atoms.
-size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max) {
-    const int nt = nta / kTile;
-    const size_t ntp4 = (size_t)((ntp_max + 3) & ~3);
-    (void)ncon_max;  // contacts live in the topology (global memory)
-    return sizeof(float4) * nta * 3 + sizeof(float4) * 6 * nt + sizeof(long long) * 12 * nta +
-           sizeof(float2) * nta + sizeof(uint32_t) * ntp4;
+// Shared-memory bytes of the resident kernels for nta atom slots (plus the 8 sentinel
+// slots): positions, velocities, noise, LJ parameters and the two parities of force and
+// bias-gradient partials (integer and fraction words).
+size_t resident_smem_bytes(int nta) {
+    const size_t na8 = (size_t)nta + 8;
+    return sizeof(float4) * (na8 + 2 * (size_t)nta) + sizeof(float2) * na8 +
+           2 * 4 * 3 * sizeof(int) * na8;
 }
 
 // Dynamic shared memory a resident or frame-evaluation CTA may request on the current
@@ -1152,9 +1372,8 @@ size_t resident_smem_limit() {
 
 template <int ELEC, int CL, bool TUBE>
 static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, const StateDev& st,
-                                     const RunParams& P, int nta, int ntp_max, int ncon_max,
-                                     int threads, cudaStream_t stream) {
-    const size_t smem = resident_smem_bytes(nta, ntp_max, ncon_max);
+                                     const RunParams& P, int nta, int threads, cudaStream_t stream) {
+    const size_t smem = resident_smem_bytes(nta);
     auto kern = k_resident<ELEC, CL, TUBE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1170,45 +1389,43 @@ static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta, ntp_max, ncon_max);
+    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <int CL>
 static cudaError_t launch_resident_cl(int elec, const TopoDev* topos, const RepDev* reps,
-                                      const StateDev& st, const RunParams& P, int nta, int ntp_max,
-                                      int ncon_max, int threads, cudaStream_t stream) {
+                                      const StateDev& st, const RunParams& P, int nta, int threads,
+                                      cudaStream_t stream) {
     if (P.bias == 5) {  // contact-map tube bias: its own instantiation
         switch (elec) {
-            case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-            case ELEC_RF: return launch_resident_t<ELEC_RF, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-            case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-            default: return launch_resident_t<ELEC_NONE, CL, true>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+            case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL, true>(topos, reps, st, P, nta, threads, stream);
+            case ELEC_RF: return launch_resident_t<ELEC_RF, CL, true>(topos, reps, st, P, nta, threads, stream);
+            case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL, true>(topos, reps, st, P, nta, threads, stream);
+            default: return launch_resident_t<ELEC_NONE, CL, true>(topos, reps, st, P, nta, threads, stream);
         }
     }
     switch (elec) {
-        case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-        case ELEC_RF: return launch_resident_t<ELEC_RF, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-        case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-        default: return launch_resident_t<ELEC_NONE, CL, false>(topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+        case ELEC_DDIEL: return launch_resident_t<ELEC_DDIEL, CL, false>(topos, reps, st, P, nta, threads, stream);
+        case ELEC_RF: return launch_resident_t<ELEC_RF, CL, false>(topos, reps, st, P, nta, threads, stream);
+        case ELEC_PLAIN: return launch_resident_t<ELEC_PLAIN, CL, false>(topos, reps, st, P, nta, threads, stream);
+        default: return launch_resident_t<ELEC_NONE, CL, false>(topos, reps, st, P, nta, threads, stream);
     }
 }
 
 cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const RepDev* reps,
-                            const StateDev& st, const RunParams& P, int nta, int ntp_max,
-                            int ncon_max, int threads, cudaStream_t stream) {
-    if (cluster == 2)
-        return launch_resident_cl<2>(elec, topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
-    return launch_resident_cl<1>(elec, topos, reps, st, P, nta, ntp_max, ncon_max, threads, stream);
+                            const StateDev& st, const RunParams& P, int nta, int threads,
+                            cudaStream_t stream) {
+    if (cluster == 2) return launch_resident_cl<2>(elec, topos, reps, st, P, nta, threads, stream);
+    return launch_resident_cl<1>(elec, topos, reps, st, P, nta, threads, stream);
 }
 
 template <int ELEC>
 static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const float* X,
                                  double* U, float* F, double* Z, long long n_frames, int nta,
-                                 int ntp_max, int ncon_max, int threads, int cl,
-                                 cudaStream_t stream) {
-    const size_t smem = resident_smem_bytes(nta, ntp_max, ncon_max);
+                                 int threads, int cl, cudaStream_t stream) {
+    const size_t smem = resident_smem_bytes(nta);
     auto kern = cl == 2 ? k_eval_frames<ELEC, 2> : k_eval_frames<ELEC, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1224,19 +1441,19 @@ static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, topo, P, X, U, F, Z, nta, ntp_max, ncon_max);
+    e = cudaLaunchKernelEx(&cfg, kern, topo, P, X, U, F, Z, nta);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
-                        double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
-                        int ncon_max, int threads, int cl, cudaStream_t stream) {
+                        double* U, float* F, double* Z, long long n_frames, int nta, int threads,
+                        int cl, cudaStream_t stream) {
     switch (elec) {
-        case ELEC_DDIEL: return launch_eval_t<ELEC_DDIEL>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
-        case ELEC_RF: return launch_eval_t<ELEC_RF>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
-        case ELEC_PLAIN: return launch_eval_t<ELEC_PLAIN>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
-        default: return launch_eval_t<ELEC_NONE>(topo, P, X, U, F, Z, n_frames, nta, ntp_max, ncon_max, threads, cl, stream);
+        case ELEC_DDIEL: return launch_eval_t<ELEC_DDIEL>(topo, P, X, U, F, Z, n_frames, nta, threads, cl, stream);
+        case ELEC_RF: return launch_eval_t<ELEC_RF>(topo, P, X, U, F, Z, n_frames, nta, threads, cl, stream);
+        case ELEC_PLAIN: return launch_eval_t<ELEC_PLAIN>(topo, P, X, U, F, Z, n_frames, nta, threads, cl, stream);
+        default: return launch_eval_t<ELEC_NONE>(topo, P, X, U, F, Z, n_frames, nta, threads, cl, stream);
     }
 }
 

@@ -18,16 +18,16 @@
 #include "scps_internal.h"
 
 namespace scps {
-size_t resident_smem_bytes(int nta, int ntp_max, int ncon_max);
+size_t resident_smem_bytes(int nta);
 size_t resident_smem_limit();
 size_t box_chain_smem_limit();
 size_t box_chain_smem(int n_chain, int n_contacts);
 cudaError_t launch_resident(int elec, int cluster, const TopoDev* topos, const RepDev* reps,
-                            const StateDev& st, const RunParams& P, int nta, int ntp_max,
-                            int ncon_max, int threads, cudaStream_t stream);
+                            const StateDev& st, const RunParams& P, int nta, int threads,
+                            cudaStream_t stream);
 cudaError_t launch_eval(int elec, const TopoDev* topo, const RunParams& P, const float* X,
-                        double* U, float* F, double* Z, long long n_frames, int nta, int ntp_max,
-                        int ncon_max, int threads, int cl, cudaStream_t stream);
+                        double* U, float* F, double* Z, long long n_frames, int nta, int threads,
+                        int cl, cudaStream_t stream);
 cudaError_t launch_path_average_2d(const StateDev& st, int max_frames, int K, const int* sel,
                                    int n_sel, double2* out, cudaStream_t stream);
 cudaError_t launch_path_average_contacts(const StateDev& st, const int2* con_ij, int nc, int n,
@@ -81,6 +81,8 @@ int fail(int code, const char* fmt, ...) {
     } while (0)
 
 constexpr double kCoulombF = 138.935458;  // kJ mol^-1 nm e^-2
+constexpr double kDefaultChainSkin = 0.08;  // nm: pair-list buffer of the chain kernels
+constexpr long long kEvalFramesPerLaunch = 1024;  // frame clusters per evaluation launch
 
 struct TopoHost {
     int n = 0, ncon = 0;
@@ -100,7 +102,15 @@ struct scps_system {
     std::vector<uint32_t> rep_id;
     std::vector<long long> host_step;
     long long n_atoms_total = 0, n_frame_atoms = 0;
-    int max_atoms = 0, nta = 0, ntp_max = 0, ncon_max = 0;
+    int max_atoms = 0, nta = 0, ncon_max = 0;
+    // pair lists of the resident chain kernels: one slab per replica, and one per frame
+    // cluster of the frame evaluation (grown on demand, at most kEvalFramesPerLaunch)
+    unsigned char* d_lists = nullptr;
+    long long list_slab = 0;
+    unsigned char* d_eval_lists = nullptr;
+    long long eval_frames_cap = 0, eval_slab = 0;
+    double list_skin = 0.0;          // r_list - r_c of the chain pair lists
+    long long last_launch_steps = 0; // steps of the latest resident launch
     TopoDev* d_topos = nullptr;
     RepDev* d_reps = nullptr;
     uint32_t* d_rep_ids = nullptr;
@@ -116,7 +126,7 @@ struct scps_system {
     // resident form: one launch per group (groups after the first run on forked streams)
     struct Group {
         RepDev* d_reps = nullptr;  // this group's replicas (owned by `allocs`)
-        int count = 0, nta = 0, ntp_max = 0, cluster = 1, threads = 1024;
+        int count = 0, nta = 0, cluster = 1, threads = 1024;
     };
     std::vector<Group> groups;
     int plan = 0;  // 0: one launch, replicas by decreasing size; 1: one launch per size class
@@ -344,14 +354,13 @@ int set_groups(scps_system* s, int plan, int cluster, int threads) {
         int na = 0;
         for (int r : m) na = std::max(na, s->topos[s->rep_topo[r]].n);
         g.nta = plan == 0 ? s->nta : tile_atoms(na);
-        const int nt = g.nta / kTile;
-        g.ntp_max = nt * (nt + 1) / 2;
         g.cluster = cluster;
         g.threads = threads;
         std::vector<RepDev> reps(m.size());
         for (size_t k = 0; k < m.size(); ++k) {
             const int r = m[k];
-            reps[k] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r};
+            reps[k] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r,
+                             (long long)r * s->list_slab};
         }
         SCPS_CU(s->upload(&g.d_reps, reps));
         groups.push_back(g);
@@ -394,7 +403,7 @@ cudaError_t launch_groups(scps_system* s, const RunParams& P0, long long n_steps
         P.n_replicas = g.count;
         cudaStream_t st = k == 0 ? cs : s->fork_streams[k - 1];
         cudaError_t e = launch_resident(s->d.elec, g.cluster, s->d_topos, g.d_reps, s->st, P, g.nta,
-                                        g.ntp_max, s->ncon_max, g.threads, st);
+                                        g.threads, st);
         if (e != cudaSuccess) return e;
     }
     for (size_t k = 1; k < G; ++k) {
@@ -403,6 +412,15 @@ cudaError_t launch_groups(scps_system* s, const RunParams& P0, long long n_steps
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// List radius of the resident chain kernels (forces do not depend on it: the skin only
+// trades pairs per step against list rebuilds).
+void set_skin(scps_system* s, double skin) {
+    const double rc = s->base.pc.rc > 0.f ? (double)s->base.pc.rc : 1.0;
+    s->list_skin = skin;
+    s->base.rlist2 = (float)((rc + skin) * (rc + skin));
+    s->base.skin_half = (float)(0.5 * skin);
 }
 
 }  // namespace
@@ -535,6 +553,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         ALLOC(s->d_reps, R);
         ALLOC(s->plain_f, (size_t)6 * s->max_atoms + 16384 + 64);
         ALLOC(s->plain_d, 8);
+        ALLOC(st.pair_slots, R);
+        ALLOC(st.list_builds, R);
     } else {
         ALLOC(st.xy, R);
         ALLOC(st.sm, R);
@@ -547,16 +567,21 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         cudaMemcpy(s->d_rep_ids, s->rep_id.data(), sizeof(uint32_t) * R, cudaMemcpyHostToDevice);
     }
     if (d->model == SCPS_MODEL_CHAIN) {
+        s->nta = ((s->max_atoms + kTile - 1) / kTile) * kTile;
+        if (!s->is_box && d->exec == SCPS_EXEC_RESIDENT) {  // pair-list slabs
+            s->list_slab = list_slab_bytes(s->nta);
+            cudaError_t e_ = s->alloc(&s->d_lists, (size_t)R * (size_t)s->list_slab);
+            if (e_ != cudaSuccess)
+                return bail(fail(SCPS_ERR_CUDA, "cudaMalloc of the pair lists: %s", cudaGetErrorString(e_)));
+        }
         std::vector<RepDev> reps(R);
         for (int r = 0; r < R; ++r)
-            reps[r] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r};
+            reps[r] = RepDev{s->rep_topo[r], s->atom_off[r], s->frame_off[r], s->rep_id[r], r,
+                             (long long)r * s->list_slab};
         if (cudaMemcpy(s->d_reps, reps.data(), sizeof(RepDev) * R, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(SCPS_ERR_CUDA, "upload of the replica table failed"));
         rc = sync_topos(s);
         if (rc) return bail(rc);
-        s->nta = ((s->max_atoms + kTile - 1) / kTile) * kTile;
-        const int nt = s->nta / kTile;
-        s->ntp_max = nt * (nt + 1) / 2;
         int n_sm = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
         // a 2-CTA cluster per replica when the replicas alone leave SMs idle
@@ -568,7 +593,7 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         if (s->cluster == 2 && !d->threads) s->threads = std::min(s->threads, kMaxThreadsPair);
         s->steps_per_graph = d->steps_per_graph > 0 ? d->steps_per_graph : 1000;
         if (!s->is_box && d->exec == SCPS_EXEC_RESIDENT) {
-            const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, 0);
+            const size_t smem = resident_smem_bytes(s->nta);
             if (smem > resident_smem_limit())
                 return bail(fail(SCPS_ERR_UNSUPPORTED,
                                  "%d atoms need %zu B of shared memory per CTA, above the limit; "
@@ -671,6 +696,14 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     const double krf = (d->eps_rf - 1.0) / ((2.0 * d->eps_rf + 1.0) * rcut * rcut * rcut);
     P.pc.krf = (float)krf;
     P.pc.crf = (float)(1.0 / rcut + krf * rcut * rcut);
+    // the 2^-13 pair terms of one item (8 per accumulator) stay below 2^31 while
+    // |s| r_c 2^13 8 < 2^31; larger |s| take the exact slow path
+    P.pc.s_lim = (float)(32000.0 / rcut);
+    // pair list of the resident chain kernels (the periodic box keeps its own)
+    const double skin = d->skin > 0.0 ? d->skin : (s->is_box ? 0.15 : kDefaultChainSkin);
+    P.list_base = s->d_lists;
+    set_skin(s, skin);
+    P.rebuild_every = s->is_box ? 0 : std::max(d->rebuild_every, 0);
     *out = s;
     return SCPS_OK;
 }
@@ -684,6 +717,7 @@ int scps_destroy_system(scps_system* s) {
     for (auto st : s->fork_streams) cudaStreamDestroy(st);
     for (auto ev : s->fork_events) cudaEventDestroy(ev);
     for (void* p : s->allocs) cudaFree(p);
+    if (s->d_eval_lists) cudaFree(s->d_eval_lists);
     delete s;
     return SCPS_OK;
 }
@@ -853,7 +887,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
                             s->box.n_chain, ncon_max);
             SCPS_CU(box_prepare(s->box, ncon_max));
         } else {
-            const size_t smem = resident_smem_bytes(s->nta, s->ntp_max, ncon_max);
+            const size_t smem = resident_smem_bytes(s->nta);
             if (s->d.exec == SCPS_EXEC_RESIDENT && smem > resident_smem_limit())
                 return fail(SCPS_ERR_UNSUPPORTED, "shared memory %zu B exceeds the per-CTA limit", smem);
         }
@@ -961,6 +995,7 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
             SCPS_CU(launch_groups(s, P, rem, cs));
         }
         launches = (full + (rem > 0)) * (long long)s->groups.size();
+        s->last_launch_steps = rem > 0 ? rem : chunk;
     }
     for (int r = 0; r < R; ++r) s->host_step[r] += n_steps;
     s->info.graph_nodes_last_call = launches;
@@ -990,17 +1025,44 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
     }
     const TopoHost& th = s->topos[topo];
     const int nta = ((th.n + kTile - 1) / kTile) * kTile;
-    const int nt = nta / kTile;
     RunParams P = s->base;
     if (!z) P.bias = 0;
+    P.rlist2 = P.pc.rc2;  // one list per frame: no skin needed
+    // list slabs: one per frame cluster of a launch (grown on demand; the previous
+    // buffer is freed once no enqueued work can still read it)
+    const long long per_launch = std::min<long long>(n_frames, kEvalFramesPerLaunch);
+    const long long slab = list_slab_bytes(nta);
+    if (per_launch > s->eval_frames_cap || slab > s->eval_slab) {
+        const long long cap = std::max(per_launch, s->eval_frames_cap);
+        const long long sl = std::max(slab, s->eval_slab);
+        SCPS_CU(cudaDeviceSynchronize());
+        if (s->d_eval_lists) {
+            cudaFree(s->d_eval_lists);
+            s->bytes -= (size_t)(s->eval_frames_cap * s->eval_slab);
+            s->d_eval_lists = nullptr;
+        }
+        s->eval_frames_cap = 0;
+        s->eval_slab = 0;
+        SCPS_CU(cudaMalloc(&s->d_eval_lists, (size_t)(cap * sl)));
+        s->eval_frames_cap = cap;
+        s->eval_slab = sl;
+        s->bytes += (size_t)(cap * sl);
+    }
+    P.list_base = s->d_eval_lists;
+    P.list_slab = s->eval_slab;
     // few frames (a checkpoint segment): a 2-CTA cluster per frame, 1024 threads per CTA,
     // so that the frames spread over the SMs; many frames: one CTA each
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
-    const int cl = 2 * n_frames <= n_sm ? 2 : 1;
-    const int threads = n_frames * cl <= n_sm ? 1024 : auto_threads(nta);
-    SCPS_CU(launch_eval(s->d.elec, s->d_topos + topo, P, X, U, F, z, n_frames, nta, nt * (nt + 1) / 2,
-                        th.ncon, threads, cl, (cudaStream_t)stream));
+    const int n3 = 3 * th.n;
+    for (long long f0 = 0; f0 < n_frames; f0 += per_launch) {
+        const long long nf = std::min(per_launch, n_frames - f0);
+        const int cl = 2 * nf <= n_sm ? 2 : 1;
+        const int threads = nf * cl <= n_sm ? 1024 : auto_threads(nta);
+        SCPS_CU(launch_eval(s->d.elec, s->d_topos + topo, P, X + f0 * n3, U + f0,
+                            F ? F + f0 * n3 : nullptr, z ? z + f0 : nullptr, nf, nta, threads, cl,
+                            (cudaStream_t)stream));
+    }
     return SCPS_OK;
 }
 
@@ -1236,6 +1298,24 @@ int scps_get_info(const scps_system* s, scps_info* info) {
     info->plan = s->plan;
     info->kernels_per_step_call = 1;
     info->device_bytes = s->bytes;
+    info->pair_checks_per_step = 0;
+    info->list_skin = s->list_skin;
+    info->steps_per_list_build = 0.0;
+    if (s->st.pair_slots && !s->is_box) {  // summed over replicas, from the lists each built last
+        std::vector<long long> ps(s->d.n_replicas);
+        std::vector<int> nb(s->d.n_replicas);
+        SCPS_CU(cudaMemcpy(ps.data(), s->st.pair_slots, sizeof(long long) * ps.size(),
+                           cudaMemcpyDeviceToHost));
+        SCPS_CU(cudaMemcpy(nb.data(), s->st.list_builds, sizeof(int) * nb.size(),
+                           cudaMemcpyDeviceToHost));
+        double builds = 0.0;
+        for (size_t r = 0; r < ps.size(); ++r) {
+            info->pair_checks_per_step += ps[r];
+            builds += nb[r];
+        }
+        if (builds > 0.0 && s->last_launch_steps > 0)
+            info->steps_per_list_build = (double)s->last_launch_steps * (double)ps.size() / builds;
+    }
     return SCPS_OK;
 }
 
@@ -1310,11 +1390,12 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
                       std::to_string(s->bias_kind);
     for (auto& kv : sizes) key += "|" + std::to_string(kv.first) + "x" + std::to_string(kv.second);
     static std::mutex mu;
-    static std::map<std::string, std::vector<int>> cache;  // plan, cluster, threads
+    static std::map<std::string, std::vector<int>> cache;  // plan, cluster, threads, skin (pm)
     scps_tune_result res{};
     res.plan = s->plan;
     res.cluster_size = s->cluster;
     res.threads = s->threads;
+    res.skin = s->list_skin;
     if (use_cache) {
         std::vector<int> hit;
         {
@@ -1325,9 +1406,12 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
         if (!hit.empty()) {
             int rc = set_groups(s, hit[0], hit[1], hit[2]);
             if (rc) return rc;
+            set_skin(s, 1e-3 * hit[3]);
+            drop_graphs(s);
             res.plan = hit[0];
             res.cluster_size = hit[1];
             res.threads = hit[2];
+            res.skin = s->list_skin;
             res.from_cache = 1;
             if (out) *out = res;
             return SCPS_OK;
@@ -1389,35 +1473,42 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
     double best = 1e300;
     std::vector<int> best_c = cands[0];
     int timed = 0;
+    // one short untimed run (first-launch set-up), then the timed probe; the state is
+    // restored after each. Returns the time per step in us, or a negative value when the
+    // launch was refused (the candidate is skipped); a failed restore is fatal (-2e300).
+    auto probe = [&](const RunParams& Pp) -> double {
+        cudaError_t le = launch_groups(s, Pp, std::max(1, probe_steps / 4), s->cap_stream);
+        if (le == cudaSuccess) le = copy_all(false);
+        if (le == cudaSuccess) le = cudaEventRecord(e0, s->cap_stream);
+        if (le == cudaSuccess) le = launch_groups(s, Pp, probe_steps, s->cap_stream);
+        if (le == cudaSuccess) le = cudaEventRecord(e1, s->cap_stream);
+        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+        if (copy_all(false) != cudaSuccess) return -2e300;
+        if (le != cudaSuccess) {
+            (void)cudaGetLastError();  // a launch-configuration error
+            return -1.0;
+        }
+        return 1e3 * ms / probe_steps;
+    };
+    auto abort_restore = [&]() {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        release();
+        return fail(SCPS_ERR_CUDA, "tuner restore failed");
+    };
     for (size_t k = 0; k < cands.size(); ++k) {
         const std::vector<int>& c = cands[k];
         if (set_groups(s, c[0], c[1], c[2]) != SCPS_OK) continue;
         bool fits = true;
         for (auto& g : s->groups)
-            fits = fits && resident_smem_bytes(g.nta, g.ntp_max, s->ncon_max) <= smem_limit;
+            fits = fits && resident_smem_bytes(g.nta) <= smem_limit;
         if (!fits) continue;
-        // one short untimed run (first-launch set-up), then the timed probe; state restored after each
-        cudaError_t le = launch_groups(s, P, std::max(1, probe_steps / 4), s->cap_stream);
-        if (le == cudaSuccess) le = copy_all(false);
-        if (le == cudaSuccess) le = cudaEventRecord(e0, s->cap_stream);
-        if (le == cudaSuccess) le = launch_groups(s, P, probe_steps, s->cap_stream);
-        if (le == cudaSuccess) le = cudaEventRecord(e1, s->cap_stream);
-        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
-        cudaError_t re = copy_all(false);
-        if (re != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            release();
-            return fail(SCPS_ERR_CUDA, "tuner restore failed: %s", cudaGetErrorString(re));
-        }
-        if (le != cudaSuccess) {
-            (void)cudaGetLastError();  // a launch-configuration error: skip the candidate
-            continue;
-        }
+        const double us = probe(P);
+        if (us < -1e300) return abort_restore();
+        if (us < 0.0) continue;
         ++timed;
-        const double us = 1e3 * ms / probe_steps;
         if (k == 0) res.us_per_step_initial = us;
         // a candidate must win by more than 2 %: a shape within the timing noise of a
         // short probe does not replace the current one (or an earlier candidate)
@@ -1426,11 +1517,39 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
             best_c = c;
         }
     }
+    int rc = set_groups(s, best_c[0], best_c[1], best_c[2]);
+    if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        release();
+        return rc;
+    }
+    // list skin at the chosen shape: a larger skin adds pairs to every step and makes
+    // list builds rarer (the cadence follows from the displacement bound). Forces do not
+    // depend on it, so every choice gives the same trajectory bit for bit.
+    double best_skin = s->list_skin;
+    for (double sk : {0.04, 0.06, 0.08, 0.11, 0.15}) {
+        if (std::fabs(sk - s->list_skin) < 1e-9) continue;
+        const double keep = s->list_skin;
+        set_skin(s, sk);
+        RunParams Ps = s->base;
+        Ps.save_interval = 0;
+        const double us = probe(Ps);
+        set_skin(s, keep);
+        if (us < -1e300) return abort_restore();
+        if (us < 0.0) continue;
+        ++timed;
+        if (us < 0.98 * best) {
+            best = us;
+            best_skin = sk;
+        }
+    }
+    set_skin(s, best_skin);
+    drop_graphs(s);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     release();
-    int rc = set_groups(s, best_c[0], best_c[1], best_c[2]);
-    if (rc) return rc;
+    best_c.push_back((int)std::lround(1e3 * best_skin));
     {
         std::lock_guard<std::mutex> lk(mu);
         cache[key] = best_c;
@@ -1438,6 +1557,7 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
     res.plan = best_c[0];
     res.cluster_size = best_c[1];
     res.threads = best_c[2];
+    res.skin = best_skin;
     res.candidates = timed;
     res.us_per_step = best;
     if (out) *out = res;

@@ -209,6 +209,7 @@ enum { ELEC_NONE = 0, ELEC_DDIEL = 1, ELEC_RF = 2, ELEC_PLAIN = 3 };
 struct PairConst {
     float rc, rc2, inv_rc, inv_rc2, inv_rc3;
     float krf, crf;  // reaction field: k_rf, c_rf
+    float s_lim;     // largest |s| whose pair terms the 2^-13 integer sums of one item hold
 };
 
 // LJ constants of one pair: sigma^2, 24 eps, and (sigma / r_c)^6 with the

@@ -50,7 +50,28 @@ struct RepDev {
     long long frame_off;  // offset (in atoms) of the replica's frame ring buffer
     uint32_t rep_id;  // global replica id (noise counter word)
     int index;        // index of the replica in the per-replica state arrays
+    long long list_off;   // byte offset of the replica's pair-list slab (resident chains)
 };
+
+// Pair list of a chain replica in global memory (one slab per replica, laid out for a
+// launch with nta atom slots, nbs = nta / 8 blocks of 8 atoms):
+//   j entries (uint16): for block I, the atoms j of later blocks within the list radius
+//     of some atom of the block, ascending, padded to a multiple of 8 with the sentinel
+//     slot nta; block I owns 8 (nbs - 1 - I) entries from offset list_jl_off(nbs, I);
+//   item tables (uint32), one per CTA of a cluster: (I << 17 | near << 16 | chunk).
+__host__ __device__ __forceinline__ long long list_jl_off(int nbs, int I) {
+    return 8ll * ((long long)I * (nbs - 1) - (long long)I * (I - 1) / 2);
+}
+__host__ __device__ __forceinline__ long long list_jl_bytes(int nbs) {
+    return ((2ll * 4ll * nbs * (nbs - 1)) + 15) & ~15ll;
+}
+__host__ __device__ __forceinline__ long long list_items_cap(int nbs) {
+    return (long long)nbs * (nbs - 1) / 2 + 8;
+}
+__host__ __device__ __forceinline__ long long list_slab_bytes(int nta) {
+    const int nbs = nta / 8;
+    return list_jl_bytes(nbs) + 2 * ((4 * list_items_cap(nbs) + 15) & ~15ll);
+}
 
 // Replica state and outputs (device pointers).
 struct StateDev {
@@ -72,6 +93,8 @@ struct StateDev {
     double2* xy;
     double* sm;       // running minimum of s_lambda (tube bias)
     double* wm;       // running minimum of w_lambda (tube bias)
+    long long* pair_slots;  // resident chains: pairs one evaluation takes with the latest list
+    int* list_builds;       // resident chains: pair-list builds in the latest launch
 };
 
 struct RunParams {
@@ -85,6 +108,12 @@ struct RunParams {
     int save_interval, max_frames;
     long long n_steps;            // steps in this launch
     PairConst pc;
+    // pair list of the resident chain kernels
+    unsigned char* list_base;     // slabs (RepDev::list_off, or one per frame cluster)
+    long long list_slab;          // bytes per frame cluster (frame evaluation)
+    float rlist2;                 // (cutoff + skin)^2
+    float skin_half;              // rebuild once the displacement bound reaches skin / 2
+    int rebuild_every;            // and at least every this many steps (0: bound only)
     // two-dimensional models
     double toy_dt_over_gamma, toy_sd, toy_x_ref;
     double gamma;

@@ -420,10 +420,10 @@ def test_cluster_pair_matches_single_cta_and_oracle(pkg):
 
 # ------------------------------------------------------------------ size limits
 def test_largest_resident_chain_one_step_and_cta_shapes(pkg):
-    # 90 residues = 1440 atoms = 45 tiles: the largest chain whose resident state fits the
-    # shared memory of one CTA (152 B per atom slot plus boxes and the tile-pair table)
-    c = chain(90)
-    assert c.n_atoms == 1440
+    # 92 residues = 1472 atoms = 46 tiles: the largest chain whose resident state fits the
+    # shared memory of one CTA (152 B per atom slot, plus 8 sentinel slots)
+    c = chain(92)
+    assert c.n_atoms == 1472
     R = 2
     x0 = f32(np.stack([c.x_unfolded] * R))
     v0 = f32(c.velocities(R, KT, 15))
@@ -448,9 +448,9 @@ def test_largest_resident_chain_one_step_and_cta_shapes(pkg):
 
 
 def test_chain_above_the_shared_memory_limit(pkg):
-    # 92 residues = 1472 atoms = 46 tiles no longer fit one CTA: the resident form refuses
+    # 94 residues = 1504 atoms = 47 tiles no longer fit one CTA: the resident form refuses
     # at creation with UNSUPPORTED, the plain form (state in global memory) runs it
-    c = chain(92)
+    c = chain(94)
     R = 1
     x0 = f32(np.stack([c.x_unfolded] * R))
     v0 = f32(c.velocities(R, KT, 16))
@@ -470,8 +470,8 @@ def test_chain_above_the_shared_memory_limit(pkg):
 
 @pytest.mark.parametrize("n_res", [1, 3, 5])
 def test_small_chains_one_step_both_cta_shapes(pkg, n_res):
-    # 1, 2 and 3 tiles: only the tile with itself; the neighbour halves; one far tile pair
-    # (four quarter items, an odd live one runs alone)
+    # 1, 2 and 3 tiles (2, 4 and 6 blocks of 8): a block with itself only, the last block
+    # half padding; few pair items (most quarter warps of a batch idle)
     c = chain(n_res)
     pairs = c.contacts if len(c.contacts) else np.array([[0, c.n_atoms - 1]])
     R = 3

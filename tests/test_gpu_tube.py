@@ -76,12 +76,53 @@ def test_tube_short_run_tracks_oracle(pkg, path19):
     tb = oracle.TubeChain(c.contacts, c.x_native, A, t, 13.5, 50.0, 50.0, t[-1])
     ref = oracle.run_baoab_tube(ff, tb, x0, v0, [[np.inf, np.inf]] * R, [0] * R, np.arange(R), 13,
                                 DT, 1.0, KT, 20, save_every=5, max_frames=4)
-    assert np.abs(got["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-3
+    assert np.abs(got["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-4
     paths = s.collect_paths()
     for r in range(R):  # frames record s_lambda and its running minimum
         assert np.allclose(paths[r]["z"], ref["z"][r], atol=1e-4)
         assert np.allclose(paths[r]["zmin"], ref["zmin"][r], atol=1e-4)
     s.close()
+
+
+@pytest.mark.parametrize("K", [72, 128])
+def test_tube_benchmark_size_matches_oracle(pkg, K):
+    # the benchmarked chain (560 atoms, 2395 native contacts) with 72 and 128 reference
+    # slices: lanes take slices l, l + 32, l + 64, l + 96 in both passes and the decision,
+    # so slice blocks 1 to 3 are exercised
+    c = synth.make_chain(35, seed=1)
+    nc = len(c.contacts)
+    cu = np.array([np.linalg.norm(c.x_unfolded[j] - c.x_unfolded[i]) for i, j in c.contacts])
+    cn = np.array([np.linalg.norm(c.x_native[j] - c.x_native[i]) for i, j in c.contacts])
+    r = cu[None] + (cn - cu)[None] * np.linspace(0.0, 1.0, K)[:, None]
+    A = np.array([[oracle.contact_C(v) for v in row] for row in r])
+    assert A.shape == (K, nc)
+    t = (np.arange(K) + 1) * 7.0
+    R = 2
+    x0 = f32(np.stack([c.x_unfolded] * R))
+    v0 = f32(c.velocities(R, KT, 26))
+    ff = oracle.ForceField.from_chain(c)
+    tb = oracle.TubeChain(c.contacts, c.x_native, A, t, 13.5, 50.0, 50.0, t[-1])
+    s = tube_system(pkg, c, A, t, R, x0, v0, 50.0, 50.0, zm_value=-1.0)
+    s.step(1)
+    got = s.get_state()
+    s.close()
+    ref = oracle.run_baoab_tube(ff, tb, x0, v0, [[-1.0, -1.0]] * R, [0] * R, np.arange(R), 13, DT,
+                                1.0, KT, 1)
+    assert np.abs(got["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-6
+    assert np.all(ref["T"] > 0)
+    assert np.allclose(got["T"], ref["T"], rtol=1e-3)
+    # a short run: s_lambda and its running minimum at every saved frame
+    s = tube_system(pkg, c, A, t, R, x0, v0, 50.0, 50.0, save_interval=2, max_frames=5)
+    s.step(10)
+    got = s.get_state()
+    paths = s.collect_paths()
+    s.close()
+    ref = oracle.run_baoab_tube(ff, tb, x0, v0, [[np.inf, np.inf]] * R, [0] * R, np.arange(R), 13,
+                                DT, 1.0, KT, 10, save_every=2, max_frames=5)
+    assert np.abs(got["x"].reshape(ref["x"].shape) - ref["x"]).max() <= 1e-4
+    for q in range(R):
+        assert np.allclose(paths[q]["z"], ref["z"][q], atol=1e-5)
+        assert np.allclose(paths[q]["zmin"], ref["zmin"][q], atol=1e-5)
 
 
 def test_tube_cta_shapes_and_repeats_are_bit_identical(pkg, path19):
