@@ -79,6 +79,7 @@ struct Scalars {
     int flag[2];        // force-range bits raised during the evaluation of a given parity
     int n_items;        // pair items in this CTA's item table
     int n_diag;         // blocks whose inner pairs this CTA evaluates
+    int build_next;     // block counter of a list build
     unsigned vmax2[2];  // largest |v1|^2 + |v2|^2 of the update, by parity (float bits)
     long long pair_slots;  // pairs one evaluation with the current list takes
     long long n_saved;
@@ -154,6 +155,20 @@ __device__ __forceinline__ void add_fix(const Shared& sm, int* H, unsigned* L, i
     red_fix20(H, L, 2 * s + i, f2fix_checked(fz, sm.flag));
 }
 
+// Bonded terms: integer multiples of 2^-13 kJ mol^-1 nm^-1 (one conversion each); a term
+// that is non-finite or beyond 2.6e5 kJ mol^-1 nm^-1 (a bond stretched by more than 1 nm)
+// raises the force-range flag, which freezes the replica.
+__device__ __forceinline__ void add_term13(const Shared& sm, int* H, unsigned* L, int i, float fx,
+                                           float fy, float fz) {
+    const int s = sm.na8;
+    if (!(fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))) < 2.6e5f) ||
+        !(isfinite(fx) && isfinite(fy) && isfinite(fz)))
+        atomicOr(sm.flag, SCPS_FLAG_FORCE_RANGE);
+    red_fix13(H, L, i, __float2int_rn(fx * kPairScale));
+    red_fix13(H, L, s + i, __float2int_rn(fy * kPairScale));
+    red_fix13(H, L, 2 * s + i, __float2int_rn(fz * kPairScale));
+}
+
 // Cluster helpers: CL == 1 degenerates to a plain CTA.
 template <int CL>
 __device__ __forceinline__ void cluster_barrier() {
@@ -181,29 +196,35 @@ __device__ __forceinline__ int cta_rank() {
 
 // List slab of this replica or frame (see scps_internal.h for the layout).
 struct ListDev {
-    uint16_t* jl;       // j entries of all blocks
-    uint32_t* items;    // this CTA's item table
-    int nbs;            // blocks of the slab layout (nta / 8)
+    uint16_t* jl;               // j entries of all blocks
+    uint32_t* items;            // this CTA's item table
+    unsigned long long* excl;   // exclusion masks of this CTA's items
+    int nbs;                    // blocks of the slab layout (nta / 8)
 };
 
 __device__ __forceinline__ ListDev list_of(unsigned char* slab, int nta, int rank) {
     ListDev L;
     L.nbs = nta >> 3;
     L.jl = (uint16_t*)slab;
-    L.items = (uint32_t*)(slab + list_jl_bytes(L.nbs) +
-                          (long long)rank * ((4 * list_items_cap(L.nbs) + 15) & ~15ll));
+    const long long ib = list_items_bytes(L.nbs);
+    L.items = (uint32_t*)(slab + list_jl_bytes(L.nbs) + (long long)rank * ib);
+    L.excl = (unsigned long long*)(slab + list_jl_bytes(L.nbs) + 2 * ib) +
+             (long long)rank * list_items_cap(L.nbs);
     return L;
 }
 
 // The 64 pairs of one item (block I against the chunk whose atom j this lane holds) on
-// a quarter warp, fast path: integer pair terms summed in 32-bit registers. Returns
-// false (and adds nothing) when some |s| of the quarter warp exceeds pc.s_lim, for
-// which the integer sums of the item could overflow; the caller then takes the slow path.
+// a quarter warp, fast path: integer pair terms summed in 32-bit registers. Items near
+// their block (NEARX) take the excluded pairs from the item's mask xm. Returns false (and
+// adds nothing) when some |s| of the quarter warp exceeds pc.s_lim, for which the integer
+// sums of the item could overflow; the caller then takes the slow path.
 template <int ELEC, bool ENERGY, bool NEARX>
 __device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsigned* FL,
                                                const TopoDev& tp, const PairConst& pc, int I, int j,
-                                               int lane, long long& e18) {
+                                               unsigned long long xm, int lane, long long& e18) {
     const int l8 = lane & 7, q = lane >> 3;
+    // bit t of xr: the pair this lane takes at iteration t (block atom (l8 + t) & 7) is excluded
+    const unsigned xr = NEARX ? (unsigned)(xm >> (8 * l8)) & 0xffu : 0u;
     const int src = (lane & 24) | ((l8 + 1) & 7);
     const float4 xj = sm.xq[j];
     const float2 lj = sm.lj[j];
@@ -219,10 +240,7 @@ __device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsign
         const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         bool ok = r2 < pc.rc2;
-        if (NEARX) {  // j - i in [1, 64): a bonded neighbour may be excluded
-            const int dj = j - i + kExclWindow;
-            if (dj < 2 * kExclWindow && i < tp.n_atoms) ok = ok && !((tp.excl[i] >> dj) & 1ull);
-        }
+        if (NEARX) ok = ok && !((xr >> t) & 1u);
         float e = 0.f;
         float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
         s = ok ? s : 0.0f;
@@ -289,17 +307,19 @@ __device__ __forceinline__ void pair_batch(const Shared& sm, int* FH, unsigned* 
     const int it = 4 * batch + (lane >> 3);
     int I = 0, j = sm.nta;  // idle quarter: block 0 against the far sentinel slot (zero terms)
     bool near = false;
+    unsigned long long xm = 0ull;
     if (it < n_items) {
         const uint32_t d = __ldcg(L.items + it);
         I = (int)(d >> 17);
         near = (d >> 16) & 1u;
         j = (int)__ldcg(L.jl + list_jl_off(L.nbs, I) + 8 * (int)(d & 0xffffu) + (lane & 7));
+        if (near) xm = __ldcg(L.excl + it);
     }
     bool done;
     if (__any_sync(kFull, near))
-        done = pair_item_fast<ELEC, ENERGY, true>(sm, FH, FL, tp, pc, I, j, lane, e18);
+        done = pair_item_fast<ELEC, ENERGY, true>(sm, FH, FL, tp, pc, I, j, xm, lane, e18);
     else
-        done = pair_item_fast<ELEC, ENERGY, false>(sm, FH, FL, tp, pc, I, j, lane, e18);
+        done = pair_item_fast<ELEC, ENERGY, false>(sm, FH, FL, tp, pc, I, j, xm, lane, e18);
     if (!done) pair_item_slow<ELEC, ENERGY>(sm, FH, FL, tp, pc, I, j, lane, e20);
 }
 
@@ -389,8 +409,8 @@ __device__ __forceinline__ float bond_term(const Shared& sm, int* H, unsigned* L
     const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     const float dr = r - par.x;
     const float f = par.y * dr / r;
-    add_fix(sm, H, L, ij.x, f * dx, f * dy, f * dz);
-    add_fix(sm, H, L, ij.y, -f * dx, -f * dy, -f * dz);
+    add_term13(sm, H, L, ij.x, f * dx, f * dy, f * dz);
+    add_term13(sm, H, L, ij.y, -f * dx, -f * dy, -f * dz);
     return ENERGY ? 0.5f * par.y * dr * dr : 0.0f;
 }
 
@@ -413,23 +433,27 @@ __device__ __forceinline__ float angle_term(const Shared& sm, int* H, unsigned* 
     const float au = cs / ru2, aw = cs / rw2;
     const float fix = g * fmaf(au, ux, -wx), fiy = g * fmaf(au, uy, -wy), fiz = g * fmaf(au, uz, -wz);
     const float fkx = g * fmaf(aw, wx, -ux), fky = g * fmaf(aw, wy, -uy), fkz = g * fmaf(aw, wz, -uz);
-    add_fix(sm, H, L, ijk.x, fix, fiy, fiz);
-    add_fix(sm, H, L, ijk.z, fkx, fky, fkz);
-    add_fix(sm, H, L, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
+    add_term13(sm, H, L, ijk.x, fix, fiy, fiz);
+    add_term13(sm, H, L, ijk.z, fkx, fky, fkz);
+    add_term13(sm, H, L, ijk.y, -(fix + fkx), -(fiy + fky), -(fiz + fkz));
     return ENERGY ? 0.5f * par.y * dth * dth : 0.0f;
 }
 
-// Adds h (x_p - x_i) to G_i and its negative to G_p (2^-20 fixed point).
+// Adds h (x_p - x_i) to G_i and its negative to G_p (2^-20 fixed point). |h| <= |C - C0|
+// |dC/du| < 1 and h |x_p - x_i| stays far below 2^11, so one conversion to a 32-bit count
+// of 2^-20 units rounds exactly as the 64-bit conversion would.
 __device__ __forceinline__ void add_grad(const Shared& sm, int* GH, unsigned* GL, int i, int p,
                                          float h, float dx, float dy, float dz) {
-    const long long gx = f2fix(h * dx), gy = f2fix(h * dy), gz = f2fix(h * dz);
+    const float h20 = h * 1048576.0f;  // 2^20
+    const int gx = __float2int_rn(h20 * dx), gy = __float2int_rn(h20 * dy),
+              gz = __float2int_rn(h20 * dz);
     const int s = sm.na8;
-    red_fix20(GH, GL, i, gx);
-    red_fix20(GH, GL, s + i, gy);
-    red_fix20(GH, GL, 2 * s + i, gz);
-    red_fix20(GH, GL, p, -gx);
-    red_fix20(GH, GL, s + p, -gy);
-    red_fix20(GH, GL, 2 * s + p, -gz);
+    red_fix20(GH, GL, i, (long long)gx);
+    red_fix20(GH, GL, s + i, (long long)gy);
+    red_fix20(GH, GL, 2 * s + i, (long long)gz);
+    red_fix20(GH, GL, p, -(long long)gx);
+    red_fix20(GH, GL, s + p, -(long long)gy);
+    red_fix20(GH, GL, 2 * s + p, -(long long)gz);
 }
 
 // One native contact (i, p): (C - C0)^2 in float-float, returned as a 2^-40
@@ -452,7 +476,8 @@ __device__ __forceinline__ long long contact_term(const Shared& sm, int* GH, uns
 
 // Noise of the O half step of global step `step` for atoms 32 q .. 32 q + 31:
 // sqrt((1 - c1^2) kT / m_i) times Gaussian numbers from Philox4x32-10 with
-// counter (atom, replica id, step, 0).
+// counter (atom, replica id, step, 0). Drawn during the evaluation that precedes the
+// O half step, by warps that then go on to pull work items (the update stays short).
 __device__ __forceinline__ void noise_chunk(const Shared& sm, const TopoDev& tp, const RunParams& P,
                                             uint32_t rep_id, long long step, int q, int lane) {
     const int i = q * kTile + lane;
@@ -724,14 +749,14 @@ __device__ __forceinline__ void load_sums(const Shared& sm, int b, int peer, int
 // numbered over all blocks, chunks near a block (first j within the exclusion window of
 // the block) first; item k goes to CTA k % CL. Called by every thread of every CTA of
 // the cluster; returns after a cluster barrier (the peer has finished reading this
-// CTA's counts, which share the noise array's space).
+// CTA's counts, which share the xi array's space).
 template <int CL>
 __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, float rlist2,
                            const ListDev& L) {
     const int n = tp.n_atoms, nb = (n + 7) >> 3;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int rank = cta_rank<CL>();
-    // scratch in the noise array: boxes (2 nb float4), chunk counts, near-chunk counts
+    // scratch in the xi array: boxes (2 nb float4), chunk counts, near-chunk counts
     // and the two prefix arrays (nb ints each)
     float4* blo = sm.xi;
     float4* bhi = sm.xi + nb;
@@ -739,7 +764,8 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
     int* cntn = cnt + nb;
     int* pren = cntn + nb;
     int* pref = pren + nb;
-    __syncthreads();  // warp 0 may still be summing the bias terms held in the noise array
+    __syncthreads();  // warp 0 may still be summing the bias terms held in the xi array
+    if (tid == 0) sc.build_next = 0;
     for (int I = tid; I < nb; I += blockDim.x) {
         float4 lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
         float4 hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
@@ -757,7 +783,11 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
     }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    for (int I = rank + CL * warp; I < nb; I += CL * nw) {
+    for (;;) {  // this CTA's blocks, one warp each, pulled in order (early blocks have most work)
+        int m = 0;
+        if (lane == 0) m = atomicAdd(&sc.build_next, 1);
+        const int I = __shfl_sync(kFull, m, 0) * CL + rank;
+        if (I >= nb) break;
         const float4 bl = blo[I], bh = bhi[I];
         const int i0 = 8 * I, ia = min(8, n - i0);
         uint16_t* out = L.jl + list_jl_off(L.nbs, I);
@@ -778,33 +808,16 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
                     }
                 }
                 const int j = Jc >= 0 ? 8 * Jc + (lane & 7) : n;
-                // atoms within sqrt(rlist2) of the block's box, then, four at a time (eight
-                // lanes each, one block atom per lane), the exact test against the atoms
-                float4 xj = make_float4(0.f, 0.f, 0.f, 0.f);
-                bool pass = false;
+                bool hit = false;  // within sqrt(rlist2) of some atom of the block
                 if (j < n) {
-                    xj = sm.xq[j];
-                    const float gx = fmaxf(0.f, fmaxf(bl.x - xj.x, xj.x - bh.x));
-                    const float gy = fmaxf(0.f, fmaxf(bl.y - xj.y, xj.y - bh.y));
-                    const float gz = fmaxf(0.f, fmaxf(bl.z - xj.z, xj.z - bh.z));
-                    pass = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < rlist2;
-                }
-                const unsigned pm = __ballot_sync(kFull, pass);
-                const int np = __popc(pm), rk = __popc(pm & lt);
-                bool hit = false;
-                for (int p0 = 0; p0 < np; p0 += 4) {
-                    const int sv = p0 + (lane >> 3), a = lane & 7;
-                    const int src = sv < np ? (int)__fns(pm, 0, sv + 1) : 0;
-                    const float qx = __shfl_sync(kFull, xj.x, src), qy = __shfl_sync(kFull, xj.y, src),
-                                qz = __shfl_sync(kFull, xj.z, src);
-                    bool h = false;
-                    if (sv < np && a < ia) {
+                    const float4 xj = sm.xq[j];
+                    float dmin = 3.0e38f;
+                    for (int a = 0; a < ia; ++a) {
                         const float4 xa = sm.xq[i0 + a];
-                        const float dx = qx - xa.x, dy = qy - xa.y, dz = qz - xa.z;
-                        h = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rlist2;
+                        const float dx = xj.x - xa.x, dy = xj.y - xa.y, dz = xj.z - xa.z;
+                        dmin = fminf(dmin, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                     }
-                    const unsigned hb = __ballot_sync(kFull, h);
-                    if (pass && rk >= p0 && rk < p0 + 4) hit = ((hb >> (8 * (rk - p0))) & 0xffu) != 0u;
+                    hit = dmin < rlist2;
                 }
                 const unsigned hm = __ballot_sync(kFull, hit);
                 if (hit) out[count + __popc(hm & lt)] = (uint16_t)j;
@@ -870,6 +883,30 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
             if (k % CL == rank)
                 L.items[k / CL] = ((uint32_t)I << 17) | ((uint32_t)(c < cn) << 16) | (uint32_t)c;
         }
+        // excluded pairs of the near items, in the order the lanes meet them (byte s, bit t:
+        // entry s with block atom (s + t) & 7); four chunks per pass, eight lanes each, the
+        // block atoms' exclusion words held by lanes 0..7
+        const unsigned long long exa = (lane < 8 && 8 * I + lane < n) ? tp.excl[8 * I + lane] : 0ull;
+        const uint16_t* e = L.jl + list_jl_off(L.nbs, I);
+        for (int c0 = 0; c0 < cn; c0 += 4) {
+            const int c = c0 + (lane >> 3), sl = lane & 7;
+            const int jj = c < cn ? (int)__ldcg(e + 8 * c + sl) : 0;
+            unsigned byte = 0u;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int a = (sl + t) & 7, i = 8 * I + a;
+                const unsigned long long ex = __shfl_sync(kFull, exa, a);
+                const int dj = jj - i + kExclWindow;  // entries lie after the block
+                if (c < cn && dj < 2 * kExclWindow && ((ex >> dj) & 1ull)) byte |= 1u << t;
+            }
+            unsigned long long m = (unsigned long long)byte << (8 * sl);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) m |= __shfl_xor_sync(kFull, m, o);
+            if (sl == 0 && c < cn) {
+                const int k = pren[I] + c;
+                if (k % CL == rank) L.excl[k / CL] = m;
+            }
+        }
     }
     __threadfence();
     cluster_barrier<CL>();  // the peer is done with this CTA's counts; items are visible
@@ -925,11 +962,12 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     long long dacc[TUBE ? kMaxTubeK / 32 : 1];  // first-pass slice sums of this lane
 #pragma unroll
     for (int q = 0; q < (TUBE ? kMaxTubeK / 32 : 1); ++q) dacc[q] = 0;
+    int m_next = 0;  // the next work index is pulled while the current item runs
+    if (lane == 0) m_next = atomicAdd(counter, 1);
     for (;;) {
-        int m = 0;
-        if (lane == 0) m = atomicAdd(counter, 1);
-        const int k = __shfl_sync(kFull, m, 0);
+        const int k = __shfl_sync(kFull, m_next, 0);
         if (k >= e_all) break;
+        if (lane == 0) m_next = atomicAdd(counter, 1);
         if (k < e_pair) {
             int kp = -1, kc = -1;  // pair batch or contact item
             if (k < 2 * m_mix) {
@@ -985,26 +1023,28 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         sc.red_e[b][warp] = e;
     }
     cluster_barrier<CL>();
-    // the partials of the other parity were last read (here and in the peer CTA)
-    // before this barrier: clear them for the next evaluation meanwhile
-    for (int i = tid; i < 3 * sm.na8; i += blockDim.x) {
-        sm.FH[b ^ 1][i] = 0;
-        sm.FL[b ^ 1][i] = 0u;
-        sm.GH[b ^ 1][i] = 0;
-        sm.GL[b ^ 1][i] = 0u;
-    }
+    // (the partials of the other parity are cleared atom by atom in the update that follows;
+    // the slice sums of the tube bias here)
     if (tube)
         for (int i = tid; i < P.tube_k; i += blockDim.x) sc.red_d[b ^ 1][i] = 0;
-    // shares of z, energy and flags from every CTA of the cluster (integer sums)
+    // shares of z, energy and flags from every CTA of the cluster (integer sums); all
+    // remote loads are issued before any is used
     if (warp == 0) {
+        long long zq[CL], eq[CL];
+        int fq[CL];
+#pragma unroll
+        for (int q = 0; q < CL; ++q) {
+            zq[q] = lane < nw ? rank_ptr<CL>(&sc.red_z[b][0], q)[lane] : 0;
+            eq[q] = (ENERGY && lane < nw) ? rank_ptr<CL>(&sc.red_e[b][0], q)[lane] : 0;
+            fq[q] = lane == 0 ? *rank_ptr<CL>(&sc.flag[b], q) : 0;
+        }
         long long zt = 0, et = 0;
         int fl = 0;
+#pragma unroll
         for (int q = 0; q < CL; ++q) {
-            if (lane < nw) {
-                zt += rank_ptr<CL>(&sc.red_z[b][0], q)[lane];
-                if (ENERGY) et += rank_ptr<CL>(&sc.red_e[b][0], q)[lane];
-            }
-            if (lane == 0) fl |= *rank_ptr<CL>(&sc.flag[b], q);
+            zt += zq[q];
+            et += eq[q];
+            fl |= fq[q];
         }
         zt = warp_sum_ll(zt);
         if (ENERGY) et = warp_sum_ll(et);
@@ -1144,6 +1184,15 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
                 if (i < n) {
                     AtomSums a;
                     load_sums<CL>(sm, b, peer, i, bias, a);
+                    // the other parity's partials were last read before this evaluation's
+                    // cluster barrier (here and in the peer): clear them for the next one
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        sm.FH[nb][c * sm.na8 + i] = 0;
+                        sm.FL[nb][c * sm.na8 + i] = 0u;
+                        sm.GH[nb][c * sm.na8 + i] = 0;
+                        sm.GL[nb][c * sm.na8 + i] = 0u;
+                    }
                     float4 v = sm.v[i];
                     const float im = v.w;
                     float fx = fix2f(a.f[0]), fy = fix2f(a.f[1]), fz = fix2f(a.f[2]);
@@ -1341,7 +1390,7 @@ k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __
 }
 
 // Shared-memory bytes of the resident kernels for nta atom slots (plus the 8 sentinel
-// slots): positions, velocities, noise, LJ parameters and the two parities of force and
+// slots): positions, velocities, the xi array, LJ parameters and the two parities of force and
 // bias-gradient partials (integer and fraction words).
 size_t resident_smem_bytes(int nta) {
     const size_t na8 = (size_t)nta + 8;

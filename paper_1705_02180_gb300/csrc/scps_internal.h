@@ -58,7 +58,9 @@ struct RepDev {
 //   j entries (uint16): for block I, the atoms j of later blocks within the list radius
 //     of some atom of the block, ascending, padded to a multiple of 8 with the sentinel
 //     slot nta; block I owns 8 (nbs - 1 - I) entries from offset list_jl_off(nbs, I);
-//   item tables (uint32), one per CTA of a cluster: (I << 17 | near << 16 | chunk).
+//   item tables (uint32), one per CTA of a cluster: (I << 17 | near << 16 | chunk);
+//   exclusion masks (uint64), one per item of those tables: bit 8 a + s set when block atom a
+//     and chunk entry s form an excluded pair (items near their block only).
 __host__ __device__ __forceinline__ long long list_jl_off(int nbs, int I) {
     return 8ll * ((long long)I * (nbs - 1) - (long long)I * (I - 1) / 2);
 }
@@ -68,9 +70,12 @@ __host__ __device__ __forceinline__ long long list_jl_bytes(int nbs) {
 __host__ __device__ __forceinline__ long long list_items_cap(int nbs) {
     return (long long)nbs * (nbs - 1) / 2 + 8;
 }
+__host__ __device__ __forceinline__ long long list_items_bytes(int nbs) {
+    return (4 * list_items_cap(nbs) + 15) & ~15ll;
+}
 __host__ __device__ __forceinline__ long long list_slab_bytes(int nta) {
     const int nbs = nta / 8;
-    return list_jl_bytes(nbs) + 2 * ((4 * list_items_cap(nbs) + 15) & ~15ll);
+    return list_jl_bytes(nbs) + 2 * list_items_bytes(nbs) + 2 * 8 * list_items_cap(nbs);
 }
 
 // Replica state and outputs (device pointers).

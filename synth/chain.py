@@ -322,19 +322,52 @@ _CACHE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file
                           ".cache", "synth")
 
 
-def make_chain(n_res: int = 35, seed: int = 1, cache: bool = True) -> ChainSystem:
-    """Build (or load from the on-disk cache) the seeded chain with n_res residues."""
+_THERMAL_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "thermal")
+
+
+def thermal_unfolded(n_res: int, seed: int = 1):
+    """The stored thermally unfolded conformation of a chain (2 ns at 600 K from X_N, written
+    once by a separate run of the FP64 reference integrator), or None when there is none. The
+    file's header holds the SHA-256 of the coordinates, checked here."""
+    import hashlib
+    path = os.path.join(_THERMAL_DIR, f"chain_r{n_res}_s{seed}_600K_2ns.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        header = f.readline()
+    x = np.loadtxt(path)
+    want = header.rsplit("sha256(float64 coords)=", 1)[-1].strip()
+    got = hashlib.sha256(np.ascontiguousarray(x, np.float64).tobytes()).hexdigest()
+    if got != want:
+        raise ValueError(f"{path}: coordinates do not match their recorded hash")
+    return x
+
+
+def make_chain(n_res: int = 35, seed: int = 1, cache: bool = True,
+               thermal: bool = True) -> ChainSystem:
+    """Build (or load from the on-disk cache) the seeded chain with n_res residues. With
+    `thermal` (the default) X_U is the stored thermally unfolded conformation when one
+    exists for this chain; otherwise (and with thermal=False) it is the random coil, which
+    stays available as `x_coil`."""
     path = os.path.join(_CACHE_DIR, f"chain_v{GENERATOR_VERSION}_r{n_res}_s{seed}.pkl")
+    c = None
     if cache and os.path.exists(path):
         with open(path, "rb") as f:
-            return pickle.load(f)
-    c = _make_chain(n_res, seed)
-    if cache:
-        os.makedirs(_CACHE_DIR, exist_ok=True)
-        tmp = f"{path}.{os.getpid()}.tmp"
-        with open(tmp, "wb") as f:
-            pickle.dump(c, f)
-        os.replace(tmp, path)
+            c = pickle.load(f)
+    if c is None:
+        c = _make_chain(n_res, seed)
+        if cache:
+            os.makedirs(_CACHE_DIR, exist_ok=True)
+            tmp = f"{path}.{os.getpid()}.tmp"
+            with open(tmp, "wb") as f:
+                pickle.dump(c, f)
+            os.replace(tmp, path)
+    coil = c.x_unfolded
+    if thermal:
+        xt = thermal_unfolded(n_res, seed)
+        if xt is not None:
+            c = dataclasses.replace(c, x_unfolded=xt)
+    c.x_coil = coil
     return c
 
 
