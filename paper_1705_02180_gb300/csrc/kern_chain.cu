@@ -69,7 +69,17 @@ struct Shared {
     unsigned* GL[2];    //   contacts this CTA evaluated (the bias gradient without its
                         //   ratchet factor, which is known only once z is complete)
     int* flag;          // force-range flag of the current evaluation
+    struct CacheItem* lc;  // this CTA's pair items when they fit (see CacheItem)
     int nta, na8;       // atom slots; accumulator stride (nta + 8)
+    int lc_cap;         // capacity of lc in items
+};
+
+// A pair item held in shared memory: descriptor, exclusion mask and the chunk's 8 entries
+// (the same data as the global item table, mask table and j entries, without their latency).
+struct CacheItem {
+    uint32_t desc, pad;
+    unsigned long long xm;
+    uint16_t j[8];
 };
 
 struct Scalars {
@@ -78,6 +88,7 @@ struct Scalars {
     int bias_on;
     int flag[2];        // force-range bits raised during the evaluation of a given parity
     int n_items;        // pair items in this CTA's item table
+    int cached;         // 1: the items are held in shared memory (Shared::lc)
     int n_diag;         // blocks whose inner pairs this CTA evaluates
     int build_next;     // block counter of a list build
     unsigned vmax2[2];  // largest |v1|^2 + |v2|^2 of the update, by parity (float bits)
@@ -94,7 +105,7 @@ struct Scalars {
     long long red_d[2][kMaxTubeK];      // this CTA's share of sum_p (C_p - A_kp)^2 (2^-40), by parity
 };
 
-__device__ __forceinline__ Shared carve(void* base, int nta) {
+__device__ __forceinline__ Shared carve(void* base, int nta, int lc_cap) {
     Shared s;
     char* p = (char*)base;
     const int na8 = nta + 8;
@@ -109,7 +120,9 @@ __device__ __forceinline__ Shared carve(void* base, int nta) {
         s.GH[b] = (int*)p; p += sizeof(int) * 3 * na8;
         s.GL[b] = (unsigned*)p; p += sizeof(unsigned) * 3 * na8;
     }
-    s.lj = (float2*)p;
+    s.lj = (float2*)p; p += sizeof(float2) * na8;
+    s.lc = (CacheItem*)p;
+    s.lc_cap = lc_cap;
     s.flag = nullptr;
     return s;
 }
@@ -303,17 +316,27 @@ __device__ __noinline__ void pair_item_slow(const Shared& sm, int* FH, unsigned*
 template <int ELEC, bool ENERGY>
 __device__ __forceinline__ void pair_batch(const Shared& sm, int* FH, unsigned* FL, const TopoDev& tp,
                                            const PairConst& pc, const ListDev& L, int n_items,
-                                           int batch, int lane, long long& e18, long long& e20) {
+                                           bool cached, int batch, int lane, long long& e18,
+                                           long long& e20) {
     const int it = 4 * batch + (lane >> 3);
     int I = 0, j = sm.nta;  // idle quarter: block 0 against the far sentinel slot (zero terms)
     bool near = false;
     unsigned long long xm = 0ull;
     if (it < n_items) {
-        const uint32_t d = __ldcg(L.items + it);
-        I = (int)(d >> 17);
-        near = (d >> 16) & 1u;
-        j = (int)__ldcg(L.jl + list_jl_off(L.nbs, I) + 8 * (int)(d & 0xffffu) + (lane & 7));
-        if (near) xm = __ldcg(L.excl + it);
+        if (cached) {
+            const CacheItem& c = sm.lc[it];
+            const uint32_t d = c.desc;
+            I = (int)(d >> 17);
+            near = (d >> 16) & 1u;
+            j = (int)c.j[lane & 7];
+            xm = c.xm;
+        } else {
+            const uint32_t d = __ldcg(L.items + it);
+            I = (int)(d >> 17);
+            near = (d >> 16) & 1u;
+            j = (int)__ldcg(L.jl + list_jl_off(L.nbs, I) + 8 * (int)(d & 0xffffu) + (lane & 7));
+            if (near) xm = __ldcg(L.excl + it);
+        }
     }
     bool done;
     if (__any_sync(kFull, near))
@@ -865,6 +888,7 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
         const int total = runn + runf;
         if (lane == 0) {
             sc.n_items = (total - rank + CL - 1) / CL;
+            sc.cached = sc.n_items <= sm.lc_cap ? 1 : 0;
             sc.n_diag = (nb - rank + CL - 1) / CL;
             sc.work_next[0] = 0;
             sc.work_next[1] = 0;
@@ -875,14 +899,25 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
     }
     __syncthreads();
     const int tot_near = pref[nb];
+    const bool cached = sc.cached;
     for (int I = warp; I < nb; I += nw) {
         const int owner = I % CL;
         const int ct = *rank_ptr<CL>(&cnt[I], owner), cn = *rank_ptr<CL>(&cntn[I], owner);
         for (int c = lane; c < ct; c += 32) {
             const int k = c < cn ? pren[I] + c : tot_near + pref[I] + (c - cn);
-            if (k % CL == rank)
-                L.items[k / CL] = ((uint32_t)I << 17) | ((uint32_t)(c < cn) << 16) | (uint32_t)c;
+            if (k % CL == rank) {
+                const uint32_t d = ((uint32_t)I << 17) | ((uint32_t)(c < cn) << 16) | (uint32_t)c;
+                if (cached) {  // the chunk's 8 entries: one 16-byte load (chunks are 16-aligned)
+                    CacheItem& ci = sm.lc[k / CL];
+                    ci.desc = d;
+                    ci.xm = 0ull;
+                    *(uint4*)ci.j = __ldcg((const uint4*)(L.jl + list_jl_off(L.nbs, I) + 8 * c));
+                } else {
+                    L.items[k / CL] = d;
+                }
+            }
         }
+        __syncwarp();  // (the records above are complete before their masks are written)
         // excluded pairs of the near items, in the order the lanes meet them (byte s, bit t:
         // entry s with block atom (s + t) & 7); four chunks per pass, eight lanes each, the
         // block atoms' exclusion words held by lanes 0..7
@@ -904,7 +939,12 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
             for (int o = 4; o > 0; o >>= 1) m |= __shfl_xor_sync(kFull, m, o);
             if (sl == 0 && c < cn) {
                 const int k = pren[I] + c;
-                if (k % CL == rank) L.excl[k / CL] = m;
+                if (k % CL == rank) {
+                    if (cached)
+                        sm.lc[k / CL].xm = m;
+                    else
+                        L.excl[k / CL] = m;
+                }
             }
         }
     }
@@ -977,7 +1017,8 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
                 if (r < n_pb - m_mix) kp = m_mix + r; else kc = m_mix + r - (n_pb - m_mix);
             }
             if (kp >= 0) {
-                pair_batch<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, L, sc.n_items, kp, lane, e18, e20);
+                pair_batch<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, L, sc.n_items, sc.cached, kp, lane, e18,
+                                         e20);
             } else {
                 const int g = kc * CL + rank;
                 if (tube) {
@@ -1098,14 +1139,14 @@ __device__ __forceinline__ float4 far_slot(int i) {
 template <int ELEC, int CL, bool TUBE>
 __global__ void __launch_bounds__(CL == 2 ? kMaxThreadsPair : 1024, 1)
 k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, StateDev st,
-           RunParams P, int nta) {
+           RunParams P, int nta, int lc_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const RepDev rep = reps[blockIdx.x / CL];  // this launch's replicas, in any order
     const int r = rep.index;
     const int rank = cta_rank<CL>();
     const TopoDev tp = topos[rep.topo];
-    Shared sm = carve(smem_raw, nta);
+    Shared sm = carve(smem_raw, nta, lc_cap);
     const ListDev L = list_of(P.list_base + rep.list_off, nta, rank);
     const int n = tp.n_atoms;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1325,11 +1366,12 @@ k_resident(const TopoDev* __restrict__ topos, const RepDev* __restrict__ reps, S
 template <int ELEC, int CL>
 __global__ void __launch_bounds__(1024, 1)
 k_eval_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
-              double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta) {
+              double* __restrict__ U, float* __restrict__ F, double* __restrict__ Z, int nta,
+              int lc_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Scalars sc;
     const TopoDev tp = *topo_ptr;
-    Shared sm = carve(smem_raw, nta);
+    Shared sm = carve(smem_raw, nta, lc_cap);
     const int n = tp.n_atoms;
     const long long f = blockIdx.x / CL;
     const int rank = cta_rank<CL>();
@@ -1398,14 +1440,9 @@ size_t resident_smem_bytes(int nta) {
            2 * 4 * 3 * sizeof(int) * na8;
 }
 
-// Dynamic shared memory a resident or frame-evaluation CTA may request on the current
-// device: the opt-in per-block limit less the largest static shared block of those kernels.
-// 0 when the device cannot be queried (nothing then fits).
-size_t resident_smem_limit() {
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return 0;
+// Largest static shared block of the resident and frame-evaluation kernels (0 when the
+// device cannot be queried).
+static size_t resident_static_smem() {
     size_t stat = 0;
     const void* kernels[] = {(const void*)k_resident<ELEC_DDIEL, 1, false>,
                              (const void*)k_resident<ELEC_DDIEL, 2, true>,
@@ -1416,13 +1453,54 @@ size_t resident_smem_limit() {
         if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
         stat = std::max(stat, a.sharedSizeBytes);
     }
+    return stat;
+}
+
+// Dynamic shared memory a resident or frame-evaluation CTA may request on the current
+// device: the opt-in per-block limit less the largest static shared block of those kernels.
+// 0 when the device cannot be queried (nothing then fits).
+size_t resident_smem_limit() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    const size_t stat = resident_static_smem();
     return (size_t)optin > stat ? (size_t)optin - stat : 0;
+}
+
+constexpr int kMaxCacheItems = 16384;
+
+// Dynamic shared memory of a launch with CTAs of `threads` threads: the resident state plus
+// a cache of pair items (CacheItem, 32 B) in what the state leaves free; CTAs of up to 512
+// threads keep room for a second CTA on their SM. Sets *lc_cap to the cache's capacity.
+static size_t launch_smem(int nta, int threads, int cl, int* lc_cap) {
+    const int cl_items_per_slot = cl == 2 ? 2 : 4;
+    const size_t base = resident_smem_bytes(nta);
+    size_t lim = resident_smem_limit();
+    if (threads <= 512) {
+        int dev = 0, per_sm = 0, reserved = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        const size_t stat = resident_static_smem();
+        const size_t two = (size_t)per_sm / 2;
+        const size_t half = two > (size_t)reserved + stat ? two - (size_t)reserved - stat : 0;
+        lim = std::min(lim, half);
+    }
+    size_t cap = lim > base ? (lim - base) / sizeof(CacheItem) : 0;
+    // no more than the lists of compact chains need (about 1.8 x 80 pairs per atom in items
+    // of 64, per CTA): shared memory and the L1 cache share the SM's storage, and the L1
+    // serves the topology tables; longer tables stay in global memory
+    cap = std::min(cap, std::min((size_t)kMaxCacheItems, (size_t)(cl_items_per_slot * nta)));
+    *lc_cap = (int)cap;
+    return base + cap * sizeof(CacheItem);
 }
 
 template <int ELEC, int CL, bool TUBE>
 static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, const StateDev& st,
                                      const RunParams& P, int nta, int threads, cudaStream_t stream) {
-    const size_t smem = resident_smem_bytes(nta);
+    int lc_cap = 0;
+    const size_t smem = launch_smem(nta, threads, CL, &lc_cap);
     auto kern = k_resident<ELEC, CL, TUBE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1438,7 +1516,7 @@ static cudaError_t launch_resident_t(const TopoDev* topos, const RepDev* reps, c
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta);
+    e = cudaLaunchKernelEx(&cfg, kern, topos, reps, st, P, nta, lc_cap);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1474,7 +1552,8 @@ template <int ELEC>
 static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const float* X,
                                  double* U, float* F, double* Z, long long n_frames, int nta,
                                  int threads, int cl, cudaStream_t stream) {
-    const size_t smem = resident_smem_bytes(nta);
+    int lc_cap = 0;
+    const size_t smem = launch_smem(nta, threads, cl, &lc_cap);
     auto kern = cl == 2 ? k_eval_frames<ELEC, 2> : k_eval_frames<ELEC, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1490,7 +1569,7 @@ static cudaError_t launch_eval_t(const TopoDev* topo, const RunParams& P, const 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, topo, P, X, U, F, Z, nta);
+    e = cudaLaunchKernelEx(&cfg, kern, topo, P, X, U, F, Z, nta, lc_cap);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -52,7 +52,7 @@ def test_hvp_matches_oracle(torch_cuda, n_res):
     for t in range(len(X)):
         _, ref = ff.hvp(X[t].astype(np.float64), V[t].astype(np.float64))
         err = np.abs(HV[t].cpu().numpy() - ref).max() / rms(ref)
-        assert err <= 1e-4, (t, err)
+        assert err <= 1e-5, (t, err)
     s.close()
 
 
@@ -86,6 +86,11 @@ def test_force_norm_action_gradient_with_checkpointing(torch_cuda):
     A = force_norm_action(s, X, segment=50)
     A.backward()
     G = X.grad.cpu().numpy()
+    # the GPU's own forces on the same frames: the backward applies H to them
+    Ug = torch.empty(T, dtype=torch.float64, device="cuda")
+    Fg = torch.empty_like(X)
+    s.energy_forces(0, X.detach(), Ug, Fg)
+    Fg = Fg.double().cpu().numpy()
     ff = oracle.ForceField.from_chain(c)
     rng = np.random.default_rng(11)
     coords = [(rng.integers(T), rng.integers(c.n_atoms), rng.integers(3)) for _ in range(200)]
@@ -99,8 +104,16 @@ def test_force_norm_action_gradient_with_checkpointing(torch_cuda):
         _, hg = ff.hvp(x, gU)
         ref = 2 * hg  # oracle analytic gradient of |grad U|^2
         scale = rms(ref)
+        # the FP64 Hessian applied to the GPU's FP32 forces: isolates the HVP kernel and
+        # the autograd plumbing from the error of the forces themselves
+        _, hg_gpu = ff.hvp(x, -Fg[t])
+        ref_gpu_forces = 2 * hg_gpu
         for i, k in lst:
-            assert abs(G[t, i, k] - ref[i, k]) <= 2e-4 * scale, (t, i, k)
+            assert abs(G[t, i, k] - ref_gpu_forces[i, k]) <= 1e-5 * scale, (t, i, k)
+            # against the all-FP64 gradient the force error (<= 1e-5 of rms |F|) passes
+            # through H, whose largest curvatures (short-range repulsion) amplify it: the
+            # bound is the force tolerance times max |H dF| / rms(H grad U) over these frames
+            assert abs(G[t, i, k] - ref[i, k]) <= 5e-5 * scale, (t, i, k)
         # central finite difference (h = 1e-4 nm) of the FP64 oracle action, first coordinate
         i, k = lst[0]
         xp = x.copy(); xp[i, k] += h
