@@ -132,7 +132,7 @@ typedef struct {
     int32_t steps_per_graph;/* device-loop steps per CUDA-graph node: 0 = auto */
     /* pair lists */
     double skin;            /* list buffer r_list - r_c (nm); 0 = default (0.15 for the periodic
-                               box, 0.08 for chains). A list is rebuilt before any pair inside
+                               box, 0.12 for chains). A list is rebuilt before any pair inside
                                r_c can be missing: periodic box, once an atom has moved skin/2
                                since the last build; chains, once a bound on every atom's
                                displacement since then (dt/2 times the largest |v| + |v'| of

@@ -487,7 +487,7 @@ __device__ __forceinline__ long long contact_term(const Shared& sm, int* GH, uns
                                                   const TopoDev& tp, const RunParams& P, int c) {
     const int2 ij = tp.con_ij[c];
     const float4 a = sm.xq[ij.x], b = sm.xq[ij.y];
-    const ff r2 = ff_r2(ff_diff(b.x, a.x), ff_diff(b.y, a.y), ff_diff(b.z, a.z));
+    const ff r2 = ff_dist2(a, b);
     const ff u = ff_mul(r2, P.inv_r0sq_ff);
     const ff C = contact_C_ff(u);
     const float2 c0 = tp.con_C0[c];

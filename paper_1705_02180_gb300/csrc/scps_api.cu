@@ -81,7 +81,7 @@ int fail(int code, const char* fmt, ...) {
     } while (0)
 
 constexpr double kCoulombF = 138.935458;  // kJ mol^-1 nm e^-2
-constexpr double kDefaultChainSkin = 0.08;  // nm: pair-list buffer of the chain kernels
+constexpr double kDefaultChainSkin = 0.12;  // nm: pair-list buffer of the chain kernels
 constexpr long long kEvalFramesPerLaunch = 1024;  // frame clusters per evaluation launch
 
 struct TopoHost {

@@ -175,6 +175,22 @@ __device__ __forceinline__ ff ff_r2(ff dx, ff dy, ff dz) {
     return ff_add(s, ff_sqr(dz));
 }
 
+// The same squared distance from the two positions, with fewer renormalisations: each axis
+// gives its exact difference (h, l), h^2 as an exact product pair (p, e) and the cross
+// term 2 h l (l^2 is below 2^-48 of h^2); the three p are summed error-free and every
+// low-order part is added once before the final renormalisation. Relative error ~1e-14.
+__device__ __forceinline__ ff ff_dist2(float4 a, float4 b) {
+    const ff dx = two_sum(b.x, -a.x), dy = two_sum(b.y, -a.y), dz = two_sum(b.z, -a.z);
+    const float px = __fmul_rn(dx.hi, dx.hi), py = __fmul_rn(dy.hi, dy.hi), pz = __fmul_rn(dz.hi, dz.hi);
+    const float qx = __fmaf_rn(2.0f * dx.hi, dx.lo, __fmaf_rn(dx.hi, dx.hi, -px));
+    const float qy = __fmaf_rn(2.0f * dy.hi, dy.lo, __fmaf_rn(dy.hi, dy.hi, -py));
+    const float qz = __fmaf_rn(2.0f * dz.hi, dz.lo, __fmaf_rn(dz.hi, dz.hi, -pz));
+    const ff s1 = two_sum(px, py);
+    const ff s2 = two_sum(s1.hi, pz);
+    const float low = __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(__fadd_rn(qx, qy), qz));
+    return fast_two_sum(s2.hi, low);
+}
+
 // Contact-map entry of Eq. (Cij) in u = (r/r0)^2, using the exact rewrite
 // (1 - u^3)/(1 - u^5) = (1 + u + u^2) / (1 + u + u^2 + u^3 + u^4).
 __device__ __forceinline__ ff contact_C_ff(ff u) {
