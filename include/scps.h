@@ -285,7 +285,7 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
 /* Autotuner of the resident form (chain replicas): times the launch plans
  * (SCPS_PLAN_*), cluster sizes {1, 2} and threads per CTA {256, 512, 1024} (768 in
  * place of 1024 for 2-CTA clusters) on the system itself, then, at the chosen shape, the
- * pair-list skin {0.04, 0.06, 0.08, 0.11, 0.15} nm (a larger skin adds pairs to every
+ * pair-list skin {0.06, 0.09, 0.12, 0.16, 0.2} nm (a larger skin adds pairs to every
  * step and makes list builds rarer: the rebuild cadence follows from the displacement
  * bound), probe_steps steps each from the current state (restored after every probe; no
  * frames are saved while probing), and keeps the fastest; a candidate replaces the

@@ -1528,7 +1528,7 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
     // list builds rarer (the cadence follows from the displacement bound). Forces do not
     // depend on it, so every choice gives the same trajectory bit for bit.
     double best_skin = s->list_skin;
-    for (double sk : {0.04, 0.06, 0.08, 0.11, 0.15}) {
+    for (double sk : {0.06, 0.09, 0.12, 0.16, 0.2}) {
         if (std::fabs(sk - s->list_skin) < 1e-9) continue;
         const double keep = s->list_skin;
         set_skin(s, sk);
