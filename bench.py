@@ -2,10 +2,11 @@
 """Throughput of biased Langevin (rMD) replicas on GB300, through the C ABI.
 
 Workload (default): 64 replicas of a seeded 560-atom synthetic chain (35
-residues; stand-in for the ~550-atom Fip35 domain), unfolded start, T = 300 K,
-gamma = 1/ps, dt = 2 fs, ratchet bias on the native-contact coordinate z with
-k_R = 1e-4 kJ/mol, FP32 forces with int64 fixed-point sums, 10^5 steps in
-total. One bench step = one scps_step_replicas call of 1000 MD steps for every
+residues; stand-in for the ~550-atom Fip35 domain), thermally unfolded start
+(X_N run 2 ns at 600 K by the FP64 oracle, stored), T = 300 K, gamma = 1/ps,
+dt = 2 fs, ratchet bias on the native-contact coordinate z with k_R = 1e-4
+kJ/mol, FP32 force terms with fixed-point sums, 10^5 steps in total. The CTA
+shape and the pair-list skin are picked by the autotuner before the warm-up. One bench step = one scps_step_replicas call of 1000 MD steps for every
 replica; K bench steps are timed with CUDA events on the launching stream,
 with an L2 flush (a 512 MB write) between calls outside the events.
 
@@ -530,6 +531,9 @@ def main():
                       max_frames=args.warmup + args.steps, threads=args.threads,
                       steps_per_graph=spc)
     sysm.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4, r0=0.75)
+    # CTA shape and pair-list skin picked by the autotuner on the system itself (its probes
+    # start from the current state and restore it), unless a CTA width is forced
+    tune = sysm.autotune(probe_steps=200) if args.threads == 0 else None
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
@@ -584,7 +588,10 @@ def main():
                          "replicas_per_gpu": R, "atoms": n, "md_steps_per_call": spc,
                          "md_steps_total": spc * args.steps, "native_contacts": int(len(c.contacts)),
                          "l2": "flushed between calls (512 MB write)",
-                         "threads_per_cta": info["threads"], "parallelism": f"replicas x{world}"},
+                         "threads_per_cta": info["threads"], "cluster": info["cluster_size"],
+                         "list_skin_nm": info["list_skin"],
+                         "steps_per_list_build": info["steps_per_list_build"],
+                         "autotune": tune, "parallelism": f"replicas x{world}"},
               "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak, "traffic": None,
                            "note": f"FP32 peak = {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "

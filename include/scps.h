@@ -206,6 +206,8 @@ typedef struct {
     double us_per_step;                 /* probe time per step of the choice */
     double us_per_step_initial;         /* probe time per step of the configuration before */
     double skin;                        /* chosen pair-list skin (nm) */
+    int32_t rebuild_every;              /* periodic box: chosen rebuild cadence (steps);
+                                           chains: the descriptor's value (0: displacement only) */
 } scps_tune_result;
 
 typedef struct scps_system scps_system;
@@ -294,7 +296,14 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
  * count, electrostatics, bias kind, multiset of replica sizes); use_cache != 0 takes a
  * cached choice without probing. The plan changes only which CTA runs which replica and
  * forces do not depend on the skin, so trajectories are bit-identical under every
- * choice. Synchronous; out may be NULL. */
+ * choice.
+ * Periodic box: the pair-list skin {0.1, 0.15, 0.2} nm x the rebuild cadence {10, 20,
+ * 40} steps (a rebuild also comes earlier once an atom has moved skin/2), probed the
+ * same way from a device snapshot of the box state; the probes and the final choice
+ * force a list rebuild at the next step, so the trajectory equals that of a run with one
+ * more rebuild there (the box's FP32 per-atom sums follow the list order: equal to
+ * rounding, not bit for bit). Cached under (SM count, electrostatics, atoms, replicas).
+ * Synchronous; out may be NULL. */
 int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out);
 
 /* Philox4x32-10 blocks on the device, for checking the noise stream:

@@ -67,7 +67,8 @@ class Info(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("plan", C.c_int32), ("cluster_size", C.c_int32), ("threads", C.c_int32),
                 ("candidates", C.c_int32), ("from_cache", C.c_int32), ("us_per_step", C.c_double),
-                ("us_per_step_initial", C.c_double), ("skin", C.c_double)]
+                ("us_per_step_initial", C.c_double), ("skin", C.c_double),
+                ("rebuild_every", C.c_int32)]
 
 
 PLAN_ONE_LAUNCH, PLAN_PER_SIZE_CLASS = 0, 1

@@ -1374,12 +1374,180 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
     return SCPS_OK;
 }
 
+// Autotuner of the periodic box: pair-list skin x rebuild cadence, each probed for
+// probe_steps steps on the system itself from a device snapshot of the box state (slot
+// order, positions, velocities, ids and the per-replica scalars); every probe and the final
+// restore force a list rebuild, since a list built for a smaller skin does not cover the
+// displacements a larger one allows.
+static int box_autotune(scps_system* s, int probe_steps, int use_cache, scps_tune_result* out) {
+    BoxDev& B = s->box;
+    const int R = s->d.n_replicas;
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
+    const std::string key = "box|" + std::to_string(n_sm) + "|" + std::to_string(s->d.elec) + "|" +
+                            std::to_string(B.n_atoms) + "x" + std::to_string(R);
+    static std::mutex mu;
+    static std::map<std::string, std::pair<double, int>> cache;  // skin, rebuild_every
+    const double rc = s->base.pc.rc > 0.f ? (double)s->base.pc.rc : 1.0;
+    std::vector<int> ones(R, 1);
+    auto apply = [&](double skin, int every) {
+        s->list_skin = skin;
+        B.rebuild_every = every;
+        B.rlist2 = (float)((rc + skin) * (rc + skin));
+        B.skin2_quarter = (float)(0.25 * skin * skin);
+        return cudaMemcpyAsync(B.need, ones.data(), sizeof(int) * R, cudaMemcpyHostToDevice,
+                               s->cap_stream);
+    };
+    scps_tune_result res{};
+    res.plan = s->plan;
+    res.cluster_size = 1;
+    res.threads = 0;
+    res.skin = s->list_skin;
+    res.rebuild_every = B.rebuild_every;
+    if (use_cache) {
+        bool hit = false;
+        std::pair<double, int> c;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                hit = true;
+                c = it->second;
+            }
+        }
+        if (hit) {
+            SCPS_CU(apply(c.first, c.second));
+            SCPS_CU(cudaStreamSynchronize(s->cap_stream));
+            res.skin = c.first;
+            res.rebuild_every = c.second;
+            res.from_cache = 1;
+            if (out) *out = res;
+            return SCPS_OK;
+        }
+    }
+    // device snapshot of what a probe changes
+    const size_t np = (size_t)R * B.np;
+    struct Region {
+        void* p;
+        size_t n;
+    };
+    const Region regions[] = {
+        {B.pos, sizeof(float4) * np},          {B.vel, sizeof(float4) * np},
+        {B.id, sizeof(int) * np},              {B.par, sizeof(float2) * np},
+        {B.slot_of, sizeof(int) * (size_t)R * B.n_atoms},
+        {B.pos_ref, sizeof(float4) * np},      {B.since, sizeof(int) * R},
+        {B.maxd2, sizeof(unsigned) * R},       {B.eb, sizeof(double) * R},
+        {s->st.zm, sizeof(double) * R},        {s->st.z, sizeof(double) * R},
+        {s->st.T, sizeof(double) * R},         {s->st.step, sizeof(long long) * R},
+        {s->st.status, sizeof(int) * R}};
+    size_t total = 0;
+    for (const Region& g : regions) total += (g.n + 255) & ~(size_t)255;
+    unsigned char* snap = nullptr;
+    SCPS_CU(cudaMalloc(&snap, total));
+    auto copy_all = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        cudaError_t c = cudaSuccess;
+        for (const Region& g : regions) {
+            if (c == cudaSuccess)
+                c = cudaMemcpyAsync(save ? (void*)(snap + off) : g.p, save ? g.p : (void*)(snap + off),
+                                    g.n, cudaMemcpyDeviceToDevice, s->cap_stream);
+            off += (g.n + 255) & ~(size_t)255;
+        }
+        if (c == cudaSuccess) c = cudaStreamSynchronize(s->cap_stream);
+        return c;
+    };
+    cudaError_t e = copy_all(true);
+    if (e != cudaSuccess) {
+        cudaFree(snap);
+        return fail(SCPS_ERR_CUDA, "tuner snapshot failed: %s", cudaGetErrorString(e));
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    RunParams P = s->base;
+    P.save_interval = 0;
+    const long long frame_atoms = (long long)std::max(s->d.max_frames, 1) * B.n_atoms;
+    const long long step0 = s->host_step[0];
+    // returns us per step, or -2e300 when a restore failed
+    auto probe = [&](double skin, int every) -> double {
+        cudaError_t le = apply(skin, every);
+        if (le == cudaSuccess)
+            le = box_run(B, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max, step0,
+                         std::max(1, probe_steps / 4), frame_atoms, s->cap_stream);
+        if (le == cudaSuccess) le = copy_all(false);
+        if (le == cudaSuccess) le = apply(skin, every);
+        if (le == cudaSuccess) le = cudaEventRecord(e0, s->cap_stream);
+        if (le == cudaSuccess)
+            le = box_run(B, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max, step0,
+                         probe_steps, frame_atoms, s->cap_stream);
+        if (le == cudaSuccess) le = cudaEventRecord(e1, s->cap_stream);
+        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+        std::vector<int> stat(R, 0);  // a frozen replica (e.g. a list overflow) voids the probe
+        if (le == cudaSuccess)
+            le = cudaMemcpy(stat.data(), s->st.status, sizeof(int) * R, cudaMemcpyDeviceToHost);
+        if (copy_all(false) != cudaSuccess || le != cudaSuccess) return -2e300;
+        for (int r = 0; r < R; ++r)
+            if (stat[r] != 0) return -1.0;
+        return 1e3 * ms / probe_steps;
+    };
+    const double skin0 = s->list_skin;
+    const int every0 = B.rebuild_every;
+    std::vector<std::pair<double, int>> cands{{skin0, every0}};
+    for (double sk : {0.1, 0.15, 0.2})
+        for (int ev : {10, 20, 40})
+            if (std::fabs(sk - skin0) > 1e-9 || ev != every0) cands.push_back({sk, ev});
+    double best = 1e300;
+    std::pair<double, int> best_c = cands[0];
+    int timed = 0;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        const double us = probe(cands[k].first, cands[k].second);
+        if (us < -1e300) {
+            apply(skin0, every0);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaFree(snap);
+            return fail(SCPS_ERR_CUDA, "tuner probe or restore failed");
+        }
+        if (us < 0.0) continue;
+        ++timed;
+        if (k == 0) res.us_per_step_initial = us;
+        if (us < 0.98 * best) {  // more than 2 % faster, as for the chains
+            best = us;
+            best_c = cands[k];
+        }
+    }
+    e = apply(best_c.first, best_c.second);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cap_stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    SCPS_CU(e);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = best_c;
+    }
+    res.skin = best_c.first;
+    res.rebuild_every = best_c.second;
+    res.candidates = timed;
+    res.us_per_step = best;
+    if (out) *out = res;
+    return SCPS_OK;
+}
+
 int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out) {
     TraceRange trace_("scps_autotune");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
-    if (s->model != SCPS_MODEL_CHAIN || s->is_box || s->d.exec != SCPS_EXEC_RESIDENT)
-        return fail(SCPS_ERR_UNSUPPORTED, "the tuner covers the resident form of chain replicas");
     if (probe_steps < 1 || probe_steps > 100000) return fail(SCPS_ERR_INVALID_ARG, "probe_steps outside [1, 1e5]");
+    if (s->model == SCPS_MODEL_CHAIN && s->is_box) {
+        for (int r = 1; r < s->d.n_replicas; ++r)
+            if (s->host_step[r] != s->host_step[0])
+                return fail(SCPS_ERR_STATE, "periodic-box replicas must share one step counter");
+        return box_autotune(s, probe_steps, use_cache, out);
+    }
+    if (s->model != SCPS_MODEL_CHAIN || s->d.exec != SCPS_EXEC_RESIDENT)
+        return fail(SCPS_ERR_UNSUPPORTED, "the tuner covers the resident form of chain replicas and the periodic box");
     const int R = s->d.n_replicas;
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -1396,6 +1564,7 @@ int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_t
     res.cluster_size = s->cluster;
     res.threads = s->threads;
     res.skin = s->list_skin;
+    res.rebuild_every = s->base.rebuild_every;
     if (use_cache) {
         std::vector<int> hit;
         {

@@ -117,3 +117,40 @@ def test_box_rejects_small_box(torch_cuda, box):
     with pytest.raises(pkg.ScpsError):
         pkg.System(topologies=[b.topology()], replica_topology=[0], x0=b.x, cutoff=1.0, elec=2,
                    box=2.0, dt=0.002, gamma=1.0, kT=KT)
+
+
+def test_box_autotune_restores_state_and_keeps_the_trajectory(torch_cuda, box):
+    # the tuner probes skin x rebuild cadence from a device snapshot and restores it: the
+    # state after tuning is the state before, bit for bit; the tuned run then follows the
+    # untuned one to FP32 rounding (a list rebuild at the restore point changes only the
+    # order of the per-atom FP32 sums)
+    import paper_1705_02180_gb300 as pkg
+    b = box
+    c = b.chain
+    pairs = c.contacts if len(c.contacts) else np.array([[0, c.n_atoms - 1]])
+    R = 2
+    x0 = np.stack([f32(b.x)] * R)
+    v0 = f32(b.velocities(R, KT, 5))
+    runs = []
+    for tune in (False, True):
+        s = make(pkg, b, R, v0=v0)
+        s.set_contact_bias([pairs], [c.x_native], k_R=1e-4)
+        s.step(10)
+        before = s.get_state()
+        if tune:
+            t = s.autotune(probe_steps=8, use_cache=False)
+            assert t["skin"] in (0.1, 0.15, 0.2) and t["rebuild_every"] in (10, 20, 40)
+            assert t["candidates"] >= 9 and t["us_per_step"] > 0
+            after = s.get_state()
+            for k in ("x", "v", "zm", "step", "T"):
+                assert np.array_equal(before[k], after[k]), k
+            info = s.info()
+            assert info["list_skin"] == pytest.approx(t["skin"])
+            again = s.autotune(probe_steps=8)  # cached: no probes
+            assert again["from_cache"] == 1 and again["skin"] == t["skin"]
+        s.step(30)
+        assert not s.status()[1].any()
+        runs.append(s.get_state())
+        s.close()
+    assert np.abs(runs[0]["x"] - runs[1]["x"]).max() < 1e-4
+    assert np.array_equal(runs[0]["step"], runs[1]["step"])
