@@ -342,6 +342,7 @@ def extra_config(torch, pkg, name, args, K, W):
                        cutoff=1.0, elec=pkg.ELEC_RF, eps_rf=78.5, box=b.box, dt=0.002, gamma=1.0,
                        kT=KT_300, seed=SEED, skin=0.15, rebuild_every=20)
         s.set_contact_bias([c.contacts], [c.x_native], k_R=1e-4)
+        tune = s.autotune(probe_steps=20)  # pair-list skin x rebuild cadence
         durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
         atoms = b.n_atoms * R
         rate = atoms * spc * K / durs.sum()
@@ -358,9 +359,10 @@ def extra_config(torch, pkg, name, args, K, W):
         out = {"metric": "biased-Langevin atom-steps/s", "value": rate, "unit": "atom-steps/s",
                "ms_per_step": durs.mean() * 1e3, "steps": K, "warmup": W,
                "config": {"workload": f"{R} replicas x ({c.n_atoms}-atom chain + 24000 solvent "
-                                      f"sites), L {b.box:.3f} nm, RF, rc 1.0, skin 0.15, rebuild "
-                                      "<= 20 steps, dt 2 fs, 300 K",
-                          "atoms": atoms, "md_steps_per_call": spc},
+                                      f"sites), L {b.box:.3f} nm, RF, rc 1.0, skin "
+                                      f"{tune['skin']:.2f}, rebuild <= {tune['rebuild_every']} "
+                                      "steps (autotuned), dt 2 fs, 300 K",
+                          "atoms": atoms, "md_steps_per_call": spc, "autotune": tune},
                "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                             "frac": ach / peak, "traffic": None,
                             "in_cutoff_pairs_per_replica": p_in},
@@ -368,9 +370,10 @@ def extra_config(torch, pkg, name, args, K, W):
                        "peak_GBps": hbm_peak,
                        "frac": gbs / hbm_peak if hbm_peak else None,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm_peak else None},
-               # per call: one re-evaluation (5 kernels) + its A half step, then
-               # 5 + 1 kernels per step and the step counter
-               "gpu_launches": K * (6 + 6 * spc + 1), "clocks": clk}
+               # per call: one re-evaluation (8 list kernels, which return at once unless a
+               # rebuild is due, pairs, chain) + its A half step, the same 11 kernels per
+               # step, and the step counter
+               "gpu_launches": K * (11 * (spc + 1) + 1), "clocks": clk}
         rc, st = s.status()
         out["status"] = int(rc)
         s.close()

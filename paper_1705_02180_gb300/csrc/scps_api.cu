@@ -957,7 +957,9 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
         const long long frame_atoms = (long long)std::max(s->d.max_frames, 1) * s->box.n_atoms;
         SCPS_CU(box_run(s->box, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max,
                         s->host_step[0], n_steps, frame_atoms, cs));
-        launches = 8 * (n_steps + 1);
+        // per evaluation 8 list kernels (they return at once unless a rebuild is due), pairs
+        // and chain; an integrate per half step pair; the step counter
+        launches = 11 * (n_steps + 1) + 1;
     } else if (s->d.exec == SCPS_EXEC_PLAIN) {
         P.n_steps = n_steps;
         std::vector<RepDev> reps(R);
