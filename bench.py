@@ -346,6 +346,7 @@ def extra_config(torch, pkg, name, args, K, W):
         durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
         atoms = b.n_atoms * R
         rate = atoms * spc * K / durs.sum()
+        slots = s.info()["pair_checks_per_step"] / R
         xs = s.get_state()["x"].reshape(R, b.n_atoms, 3)[0] % b.box
         p_in = len(cKDTree(xs, boxsize=b.box).query_pairs(1.0)) - len(c.exclusions)
         t = b.topology()
@@ -365,7 +366,8 @@ def extra_config(torch, pkg, name, args, K, W):
                           "atoms": atoms, "md_steps_per_call": spc, "autotune": tune},
                "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                             "frac": ach / peak, "traffic": None,
-                            "in_cutoff_pairs_per_replica": p_in},
+                            "in_cutoff_pairs_per_replica": p_in,
+                            "pair_slots_evaluated_per_replica": slots},
                "hbm": {"algorithmic_GBps": gbs, "bytes_per_atom_step": bytes_per_atom_step,
                        "peak_GBps": hbm_peak,
                        "frac": gbs / hbm_peak if hbm_peak else None,

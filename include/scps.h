@@ -182,11 +182,13 @@ typedef struct {
     int64_t pair_checks_per_step;       /* resident chains: non-bonded pair slots one step
                                            evaluates, summed over replicas, with the pair list
                                            each replica built last (64 per list item of 8 x 8
-                                           atoms, 28 per block of 8 with itself) */
+                                           atoms, 28 per block of 8 with itself); periodic
+                                           box: 64 per chunk of 8 list entries of an 8-slot
+                                           cluster (synchronises) */
     size_t device_bytes;                /* device memory held by the system */
     int32_t launch_groups;              /* resident form: launches per step call chunk */
     int32_t plan;                       /* resident form: SCPS_PLAN_* */
-    double list_skin;                   /* chains: pair-list skin r_list - r_c (nm) */
+    double list_skin;                   /* pair-list skin r_list - r_c (nm) */
     double steps_per_list_build;        /* resident chains: mean steps per pair-list build in
                                            the latest launch (the build that opens a launch
                                            counts) */

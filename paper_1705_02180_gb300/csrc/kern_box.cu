@@ -1,5 +1,5 @@
 // Solvated periodic box: rMD replicas of one chain in LJ + Coulomb solvent
-// (reaction field), cubic box, column-sorted tiles and cluster pair lists.
+// (reaction field), cubic box, column-sorted slots and atom-level pair lists.
 //
 // Per step (kernels in stream order):
 //   [rebuild, when due]  wrap; sort atoms into ncol x ncol columns in (x, y),
@@ -7,19 +7,22 @@
 //                        column into tiles of 32 slots (the last one padded);
 //                        inside a tile, order by x into two halves of 16 and
 //                        each half by y, so that slots 8q..8q+7 form a compact
-//                        j cluster; tile and cluster boxes; per i tile the list
-//                        of j clusters within r_c + skin of the tile box, each
-//                        with the periodic shift that is the minimum image of
-//                        all its pairs (else the tile takes it pair by pair)
-//   pairs                one warp per i tile; each lane owns one slot and adds
-//                        up its own force over the listed clusters (both
-//                        directions of every pair: no atomics, a fixed order)
+//                        cluster; cluster boxes; per 8-slot cluster the list
+//                        of atoms of later clusters within r_c + skin of one of
+//                        its atoms, each with the periodic shift of its cluster
+//                        (the cluster takes the minimum image pair by pair where
+//                        that shift might not hold until the next rebuild)
+//   pairs                one warp per cluster, four chunks of 8 entries at a
+//                        time on quarter warps, every pair once; all force
+//                        terms summed in fixed point (order-free)
 //   chain                one CTA per replica: bonds, angles, z(X) of Eq.
 //                        (zrMD), the ratchet of Eq. (FrMD), the bias force
 //   integrate            BAOAB half steps with Philox noise keyed by atom id
 // A rebuild is due every `rebuild_every` steps, or earlier when an atom has
 // moved more than skin/2 since the last one, so every pair inside the cutoff
-// is always in the list. The rebuild order depends only on positions and ids.
+// is always in the list. Forces are integer sums of per-pair terms (order-free);
+// positions are wrapped into the box at each rebuild, so runs that rebuild at
+// other steps agree to rounding.
 #include "scps_internal.h"
 
 namespace scps {
@@ -245,9 +248,9 @@ __global__ void k_box_subsort(BoxDev B, const TopoDev* __restrict__ topo, int r0
     }
 }
 
-// Rebuild step 2: boxes of the 16-slot i groups (tile halves) and of the 8-slot
-// j clusters (one warp per tile), and which groups and clusters hold only atoms with the LJ parameters of the last atom (a
-// solvent site), whose pair constants the pair kernel then computes once.
+// Rebuild step 2 (one warp per tile): box of each 8-slot cluster, and whether it holds
+// chain atoms or only atoms with the LJ parameters of the last atom (a solvent site), whose
+// pair constants the pair kernel then computes once.
 __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) {
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
@@ -256,71 +259,75 @@ __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) 
     const int lane = threadIdx.x & 31;
     const int s = t * 32 + lane;
     const float4 p = B.pos[(size_t)r * B.np + s];
-    const bool valid = B.id[(size_t)r * B.np + s] >= 0;
+    const int a = B.id[(size_t)r * B.np + s];
+    const bool valid = a >= 0;
     const float2 ref = topo->lj[B.n_atoms - 1];
     const float2 par = B.par[(size_t)r * B.np + s];
     const unsigned pure = __ballot_sync(kFullB, !valid || (par.x == ref.x && par.y == ref.y));
+    const unsigned chain = __ballot_sync(kFullB, valid && a < B.n_chain);
     float lx = valid ? p.x : 3.0e38f, ly = valid ? p.y : 3.0e38f, lz = valid ? p.z : 3.0e38f;
     float hx = valid ? p.x : -3.0e38f, hy = valid ? p.y : -3.0e38f, hz = valid ? p.z : -3.0e38f;
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
+    for (int o = 1; o < 8; o <<= 1) {
         lx = fminf(lx, __shfl_xor_sync(kFullB, lx, o));
         ly = fminf(ly, __shfl_xor_sync(kFullB, ly, o));
         lz = fminf(lz, __shfl_xor_sync(kFullB, lz, o));
         hx = fmaxf(hx, __shfl_xor_sync(kFullB, hx, o));
         hy = fmaxf(hy, __shfl_xor_sync(kFullB, hy, o));
         hz = fmaxf(hz, __shfl_xor_sync(kFullB, hz, o));
-        if (o == 4 && (lane & 7) == 0) {  // the box of the 8-slot cluster of this lane
-            const size_t c = (size_t)r * 4 * B.nt + 4 * t + (lane >> 3);
-            const bool cpure = ((pure >> (lane & ~7)) & 0xffu) == 0xffu;
-            B.clo[c] = make_float4(lx, ly, lz, cpure ? 1.f : 0.f);
-            B.chi[c] = make_float4(hx, hy, hz, 0.f);
-        }
     }
-    // lanes 0 and 16 now hold the boxes of the two 16-slot halves (the i groups)
-    const int a = B.id[(size_t)r * B.np + s];
-    const unsigned chain = __ballot_sync(kFullB, a >= 0 && a < B.n_chain);
-    if ((lane & 15) == 0) {
-        const int h = lane >> 4;
-        const size_t g = (size_t)r * 2 * B.nt + 2 * t + h;
-        const unsigned half = 0xffffu << (16 * h);
-        B.tlo[g] = make_float4(lx, ly, lz, 0.f);
-        B.thi[g] = make_float4(hx, hy, hz, 0.f);
-        B.tflag[g] = ((chain & half) ? 1 : 0) | ((pure & half) == half ? 4 : 0);
+    if ((lane & 7) == 0) {  // the box of the 8-slot cluster of this lane
+        const size_t c = (size_t)r * 4 * B.nt + 4 * t + (lane >> 3);
+        const unsigned mine = 0xffu << (lane & ~7);
+        const bool cpure = (pure & mine) == mine;
+        B.clo[c] = make_float4(lx, ly, lz, cpure ? 1.f : 0.f);
+        B.chi[c] = make_float4(hx, hy, hz, 0.f);
+        B.cflag[c] = ((chain & mine) ? 1 : 0) | (cpure ? 4 : 0);
     }
 }
 
-// Rebuild step 3: j clusters near every i group (one warp per group), in cluster order;
-// the group's own tile comes first, then later tiles only (each pair once).
-// Each entry carries the periodic shift s (per axis -1, 0 or 1, in units of L) that
-// takes the cluster's box centre nearest to the tile's. When |d_c + s L| plus both
-// half widths plus the skin (the most two atoms can close in before the next
-// rebuild) stays below L / 2 on every axis, s is the minimum image of every pair of
-// the two boxes until then; otherwise the tile is flagged for the per-pair minimum
-// image.
-__global__ void k_box_list(BoxDev B, StateDev st, int r0) {
+// Rebuild step 3 (one warp per 8-slot i cluster c): the pair list of c. Its own 8 slots
+// come first (the pair kernel takes those pairs once, j slot after i slot); then, from the
+// clusters after c in slot order whose boxes come within r_list of c's box, the atoms within
+// r_list of some atom of c (minimum-image distances), in ascending slot order. Each entry
+// carries the periodic shift s (per axis -1, 0 or 1 in units of L) that takes its cluster's
+// box centre nearest to c's. Where a coordinate difference of some atom of c and the entry
+// under s, plus the skin (the most two atoms can close in before the next rebuild), reaches
+// L / 2, s may stop being the minimum image of that pair: c is then flagged for the per-pair
+// minimum image.
+__global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0) {
+    __shared__ float4 sxi[4][8];
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // i group (tile half)
-    if (g >= 2 * B.nt) return;
-    const int t = g >> 1;
-    const int lane = threadIdx.x & 31;
-    const size_t gi = (size_t)r * 2 * B.nt + g;
-    const float4 al = B.tlo[gi], ah = B.thi[gi];
-    uint32_t* out = B.nbr + gi * B.max_nbr;
-    int count = 0;
+    const int ncl = 4 * B.nt;
+    const int w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 4 + w;
+    if (c >= ncl) return;
+    const int lane = threadIdx.x & 31, l8 = lane & 7, q = lane >> 3;
+    const size_t base = (size_t)r * B.np;
+    const size_t ci = (size_t)r * ncl + c;
+    uint32_t* out = B.ent + ci * B.max_ent;
+    constexpr uint32_t kNoShift = (1u << 24) | (1u << 26) | (1u << 28);
+    const float4 al = B.clo[ci], ah = B.chi[ci];
+    const int si = 8 * c + l8;
+    const unsigned ivalid = __ballot_sync(kFullB, B.id[base + si] >= 0) & 0xffu;
+    if (lane < 8) {
+        sxi[w][lane] = B.pos[base + si];
+        out[lane] = (uint32_t)si | kNoShift | (al.w != 0.f ? 1u << 30 : 0u);
+    }
+    __syncwarp();
+    int count = 8;
     bool inexact = false;
     const float room = 0.5f * B.L - 2.0f * sqrtf(B.skin2_quarter);  // L/2 - skin
-    if (al.x <= ah.x) {  // the i group holds atoms
+    if (ivalid) {
         const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
         const float hx = 0.5f * (ah.x - al.x), hy = 0.5f * (ah.y - al.y), hz = 0.5f * (ah.z - al.z);
-        const int ncl = 4 * B.nt;
-        for (int j0 = 4 * t; j0 < ncl; j0 += 32) {
-            const int j = j0 + lane;
-            bool hit = false, exact = true;
+        for (int j0 = c + 1; j0 < ncl; j0 += 32) {
+            const int jc = j0 + lane;
+            bool hit = false;
             uint32_t code = 0;
-            if (j < ncl) {
-                const float4 bl = B.clo[(size_t)r * ncl + j], bh = B.chi[(size_t)r * ncl + j];
+            if (jc < ncl) {
+                const float4 bl = B.clo[(size_t)r * ncl + jc], bh = B.chi[(size_t)r * ncl + jc];
                 if (bl.x <= bh.x) {  // the cluster holds atoms
                     const float dx = 0.5f * (bl.x + bh.x) - cx, dy = 0.5f * (bl.y + bh.y) - cy,
                                 dz = 0.5f * (bl.z + bh.z) - cz;
@@ -334,50 +341,87 @@ __global__ void k_box_list(BoxDev B, StateDev st, int r0) {
                     const float gx = fmaxf(0.f, ex - wx), gy = fmaxf(0.f, ey - wy),
                                 gz = fmaxf(0.f, ez - wz);
                     hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
-                    exact = ex + wx < room && ey + wy < room && ez + wz < room;
-                    code = (uint32_t)j | ((uint32_t)(sx + 1.f) << 24) | ((uint32_t)(sy + 1.f) << 26) |
+                    code = ((uint32_t)(sx + 1.f) << 24) | ((uint32_t)(sy + 1.f) << 26) |
                            ((uint32_t)(sz + 1.f) << 28) | (bl.w != 0.f ? 1u << 30 : 0u);
                 }
             }
-            const unsigned m = __ballot_sync(kFullB, hit);
-            if (hit) {
-                const int pos = count + __popc(m & ((1u << lane) - 1u));
-                if (pos < B.max_nbr) out[pos] = code;
+            unsigned m = __ballot_sync(kFullB, hit);
+            while (m) {  // four hit clusters at a time: lane 8 k + a takes atom a of the k-th
+                const int nh = min(__popc(m), 4);
+                unsigned mm = m;
+                for (int k = 0; k < q; ++k) mm &= mm - 1u;
+                const int src = __ffs(mm) - 1;  // lane of this quarter's hit cluster (-1: none)
+                const uint32_t hcode = __shfl_sync(kFullB, code, src & 31);
+                for (int k = 0; k < nh; ++k) m &= m - 1u;
+                bool keep = false;
+                uint32_t e = 0;
+                if (q < nh) {
+                    const int sj = 8 * (j0 + src) + l8;
+                    if (B.id[base + sj] >= 0) {
+                        const float4 xj = B.pos[base + sj];
+                        const float ox = (float)((int)((hcode >> 24) & 3u) - 1) * B.L,
+                                    oy = (float)((int)((hcode >> 26) & 3u) - 1) * B.L,
+                                    oz = (float)((int)((hcode >> 28) & 3u) - 1) * B.L;
+                        float d2 = 3.0e38f, dm = 0.f;
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            if (!((ivalid >> t) & 1u)) continue;
+                            const float4 a = sxi[w][t];
+                            const float dx = xj.x - a.x, dy = xj.y - a.y, dz = xj.z - a.z;
+                            const float mx = min_img(dx, B.L, B.invL), my = min_img(dy, B.L, B.invL),
+                                        mz = min_img(dz, B.L, B.invL);
+                            d2 = fminf(d2, fmaf(mx, mx, fmaf(my, my, mz * mz)));
+                            dm = fmaxf(dm, fmaxf(fabsf(dx + ox), fmaxf(fabsf(dy + oy), fabsf(dz + oz))));
+                        }
+                        keep = d2 < B.rlist2;
+                        inexact = inexact || (keep && !(dm < room));
+                        e = (uint32_t)sj | (hcode & 0x7f000000u);
+                    }
+                }
+                const unsigned kb = __ballot_sync(kFullB, keep);
+                if (keep) {
+                    const int pos = count + __popc(kb & ((1u << lane) - 1u));
+                    if (pos < B.max_ent) out[pos] = e;
+                }
+                count += __popc(kb);
             }
-            count += __popc(m);
-            inexact = inexact || (hit && !exact);
         }
     }
-    const bool overflow = count > B.max_nbr;
-    if (overflow) count = B.max_nbr;
+    const int padded = (count + 7) & ~7;
+    const int k = count + lane;
+    if (k < padded && k < B.max_ent) out[k] = kBoxNoSlot | (1u << 30);  // padding: far, "pure"
+    const bool overflow = padded > B.max_ent;
     const bool any_inexact = __any_sync(kFullB, inexact);
     if (lane == 0) {
-        B.nnbr[gi] = count;
-        B.tflag[gi] |= any_inexact ? 2 : 0;
+        B.nent[ci] = overflow ? (B.max_ent & ~7) : padded;
+        if (any_inexact) B.cflag[ci] |= 2;
         if (overflow) atomicOr(&st.status[r], SCPS_FLAG_LIST_OVERFLOW);
     }
 }
 
-// The pairs of i lane `lane` with one staged group of 32 j slots: half-warp h
-// (lanes 16h .. 16h + 15, the group's 16 i atoms once more) takes staged slots
-// 16h .. 16h + 15; at iteration u lane l takes staged slot 16h + ((l + u) & 15) and
-// the j-force accumulators rotate one lane per iteration within the half-warp, so
-// after 16 lane l holds staged slot l's.
-// SELF: the group holds the tile's own clusters; a pair counts when its j slot
-// comes after its i slot. FAST: every i and j atom has the reference LJ
-// parameters, whose pair constants U are computed once.
-template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG, bool SELF, bool FAST>
-__device__ __forceinline__ void group_pairs(const BoxDev& B, const RunParams& P, const LJPair& U,
-                                            float4 xi, float2 li, int idi, unsigned long long em,
-                                            int si, int lane, const float4* sj, const float2* sp,
-                                            const int* sid, const int* sslot, float4& fi,
-                                            float& gx, float& gy, float& gz) {
-    const int h16 = lane & 16;
-    const int src = h16 | ((lane + 1) & 15);
-#pragma unroll 4
-    for (int u = 0; u < 16; ++u) {
-        const int k = h16 | ((lane + u) & 15);
-        const float4 xj = sj[k];
+// The 64 pairs of one chunk (8 list entries) with the 8 atoms of the i cluster, on a quarter
+// warp: lane l holds entry j_l; at iteration t it takes cluster atom (l + t) & 7, so the
+// i-force sums rotate one lane per iteration (after 8 lane l holds atom l's) while the j
+// force stays in the lane. Each pair term s (x_j - x_i) is rounded to 2^-13 units and summed
+// in 32-bit registers. FIRST: quarter 0 holds the cluster's own slots, whose pairs count
+// once (j slot after i slot). EXCL: exclusion masks (clusters holding chain atoms); MINIMG:
+// per-pair minimum image; FAST: every atom has the reference LJ parameters, whose pair
+// constants U are computed once. Returns false for the quarters where some |s| exceeds
+// pc.s_lim (their 32-bit sums could overflow; the caller redoes those chunks pair by pair).
+template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG, bool FAST, bool FIRST>
+__device__ __forceinline__ bool box_chunk(const BoxDev& B, const PairConst& pc, const LJPair& U,
+                                          const float4* sx, const float2* sp, const int* sid,
+                                          const unsigned long long* sem, float4 xj, float2 lj,
+                                          int idj, int lane, int& fix, int& fiy, int& fiz,
+                                          int& fjx, int& fjy, int& fjz, long long& e18) {
+    const int l8 = lane & 7, q = lane >> 3;
+    const int src = (lane & 24) | ((l8 + 1) & 7);
+    long long ech = 0;
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int ii = (l8 + t) & 7;
+        const float4 xi = sx[ii];
         float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         if (MINIMG) {
             dx = min_img(dx, B.L, B.invL);
@@ -385,151 +429,220 @@ __device__ __forceinline__ void group_pairs(const BoxDev& B, const RunParams& P,
             dz = min_img(dz, B.L, B.invL);
         }
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        bool ok = r2 < P.pc.rc2;
-        if (SELF) ok = ok && sslot[k] > si;
+        bool ok = r2 < pc.rc2;
+        if (FIRST) ok = ok && (q != 0 || l8 > ii);
         if (MINIMG || EXCL) {
-            const int idj = sid[k];
+            const int idi = sid[ii];
             if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
             if (EXCL) {
                 const unsigned dj = (unsigned)(idj - idi + kExclWindow);
-                if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((em >> dj) & 1ull);
+                if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((sem[ii] >> dj) & 1ull);
             }
         }
-        float ep = 0.f, sc;
+        float ep = 0.f, s;
         if (FAST) {
-            sc = pair_s_lj<ELEC, ENERGY>(r2, U, xi.w * xj.w, P.pc, &ep);
+            s = pair_s_lj<ELEC, ENERGY>(r2, U, xi.w * xj.w, pc, &ep);
         } else {
-            const float2 lj = sp[k];
-            sc = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, P.pc, &ep);
+            const float2 li = sp[ii];
+            s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &ep);
         }
-        sc = ok ? sc : 0.0f;
-        fi.x = fmaf(sc, dx, fi.x);
-        fi.y = fmaf(sc, dy, fi.y);
-        fi.z = fmaf(sc, dz, fi.z);
-        gx = fmaf(-sc, dx, gx);
-        gy = fmaf(-sc, dy, gy);
-        gz = fmaf(-sc, dz, gz);
-        if (ENERGY) fi.w += ok ? ep : 0.0f;
-        gx = __shfl_sync(kFullB, gx, src);
-        gy = __shfl_sync(kFullB, gy, src);
-        gz = __shfl_sync(kFullB, gz, src);
+        s = ok ? s : 0.0f;
+        bad = bad || !(fabsf(s) <= pc.s_lim);
+        if (ENERGY) bad = bad || (ok && !(fabsf(ep) < kPairEMax));
+        const float s13 = s * kPairScale;
+        const int tx = __float2int_rn(s13 * dx), ty = __float2int_rn(s13 * dy),
+                  tz = __float2int_rn(s13 * dz);
+        fix += tx;
+        fiy += ty;
+        fiz += tz;
+        fjx -= tx;
+        fjy -= ty;
+        fjz -= tz;
+        if (ENERGY) ech += ok ? __float2int_rn(ep * kPairEScale) : 0;
+        fix = __shfl_sync(kFullB, fix, src);
+        fiy = __shfl_sync(kFullB, fiy, src);
+        fiz = __shfl_sync(kFullB, fiz, src);
     }
+    const bool good = !((__ballot_sync(kFullB, bad) >> (8 * q)) & 0xffu);
+    if (ENERGY && good) e18 += ech;
+    return good;
 }
 
-// Non-bonded forces of i tile t on one warp, each pair once (Newton's third
-// law): lane l owns slot 32 t + l and adds up its force as i atom in registers.
-// The j slots come four listed clusters at a time (lane l stages slot l & 7 of
-// cluster l >> 3 of the group, moved by the entry's periodic shift unless
-// MINIMG, where every pair takes its own minimum image); each lane then adds the
-// j force of the slot it staged to that slot's fixed-point j force. Lists hold
-// the tile's own clusters first, then clusters of later tiles only. EXCL tests
-// the exclusion mask (tiles holding chain atoms); padding slots sit far away
-// from everything (MINIMG tests their ids instead).
+// Slow path of one chunk (the quarter of a chunk that failed the fast path): every pair
+// term, rounded to 2^-13 units as on the fast path, goes to both slots' 64-bit
+// accumulators, so the forces are the same integers on either path.
 template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG>
-__device__ __forceinline__ float4 box_tile_forces(const BoxDev& B, const TopoDev* __restrict__ topo,
-                                                  const RunParams& P, int r, int g, int lane,
-                                                  bool tile_pure, float4 (&sj)[32], float2 (&sp)[32],
-                                                  int (&sid)[32], int (&sslot)[32]) {
-    const size_t base = (size_t)r * B.np;
-    const int si = g * 16 + (lane & 15);  // both half-warps hold the group's 16 i slots
-    const float4 xi = B.pos[base + si];
-    const float2 li = B.par[base + si];
-    const int idi = B.id[base + si];
-    const unsigned long long em = (EXCL && idi >= 0 && idi < B.n_chain) ? topo->excl[idi] : 0ull;
-    const uint32_t* lst = B.nbr + ((size_t)r * 2 * B.nt + g) * B.max_nbr;
-    const int cnt = B.nnbr[(size_t)r * 2 * B.nt + g];
-    long long* jacc = B.facc + 3 * base;
-    const float2 ref = topo->lj[B.n_atoms - 1];
-    const LJPair U = lj_pair(ref.x + ref.x, ref.y * ref.y, P.pc);
-    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < cnt; q += 4) {
-        const int qe = q + (lane >> 3);
-        int sjl = -1;
-        bool cpure = true;
-        if (qe < cnt) {
-            const uint32_t code = lst[qe];
-            sjl = (int)(code & 0xffffffu) * 8 + (lane & 7);
-            cpure = (code >> 30) & 1u;
-            float4 p = B.pos[base + sjl];
-            if (!MINIMG) {
-                p.x = fmaf((float)((int)((code >> 24) & 3u) - 1), B.L, p.x);
-                p.y = fmaf((float)((int)((code >> 26) & 3u) - 1), B.L, p.y);
-                p.z = fmaf((float)((int)((code >> 28) & 3u) - 1), B.L, p.z);
-            }
-            sj[lane] = p;
-            sp[lane] = B.par[base + sjl];
-            sid[lane] = B.id[base + sjl];
-        } else {
-            sj[lane] = make_float4(1.0e18f, 0.f, 0.f, 0.f);  // beyond any cutoff
-            sp[lane] = make_float2(0.f, 0.f);
-            sid[lane] = -1;
+__device__ __noinline__ void box_chunk_slow(const BoxDev& B, const PairConst& pc, const float4* sx,
+                                            const float2* sp, const int* sid,
+                                            const unsigned long long* sem, float4 xj, float2 lj,
+                                            int idj, int sj, int si0, bool first, int lane,
+                                            unsigned long long* acc, long long& e18) {
+    const int l8 = lane & 7, q = lane >> 3;
+    for (int t = 0; t < 8; ++t) {
+        const int ii = (l8 + t) & 7;
+        const float4 xi = sx[ii];
+        float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        if (MINIMG) {
+            dx = min_img(dx, B.L, B.invL);
+            dy = min_img(dy, B.L, B.invL);
+            dz = min_img(dz, B.L, B.invL);
         }
-        sslot[lane] = sjl;
-        const bool gpure = __all_sync(kFullB, cpure);
-        __syncwarp();
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-        if (q == 0) {
-            group_pairs<ELEC, ENERGY, EXCL, MINIMG, true, false>(B, P, U, xi, li, idi, em, si, lane, sj, sp,
-                                                                 sid, sslot, fi, gx, gy, gz);
-        } else {
-            bool fast = false;
-            if constexpr (!EXCL && !MINIMG) fast = tile_pure && gpure;
-            if constexpr (!EXCL && !MINIMG) {
-                if (fast)
-                    group_pairs<ELEC, ENERGY, false, false, false, true>(B, P, U, xi, li, idi, em, si, lane,
-                                                                         sj, sp, sid, sslot, fi, gx, gy, gz);
-            }
-            if (!fast)
-                group_pairs<ELEC, ENERGY, EXCL, MINIMG, false, false>(B, P, U, xi, li, idi, em, si, lane,
-                                                                      sj, sp, sid, sslot, fi, gx, gy, gz);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool ok = r2 < pc.rc2;
+        if (first) ok = ok && (q != 0 || l8 > ii);
+        const int idi = sid[ii];
+        if (MINIMG) ok = ok && idj >= 0 && idi >= 0;
+        if (EXCL) {
+            const unsigned dj = (unsigned)(idj - idi + kExclWindow);
+            if (dj < 2u * kExclWindow && idj < B.n_chain) ok = ok && !((sem[ii] >> dj) & 1ull);
         }
-        if (sjl >= 0) {  // lane l holds the j force of the slot it staged
-            atomicAdd((unsigned long long*)&jacc[sjl], (unsigned long long)f2fix(gx));
-            atomicAdd((unsigned long long*)&jacc[B.np + sjl], (unsigned long long)f2fix(gy));
-            atomicAdd((unsigned long long*)&jacc[2 * B.np + sjl], (unsigned long long)f2fix(gz));
-        }
-        __syncwarp();
+        if (!ok) continue;
+        float ep = 0.f;
+        const float2 li = sp[ii];
+        const float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &ep);
+        const float s13 = s * kPairScale;
+        const long long tx = __float2ll_rn(s13 * dx) * 128, ty = __float2ll_rn(s13 * dy) * 128,
+                        tz = __float2ll_rn(s13 * dz) * 128;  // 2^-13 to 2^-20 units
+        const int si = si0 + ii;
+        const size_t np = (size_t)B.np;
+        atomicAdd(&acc[si], (unsigned long long)tx);
+        atomicAdd(&acc[np + si], (unsigned long long)ty);
+        atomicAdd(&acc[2 * np + si], (unsigned long long)tz);
+        atomicAdd(&acc[sj], (unsigned long long)(-tx));
+        atomicAdd(&acc[np + sj], (unsigned long long)(-ty));
+        atomicAdd(&acc[2 * np + sj], (unsigned long long)(-tz));
+        if (ENERGY) e18 += __float2ll_rn(ep * kPairEScale);
     }
-    // the two half-warps' shares of each i atom
-    fi.x += __shfl_xor_sync(kFullB, fi.x, 16);
-    fi.y += __shfl_xor_sync(kFullB, fi.y, 16);
-    fi.z += __shfl_xor_sync(kFullB, fi.z, 16);
-    fi.w += __shfl_xor_sync(kFullB, fi.w, 16);
-    return fi;
 }
 
-// Non-bonded forces: one warp per i tile, the variant chosen by the tile's flags.
+// Non-bonded forces of one 8-slot i cluster on one warp, each pair once (Newton's third
+// law): its list in chunks of 8 entries, four chunks at a time (quarter q takes chunk
+// 4 k + q). After a chunk each lane adds its j sums to the entry's slot (three 64-bit
+// atomics, in 2^-20 units) and its i sums to 64-bit registers, which go to the cluster's
+// slots at the end, summed over the quarters. Entries carry their periodic shift unless
+// MINIMG; padding entries sit far away from everything (MINIMG tests ids instead).
+template <int ELEC, bool ENERGY, bool EXCL, bool MINIMG>
+__device__ __forceinline__ void box_cluster_forces(const BoxDev& B, const TopoDev& tp,
+                                                   const RunParams& P, int r, int c, int lane,
+                                                   bool ipure, const float4* sx, const float2* sp,
+                                                   const int* sid, const unsigned long long* sem) {
+    const size_t base = (size_t)r * B.np;
+    const size_t ci = (size_t)r * 4 * B.nt + c;
+    const uint32_t* lst = B.ent + ci * B.max_ent;
+    const int n = B.nent[ci];
+    unsigned long long* acc = (unsigned long long*)(B.facc + 3 * base);
+    const float2 ref = tp.lj[B.n_atoms - 1];
+    const LJPair U = lj_pair(ref.x + ref.x, ref.y * ref.y, P.pc);
+    long long ax = 0, ay = 0, az = 0;  // this lane's share of cluster atom (lane & 7), 2^-13
+    long long e18 = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        const uint32_t e = k < n ? __ldg(lst + k) : (kBoxNoSlot | (1u << 30));
+        const int sj = (int)(e & kBoxNoSlot);
+        const bool real = sj != (int)kBoxNoSlot;
+        float4 xj = make_float4(1.0e18f, 0.f, 0.f, 0.f);  // beyond any cutoff
+        float2 lj = make_float2(0.f, 0.f);
+        int idj = -1;
+        if (real) {
+            xj = B.pos[base + sj];
+            if (!MINIMG) {
+                xj.x = fmaf((float)((int)((e >> 24) & 3u) - 1), B.L, xj.x);
+                xj.y = fmaf((float)((int)((e >> 26) & 3u) - 1), B.L, xj.y);
+                xj.z = fmaf((float)((int)((e >> 28) & 3u) - 1), B.L, xj.z);
+            }
+            lj = B.par[base + sj];
+            idj = B.id[base + sj];
+        }
+        bool fast = false;
+        if constexpr (!EXCL && !MINIMG) fast = __all_sync(kFullB, ipure && ((e >> 30) & 1u));
+        int fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+        bool good;
+        if (k0 == 0) {
+            if (fast)
+                good = box_chunk<ELEC, ENERGY, false, false, true, true>(
+                    B, P.pc, U, sx, sp, sid, sem, xj, lj, idj, lane, fix, fiy, fiz, fjx, fjy, fjz, e18);
+            else
+                good = box_chunk<ELEC, ENERGY, EXCL, MINIMG, false, true>(
+                    B, P.pc, U, sx, sp, sid, sem, xj, lj, idj, lane, fix, fiy, fiz, fjx, fjy, fjz, e18);
+        } else {
+            if (fast)
+                good = box_chunk<ELEC, ENERGY, false, false, true, false>(
+                    B, P.pc, U, sx, sp, sid, sem, xj, lj, idj, lane, fix, fiy, fiz, fjx, fjy, fjz, e18);
+            else
+                good = box_chunk<ELEC, ENERGY, EXCL, MINIMG, false, false>(
+                    B, P.pc, U, sx, sp, sid, sem, xj, lj, idj, lane, fix, fiy, fiz, fjx, fjy, fjz, e18);
+        }
+        if (good) {
+            ax += fix;
+            ay += fiy;
+            az += fiz;
+            if (real) {
+                atomicAdd(&acc[sj], (unsigned long long)((long long)fjx * 128));
+                atomicAdd(&acc[B.np + sj], (unsigned long long)((long long)fjy * 128));
+                atomicAdd(&acc[2 * (size_t)B.np + sj], (unsigned long long)((long long)fjz * 128));
+            }
+        } else {
+            box_chunk_slow<ELEC, ENERGY, EXCL, MINIMG>(B, P.pc, sx, sp, sid, sem, xj, lj, idj, sj,
+                                                      8 * c, k0 == 0, lane, acc, e18);
+        }
+    }
+    // the four quarters' shares of each cluster atom
+    ax += __shfl_xor_sync(kFullB, ax, 8);
+    ay += __shfl_xor_sync(kFullB, ay, 8);
+    az += __shfl_xor_sync(kFullB, az, 8);
+    ax += __shfl_xor_sync(kFullB, ax, 16);
+    ay += __shfl_xor_sync(kFullB, ay, 16);
+    az += __shfl_xor_sync(kFullB, az, 16);
+    if (lane < 8 && sid[lane] >= 0) {
+        const int si = 8 * c + lane;
+        atomicAdd(&acc[si], (unsigned long long)(ax * 128));
+        atomicAdd(&acc[B.np + si], (unsigned long long)(ay * 128));
+        atomicAdd(&acc[2 * (size_t)B.np + si], (unsigned long long)(az * 128));
+    }
+    if (ENERGY) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e18 += __shfl_xor_sync(kFullB, e18, o);
+        if (lane == 0 && e18 != 0) atomicAdd((unsigned long long*)&B.epair[r], (unsigned long long)e18);
+    }
+}
+
+// Non-bonded forces: one warp per 8-slot i cluster, the variant chosen by its flags.
 template <int ELEC, bool ENERGY>
-__global__ void __launch_bounds__(128) k_box_pairs(BoxDev B, const TopoDev* __restrict__ topo,
+__global__ void __launch_bounds__(128, 8) k_box_pairs(BoxDev B, const TopoDev* __restrict__ topo,
                                                    RunParams P, int r0) {
-    __shared__ float4 sj[4][32];
-    __shared__ float2 sp[4][32];
-    __shared__ int sid[4][32];
-    __shared__ int sslot[4][32];
+    __shared__ float4 sx[4][8];
+    __shared__ float2 sp[4][8];
+    __shared__ int sid[4][8];
+    __shared__ unsigned long long sem[4][8];
     const int r = blockIdx.y + r0;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x * 4 + w;  // i group: 16 slots, half of a tile
-    if (g >= 2 * B.nt) return;
-    const int fl = B.tflag[(size_t)r * 2 * B.nt + g];
-    const bool pure = (fl & 4) != 0;
-    float4 f;
-    switch (fl & 3) {
-        case 0: f = box_tile_forces<ELEC, ENERGY, false, false>(B, topo, P, r, g, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
-        case 1: f = box_tile_forces<ELEC, ENERGY, true, false>(B, topo, P, r, g, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
-        default: f = box_tile_forces<ELEC, ENERGY, true, true>(B, topo, P, r, g, lane, pure, sj[w], sp[w], sid[w], sslot[w]); break;
+    const int c = blockIdx.x * 4 + w;
+    if (c >= 4 * B.nt) return;
+    const TopoDev& tp = *topo;
+    if (lane < 8) {
+        const size_t sl = (size_t)r * B.np + 8 * c + lane;
+        sx[w][lane] = B.pos[sl];
+        sp[w][lane] = B.par[sl];
+        const int a = B.id[sl];
+        sid[w][lane] = a;
+        sem[w][lane] = (a >= 0 && a < B.n_chain) ? tp.excl[a] : 0ull;
     }
-    if (lane < 16) B.fnb[(size_t)r * B.np + g * 16 + lane] = f;
+    __syncwarp();
+    const int fl = B.cflag[(size_t)r * 4 * B.nt + c];
+    const bool pure = (fl & 4) != 0;
+    switch (fl & 3) {
+        case 0: box_cluster_forces<ELEC, ENERGY, false, false>(B, tp, P, r, c, lane, pure, sx[w], sp[w], sid[w], sem[w]); break;
+        case 1: box_cluster_forces<ELEC, ENERGY, true, false>(B, tp, P, r, c, lane, pure, sx[w], sp[w], sid[w], sem[w]); break;
+        default: box_cluster_forces<ELEC, ENERGY, true, true>(B, tp, P, r, c, lane, pure, sx[w], sp[w], sid[w], sem[w]); break;
+    }
 }
 
-// Total non-bonded force on slot s of replica r: its i part plus its fixed-point
-// j part, which is cleared for the next evaluation.
+// Total non-bonded force on slot s of replica r (fixed point), which is cleared for the
+// next evaluation.
 __device__ __forceinline__ float4 take_nb_force(const BoxDev& B, int r, int s) {
     const size_t base = (size_t)r * B.np;
     long long* acc = B.facc + 3 * base;
-    float4 f = B.fnb[base + s];
-    f.x += fix2f(acc[s]);
-    f.y += fix2f(acc[B.np + s]);
-    f.z += fix2f(acc[2 * B.np + s]);
+    float4 f = make_float4(fix2f(acc[s]), fix2f(acc[B.np + s]), fix2f(acc[2 * B.np + s]), 0.f);
     acc[s] = 0;
     acc[B.np + s] = 0;
     acc[2 * B.np + s] = 0;
@@ -769,25 +882,19 @@ __global__ void k_box_frame(BoxDev B, StateDev st, RunParams P, long long frame_
     fr[2] = x.z;
 }
 
-// Frame scalars; the potential energy is the sum of the per-slot shares in slot order.
-__global__ void k_box_frame_scalars(BoxDev B, StateDev st, RunParams P) {
-    const int r = blockIdx.x;
-    __shared__ double red[256];
-    double e = 0.0;
-    for (int s = threadIdx.x; s < B.np; s += blockDim.x) e += (double)B.fnb[(size_t)r * B.np + s].w;
-    red[threadIdx.x] = e;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
-        const long long slot = st.n_saved[r] % P.max_frames;
-        const long long fi = (long long)r * P.max_frames + slot;
-        st.fz[fi] = st.z[r];
-        st.fzm[fi] = st.zm[r];
-        st.fe[fi] = t + B.eb[r];
-        st.fT[fi] = st.T[r];
-        st.n_saved[r] += 1;
-    }
+// Frame scalars; the potential energy is the fixed-point pair energy (2^-18 units, cleared
+// here) plus the bonded energy.
+__global__ void k_box_frame_scalars(BoxDev B, StateDev st, RunParams P, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const long long slot = st.n_saved[r] % P.max_frames;
+    const long long fi = (long long)r * P.max_frames + slot;
+    st.fz[fi] = st.z[r];
+    st.fzm[fi] = st.zm[r];
+    st.fe[fi] = (double)B.epair[r] * 3.814697265625e-06 + B.eb[r];  // 2^-18
+    st.fT[fi] = st.T[r];
+    st.n_saved[r] += 1;
+    B.epair[r] = 0;
 }
 
 __global__ void k_box_step_count(StateDev st, int R, long long k) {
@@ -812,7 +919,7 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
     k_box_scatter<<<dim3((B.n_atoms + 255) / 256, nr), 256, 0, s>>>(B, r0);
     k_box_keyorder<<<dim3((B.ncol * B.ncol * B.nz + 255) / 256, nr), 256, 0, s>>>(B, r0);
     const dim3 gt((B.nt + 3) / 4, nr);       // one warp per tile
-    const dim3 gg((2 * B.nt + 3) / 4, nr);   // one warp per i group (tile half)
+    const dim3 gg((4 * B.nt + 3) / 4, nr);   // one warp per 8-slot i cluster
     k_box_subsort<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_tiles<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_list<<<gg, 128, 0, s>>>(B, st, r0);
@@ -878,7 +985,7 @@ cudaError_t box_run(const BoxDev& B, const TopoDev* topo, const StateDev& st, co
         if (e != cudaSuccess) return e;
         if (save) k_box_frame<<<ga, 256, 0, s>>>(B, st, P, frame_atoms);
         k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step, 1, k < n_steps ? 1 : 0);
-        if (save) k_box_frame_scalars<<<R, 256, 0, s>>>(B, st, P);
+        if (save) k_box_frame_scalars<<<(R + 127) / 128, 128, 0, s>>>(B, st, P, R);
     }
     k_box_step_count<<<(R + 127) / 128, 128, 0, s>>>(st, R, n_steps);
     return cudaGetLastError();
@@ -931,17 +1038,9 @@ __global__ void k_box_store_forces(BoxDev B, int r, float* __restrict__ F) {
 }
 
 __global__ void k_box_store_energy(BoxDev B, StateDev st, int r, double* U, double* Z) {
-    __shared__ double red[256];
-    double e = 0.0;
-    for (int s = threadIdx.x; s < B.np; s += blockDim.x) e += (double)B.fnb[(size_t)r * B.np + s].w;
-    red[threadIdx.x] = e;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
-        *U = t + B.eb[r];
-        if (Z) *Z = st.z[r];
-    }
+    *U = (double)B.epair[r] * 3.814697265625e-06 + B.eb[r];  // 2^-18
+    B.epair[r] = 0;
+    if (Z) *Z = st.z[r];
 }
 
 cudaError_t box_energy_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st,
@@ -952,7 +1051,7 @@ cudaError_t box_energy_forces(const BoxDev& B, const TopoDev* topo, const StateD
     cudaError_t e = box_eval(B, topo, st, P, r_eval, 1, elec, ncon_max, true, 0, 0, 0, s);
     if (e != cudaSuccess) return e;
     k_box_store_forces<<<g, 256, 0, s>>>(B, r_eval, F);
-    k_box_store_energy<<<1, 256, 0, s>>>(B, st, r_eval, U, Z);
+    k_box_store_energy<<<1, 1, 0, s>>>(B, st, r_eval, U, Z);
     return cudaGetLastError();
 }
 

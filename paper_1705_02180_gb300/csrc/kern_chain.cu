@@ -48,11 +48,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kChunk = 32;    // contacts / bonds / angles per work item (one per lane)
 constexpr int kTubeItem = 8;  // contacts per work item of the contact-map tube passes
-constexpr float kPairScale = 8192.0f;     // 2^13: integer units of the pair force terms
-constexpr float kPairEScale = 262144.0f;  // 2^18: integer units of the pair energies (finer:
-                                          // the many small energies near r_c share one sign,
-                                          // so their rounding does not average out)
-constexpr float kPairEMax = 8000.0f;      // larger pair energies take the slow path
 
 // Shared-memory arrays of one CTA. Atom slots: nta real or padding slots plus 8 sentinel
 // slots (a block far from everything) that absorb the padding of list chunks.
@@ -139,15 +134,6 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// Fixed-point value (2^-20 units) of a force term; a non-finite term or one above
-// 1e9 kJ/mol/nm raises the force-range flag (the replica is then frozen).
-__device__ __forceinline__ long long f2fix_checked(float v, int* flag) {
-    if (!(fabsf(v) < 262144.0f)) {
-        if (!(fabsf(v) <= 1.0e9f)) atomicOr(flag, SCPS_FLAG_FORCE_RANGE);
-    }
-    return f2fix(v);
-}
-
 // Adds a 2^-20 fixed-point value to a (integer part, fraction part) accumulator.
 __device__ __forceinline__ void red_fix20(int* H, unsigned* L, int k, long long v) {
     atomicAdd(&H[k], (int)(v >> 20));
@@ -160,12 +146,23 @@ __device__ __forceinline__ void red_fix13(int* H, unsigned* L, int k, int v) {
     atomicAdd(&L[k], ((unsigned)v & 0x1fffu) << 7);
 }
 
-__device__ __forceinline__ void add_fix(const Shared& sm, int* H, unsigned* L, int i, float fx,
-                                        float fy, float fz) {
+// Slow path of a pair term: s13 d (2^-13 units, rounded exactly as on the fast path, so the
+// sums are the same integers whichever path a pair takes) to atom i and its negative to atom
+// j, in 64-bit; a non-finite term or one above 1e9 kJ/mol/nm raises the force-range flag.
+__device__ __forceinline__ void add_pair13(const Shared& sm, int* H, unsigned* L, int i, int j,
+                                           float s13, float dx, float dy, float dz) {
+    const float tx = s13 * dx, ty = s13 * dy, tz = s13 * dz;
+    const float lim = 8.192e12f;  // 1e9 in 2^-13 units
+    if (!(fabsf(tx) <= lim && fabsf(ty) <= lim && fabsf(tz) <= lim)) atomicOr(sm.flag, SCPS_FLAG_FORCE_RANGE);
+    const long long qx = __float2ll_rn(tx) * 128, qy = __float2ll_rn(ty) * 128,
+                    qz = __float2ll_rn(tz) * 128;  // 2^-13 to 2^-20 units
     const int s = sm.na8;
-    red_fix20(H, L, i, f2fix_checked(fx, sm.flag));
-    red_fix20(H, L, s + i, f2fix_checked(fy, sm.flag));
-    red_fix20(H, L, 2 * s + i, f2fix_checked(fz, sm.flag));
+    red_fix20(H, L, i, qx);
+    red_fix20(H, L, s + i, qy);
+    red_fix20(H, L, 2 * s + i, qz);
+    red_fix20(H, L, j, -qx);
+    red_fix20(H, L, s + j, -qy);
+    red_fix20(H, L, 2 * s + j, -qz);
 }
 
 // Bonded terms: integer multiples of 2^-13 kJ mol^-1 nm^-1 (one conversion each); a term
@@ -285,12 +282,13 @@ __device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsign
     return true;
 }
 
-// Slow path of an item: every pair term goes to both atoms in 2^-20 fixed point with
-// the range check (a force beyond 1e9 kJ/mol/nm or a non-finite one freezes the replica).
+// Slow path of an item: every pair term goes to both atoms in 64-bit fixed point (rounded
+// per pair as on the fast path) with the range check (a force beyond 1e9 kJ/mol/nm or a
+// non-finite one freezes the replica).
 template <int ELEC, bool ENERGY>
 __device__ __noinline__ void pair_item_slow(const Shared& sm, int* FH, unsigned* FL,
                                             const TopoDev& tp, const PairConst& pc, int I, int j,
-                                            int lane, long long& e20) {
+                                            int lane, long long& e18) {
     const int l8 = lane & 7;
     const float4 xj = sm.xq[j];
     const float2 lj = sm.lj[j];
@@ -306,9 +304,8 @@ __device__ __noinline__ void pair_item_slow(const Shared& sm, int* FH, unsigned*
         if (!ok) continue;
         float e = 0.f;
         const float s = pair_s<ELEC, ENERGY>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, &e);
-        add_fix(sm, FH, FL, i, s * dx, s * dy, s * dz);
-        add_fix(sm, FH, FL, j, -s * dx, -s * dy, -s * dz);
-        if (ENERGY) e20 += f2fix(e);
+        add_pair13(sm, FH, FL, i, j, s * kPairScale, dx, dy, dz);
+        if (ENERGY) e18 += __float2ll_rn(e * kPairEScale);
     }
 }
 
@@ -316,8 +313,7 @@ __device__ __noinline__ void pair_item_slow(const Shared& sm, int* FH, unsigned*
 template <int ELEC, bool ENERGY>
 __device__ __forceinline__ void pair_batch(const Shared& sm, int* FH, unsigned* FL, const TopoDev& tp,
                                            const PairConst& pc, const ListDev& L, int n_items,
-                                           bool cached, int batch, int lane, long long& e18,
-                                           long long& e20) {
+                                           bool cached, int batch, int lane, long long& e18) {
     const int it = 4 * batch + (lane >> 3);
     int I = 0, j = sm.nta;  // idle quarter: block 0 against the far sentinel slot (zero terms)
     bool near = false;
@@ -343,7 +339,7 @@ __device__ __forceinline__ void pair_batch(const Shared& sm, int* FH, unsigned* 
         done = pair_item_fast<ELEC, ENERGY, true>(sm, FH, FL, tp, pc, I, j, xm, lane, e18);
     else
         done = pair_item_fast<ELEC, ENERGY, false>(sm, FH, FL, tp, pc, I, j, xm, lane, e18);
-    if (!done) pair_item_slow<ELEC, ENERGY>(sm, FH, FL, tp, pc, I, j, lane, e20);
+    if (!done) pair_item_slow<ELEC, ENERGY>(sm, FH, FL, tp, pc, I, j, lane, e18);
 }
 
 // The 28 pairs inside block I on a quarter warp: at round k = 1..4 lane l takes the pair
@@ -351,8 +347,7 @@ __device__ __forceinline__ void pair_batch(const Shared& sm, int* FH, unsigned* 
 // atom's accumulators rotate one lane per round and return home with one exchange.
 template <int ELEC, bool ENERGY>
 __device__ __forceinline__ void diag_item(const Shared& sm, int* FH, unsigned* FL, const TopoDev& tp,
-                                          const PairConst& pc, int I, int lane, long long& e18,
-                                          long long& e20) {
+                                          const PairConst& pc, int I, int lane, long long& e18) {
     const int l8 = lane & 7, q = lane >> 3;
     const int src = (lane & 24) | ((l8 + 1) & 7);
     const int i = 8 * I + l8;
@@ -412,9 +407,8 @@ __device__ __forceinline__ void diag_item(const Shared& sm, int* FH, unsigned* F
         if (!(r2 < pc.rc2 && (k < 4 || l8 < 4) && !((em >> (b - i + kExclWindow)) & 1ull))) continue;
         float e = 0.f;
         const float s = pair_s<ELEC, ENERGY>(r2, la.x + lb.x, la.y * lb.y, xa.w * xb.w, pc, &e);
-        add_fix(sm, FH, FL, i, s * dx, s * dy, s * dz);
-        add_fix(sm, FH, FL, b, -s * dx, -s * dy, -s * dz);
-        if (ENERGY) e20 += f2fix(e);
+        add_pair13(sm, FH, FL, i, b, s * kPairScale, dx, dy, dz);
+        if (ENERGY) e18 += __float2ll_rn(e * kPairEScale);
     }
 }
 
@@ -1017,8 +1011,7 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
                 if (r < n_pb - m_mix) kp = m_mix + r; else kc = m_mix + r - (n_pb - m_mix);
             }
             if (kp >= 0) {
-                pair_batch<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, L, sc.n_items, sc.cached, kp, lane, e18,
-                                         e20);
+                pair_batch<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, L, sc.n_items, sc.cached, kp, lane, e18);
             } else {
                 const int g = kc * CL + rank;
                 if (tube) {
@@ -1031,7 +1024,7 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         } else if (k < e_diag) {
             const int d = 4 * (k - e_pair) + (lane >> 3);
             const int I = d < sc.n_diag ? d * CL + rank : (sm.nta >> 3);
-            diag_item<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, I, lane, e18, e20);
+            diag_item<ELEC, ENERGY>(sm, FH, FL, tp, P.pc, I, lane, e18);
         } else if (k < e_bond) {
             const int q = ((k - e_diag) * CL + rank) * kChunk + lane;
             if (q < tp.n_bonds) {

@@ -618,7 +618,17 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         B.nz = 8192 / (B.ncol * B.ncol);
         B.nt = (t.n_atoms + kTile - 1) / kTile + B.ncol * B.ncol;
         B.np = B.nt * kTile;
-        B.max_nbr = std::min(4 * B.nt, 1024);
+        // pair-list capacity per 8-slot cluster: its own slots and the atoms within r_c +
+        // 0.75 nm of its centre at the mean density (the union of the cluster's atoms' list
+        // spheres for skins up to the tuner's 0.2 nm, with room for fluctuations). A list
+        // holds only later clusters, but for the clusters of the first columns in slot
+        // order that is nearly the whole sphere.
+        {
+            const double rho = t.n_atoms / (d->box * d->box * d->box);
+            const double rr = d->cutoff + 0.75;
+            const double full = rho * 4.18879020478639 * rr * rr * rr;
+            B.max_ent = std::min(1 << 14, 8 + 8 * (int)std::ceil(full / 8.0));
+        }
         B.rebuild_every = d->rebuild_every > 0 ? d->rebuild_every : 20;
         B.L = (float)d->box;
         B.invL = (float)(1.0 / d->box);
@@ -637,9 +647,10 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.par, np);
         BALLOC(B.id, np);
         BALLOC(B.id2, np);
-        BALLOC(B.fnb, np);
         BALLOC(B.facc, 3 * np);
-        if (cudaMemset(B.facc, 0, sizeof(long long) * 3 * np) != cudaSuccess)
+        BALLOC(B.epair, Rs);
+        if (cudaMemset(B.facc, 0, sizeof(long long) * 3 * np) != cudaSuccess ||
+            cudaMemset(B.epair, 0, sizeof(long long) * Rs) != cudaSuccess)
             return bail(fail(SCPS_ERR_CUDA, "cudaMemset failed"));
         BALLOC(B.pos2, np);
         BALLOC(B.vel2, np);
@@ -648,13 +659,11 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.colinfo, (size_t)Rs * 2 * 257);
         BALLOC(B.pos_ref, np);
         BALLOC(B.slot_of, (size_t)Rs * B.n_atoms);
-        BALLOC(B.tlo, (size_t)Rs * 2 * B.nt);  // per i group (tile half)
-        BALLOC(B.thi, (size_t)Rs * 2 * B.nt);
-        BALLOC(B.clo, (size_t)Rs * 4 * B.nt);
+        BALLOC(B.clo, (size_t)Rs * 4 * B.nt);  // per 8-slot cluster
         BALLOC(B.chi, (size_t)Rs * 4 * B.nt);
-        BALLOC(B.nbr, (size_t)Rs * 2 * B.nt * B.max_nbr);
-        BALLOC(B.nnbr, (size_t)Rs * 2 * B.nt);
-        BALLOC(B.tflag, (size_t)Rs * 2 * B.nt);
+        BALLOC(B.ent, (size_t)Rs * 4 * B.nt * B.max_ent);
+        BALLOC(B.nent, (size_t)Rs * 4 * B.nt);
+        BALLOC(B.cflag, (size_t)Rs * 4 * B.nt);
         BALLOC(B.need, Rs);
         BALLOC(B.since, Rs);
         BALLOC(B.maxd2, Rs);
@@ -1317,6 +1326,15 @@ int scps_get_info(const scps_system* s, scps_info* info) {
         }
         if (builds > 0.0 && s->last_launch_steps > 0)
             info->steps_per_list_build = (double)s->last_launch_steps * (double)ps.size() / builds;
+    }
+    if (s->is_box) {  // 64 pair slots per chunk of 8 entries, from the lists built last
+        SCPS_CU(cudaDeviceSynchronize());
+        const size_t ncl = (size_t)s->d.n_replicas * 4 * s->box.nt;
+        std::vector<int> ne(ncl);
+        SCPS_CU(cudaMemcpy(ne.data(), s->box.nent, sizeof(int) * ncl, cudaMemcpyDeviceToHost));
+        long long slots = 0;
+        for (int v : ne) slots += 8ll * v;
+        info->pair_checks_per_step = slots;
     }
     return SCPS_OK;
 }

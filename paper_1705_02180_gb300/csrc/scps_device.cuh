@@ -61,6 +61,13 @@ __device__ __forceinline__ double2 normals2_f64(uint32_t a, uint32_t b) {
 // ---------------------------------------------------------------------------
 constexpr float kFixScale = 1048576.0f;         // 2^20
 constexpr float kFixInv = 9.5367431640625e-07f;  // 2^-20
+// Non-bonded pair terms: each s (x_j - x_i) is rounded to 2^-13 units (summed in 32-bit
+// registers over a few pairs, then moved to the 2^-20 accumulators), each pair energy to
+// 2^-18 units (finer: the many small energies near r_c share one sign, so their rounding
+// does not average out); larger pair energies take the 64-bit path.
+constexpr float kPairScale = 8192.0f;     // 2^13
+constexpr float kPairEScale = 262144.0f;  // 2^18
+constexpr float kPairEMax = 8000.0f;
 
 __device__ __forceinline__ long long f2fix(float v) {
     const float a = v * 16.0f;  // v * 2^4: the part above 2^-16 of the 2^-20 grid

@@ -132,7 +132,7 @@ struct RunParams {
 
 // Periodic-box state of all replicas (slot arrays are [replica][np], in tile order).
 struct BoxDev {
-    int n_atoms, n_chain, np, nt, max_nbr, rebuild_every;
+    int n_atoms, n_chain, np, nt, max_ent, rebuild_every;
     int ncol, nz;     // ncol x ncol columns in (x, y), nz bins in z per column
     float L, invL, rlist2, skin2_quarter;
     float4* pos;      // (x, y, z, qs)
@@ -140,9 +140,10 @@ struct BoxDev {
     float2* par;      // (sigma/2, sqrt(24 eps))
     int* id;          // atom id of each slot, -1 for padding
     int* id2;         // sort buffer of id
-    float4* fnb;      // non-bonded force on the slot as i atom (w: energy share)
-    long long* facc;  // [replica][3][np] non-bonded force on the slot as j atom, fixed point
-                      // 2^-20 (order-free sums; cleared by whoever consumes it)
+    long long* facc;  // [replica][3][np] non-bonded force on the slot, fixed point 2^-20
+                      // (order-free sums; cleared by whoever consumes it)
+    long long* epair; // [replica] pair energy of energy evaluations, fixed point 2^-18
+                      // (cleared by whoever consumes it)
     float4* pos2;     // sort buffers
     float4* vel2;
     int* slot_of;     // [replica][n_atoms]
@@ -150,21 +151,25 @@ struct BoxDev {
     int* hist;        // [replica][8192] key counts, then running cursors (rebuild)
     int* colinfo;     // [replica][2][257] first compact position and first tile per column
     float4* pos_ref;  // positions at the last rebuild
-    float4* tlo;      // [replica][2 nt] boxes of the 16-slot i groups (tile halves)
-    float4* thi;
-    float4* clo;      // [replica][4 nt] boxes of the 8-slot j clusters (clo.w: 1 = reference LJ only)
+    float4* clo;      // [replica][4 nt] boxes of the 8-slot clusters (clo.w: 1 = reference LJ only)
     float4* chi;
-    uint32_t* nbr;    // [replica][2 nt][max_nbr] per i group: j cluster | periodic shift << 24 (2 bits per
-                      // axis) | 1 << 30 when the cluster holds only reference-LJ atoms
-    int* nnbr;        // [replica][2 nt]
-    int* tflag;       // [replica][2 nt] per i group: 1 = group holds chain atoms, 2 = a listed cluster needs
-                      // the minimum image per pair (its shift is not the same for all pairs),
-                      // 4 = all its atoms have the reference LJ parameters (the last atom's)
+    uint32_t* ent;    // [replica][4 nt][max_ent] pair list of each 8-slot i cluster c: its own 8
+                      // slots, then the slots j of clusters after c within r_list of some atom
+                      // of c, ascending, padded to a multiple of 8 with kBoxNoSlot; an entry is
+                      // j | (periodic shift + 1 per axis, 2 bits each) << 24 | 1 << 30 when j
+                      // has the reference LJ parameters
+    int* nent;        // [replica][4 nt] entries of each cluster (a multiple of 8)
+    int* cflag;       // [replica][4 nt] per i cluster: 1 = it holds chain atoms, 2 = some entry
+                      // needs the per-pair minimum image (the entry's shift may not hold for
+                      // every pair until the next rebuild), 4 = all its atoms have the
+                      // reference LJ parameters (the last atom's)
     int* need;        // [replica] rebuild flag
     int* since;       // [replica] evaluations since the last rebuild
     unsigned* maxd2;  // [replica] largest squared displacement since then (float bits)
     float4* fch;      // [replica][n_chain] bonded + bias force on chain atoms
     double* eb;       // [replica] bonded energy (save steps)
 };
+
+constexpr uint32_t kBoxNoSlot = 0x7fffffu;  // padding entry of a box pair list
 
 }  // namespace scps

@@ -154,3 +154,19 @@ def test_box_autotune_restores_state_and_keeps_the_trajectory(torch_cuda, box):
         s.close()
     assert np.abs(runs[0]["x"] - runs[1]["x"]).max() < 1e-4
     assert np.array_equal(runs[0]["step"], runs[1]["step"])
+
+
+def test_box_list_is_tight_and_complete(torch_cuda, box):
+    # the atom-level lists of the 8-slot clusters: every pair inside the cutoff is taken (the
+    # forces match the oracle's brute force above) and the evaluated pair slots stay within
+    # 3.5 times the non-excluded pairs inside the cutoff (skin 0.1 nm)
+    import paper_1705_02180_gb300 as pkg
+    from scipy.spatial import cKDTree
+    b = box
+    s = make(pkg, b, 1, skin=0.1)
+    s.step(1)
+    slots = s.info()["pair_checks_per_step"]
+    x = s.get_state()["x"] % b.box
+    n_in = len(cKDTree(x, boxsize=b.box).query_pairs(1.0)) - len(b.chain.exclusions)
+    assert n_in < slots < 3.5 * n_in
+    s.close()
