@@ -243,7 +243,10 @@ int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const flo
                        double* U, float* F, double* z, void* stream);
 
 /* Hessian-vector products H(X_t) V_t of the physical potential for n_frames
- * frames (device float arrays n_frames x n_atoms x 3). Stream-ordered. */
+ * frames (device float arrays n_frames x n_atoms x 3). Stream-ordered. The gradient
+ * of sum_t |grad U(X_t)|^2, a term of the Onsager-Machlup action of Eq. (SOM), is
+ * sum_t 2 H(X_t) grad U(X_t). Open-boundary chains only: a periodic-box system gets
+ * SCPS_ERR_UNSUPPORTED. Pair terms are summed per item in FP32, then in fixed point. */
 int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, const float* V,
              float* HV, void* stream);
 

@@ -322,68 +322,102 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
     if (ivalid) {
         const float cx = 0.5f * (al.x + ah.x), cy = 0.5f * (al.y + ah.y), cz = 0.5f * (al.z + ah.z);
         const float hx = 0.5f * (ah.x - al.x), hy = 0.5f * (ah.y - al.y), hz = 0.5f * (ah.z - al.z);
-        for (int j0 = c + 1; j0 < ncl; j0 += 32) {
-            const int jc = j0 + lane;
-            bool hit = false;
-            uint32_t code = 0;
-            if (jc < ncl) {
-                const float4 bl = B.clo[(size_t)r * ncl + jc], bh = B.chi[(size_t)r * ncl + jc];
-                if (bl.x <= bh.x) {  // the cluster holds atoms
-                    const float dx = 0.5f * (bl.x + bh.x) - cx, dy = 0.5f * (bl.y + bh.y) - cy,
-                                dz = 0.5f * (bl.z + bh.z) - cz;
-                    const float sx = -rintf(dx * B.invL), sy = -rintf(dy * B.invL),
-                                sz = -rintf(dz * B.invL);
-                    const float ex = fabsf(fmaf(sx, B.L, dx)), ey = fabsf(fmaf(sy, B.L, dy)),
-                                ez = fabsf(fmaf(sz, B.L, dz));
-                    const float wx = hx + 0.5f * (bh.x - bl.x), wy = hy + 0.5f * (bh.y - bl.y),
-                                wz = hz + 0.5f * (bh.z - bl.z);
-                    // lower bound of any periodic-image distance between the two boxes
-                    const float gx = fmaxf(0.f, ex - wx), gy = fmaxf(0.f, ey - wy),
-                                gz = fmaxf(0.f, ez - wz);
-                    hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
-                    code = ((uint32_t)(sx + 1.f) << 24) | ((uint32_t)(sy + 1.f) << 26) |
-                           ((uint32_t)(sz + 1.f) << 28) | (bl.w != 0.f ? 1u << 30 : 0u);
-                }
-            }
-            unsigned m = __ballot_sync(kFullB, hit);
-            while (m) {  // four hit clusters at a time: lane 8 k + a takes atom a of the k-th
-                const int nh = min(__popc(m), 4);
-                unsigned mm = m;
-                for (int k = 0; k < q; ++k) mm &= mm - 1u;
-                const int src = __ffs(mm) - 1;  // lane of this quarter's hit cluster (-1: none)
-                const uint32_t hcode = __shfl_sync(kFullB, code, src & 31);
-                for (int k = 0; k < nh; ++k) m &= m - 1u;
-                bool keep = false;
-                uint32_t e = 0;
-                if (q < nh) {
-                    const int sj = 8 * (j0 + src) + l8;
-                    if (B.id[base + sj] >= 0) {
-                        const float4 xj = B.pos[base + sj];
-                        const float ox = (float)((int)((hcode >> 24) & 3u) - 1) * B.L,
-                                    oy = (float)((int)((hcode >> 26) & 3u) - 1) * B.L,
-                                    oz = (float)((int)((hcode >> 28) & 3u) - 1) * B.L;
-                        float d2 = 3.0e38f, dm = 0.f;
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) {
-                            if (!((ivalid >> t) & 1u)) continue;
-                            const float4 a = sxi[w][t];
-                            const float dx = xj.x - a.x, dy = xj.y - a.y, dz = xj.z - a.z;
-                            const float mx = min_img(dx, B.L, B.invL), my = min_img(dy, B.L, B.invL),
-                                        mz = min_img(dz, B.L, B.invL);
-                            d2 = fminf(d2, fmaf(mx, mx, fmaf(my, my, mz * mz)));
-                            dm = fmaxf(dm, fmaxf(fabsf(dx + ox), fmaxf(fabsf(dy + oy), fabsf(dz + oz))));
-                        }
-                        keep = d2 < B.rlist2;
-                        inexact = inexact || (keep && !(dm < room));
-                        e = (uint32_t)sj | (hcode & 0x7f000000u);
+        // candidate columns: an atom within r_list of c lies at most `reach` columns away in x
+        // and in y (periodically); columns in ascending order keep the entries ascending
+        const int* col_tile = B.colinfo + (size_t)r * 2 * (kMaxCols + 1) + kMaxCols + 1;
+        const float colw = B.L / (float)B.ncol;
+        const int reach = (int)ceilf(sqrtf(B.rlist2) / colw);
+        const int ncols = B.ncol * B.ncol;
+        int lo = 0, hi = ncols;  // c's column: the last one whose first tile is <= c's tile
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (col_tile[mid] <= (c >> 2)) lo = mid; else hi = mid;
+        }
+        const int qx = lo / B.ncol, qy = lo % B.ncol;
+        for (int col = 0; col < ncols; ++col) {
+            int ddx = abs(col / B.ncol - qx), ddy = abs(col % B.ncol - qy);
+            ddx = min(ddx, B.ncol - ddx);
+            ddy = min(ddy, B.ncol - ddy);
+            if (ddx > reach || ddy > reach) continue;
+            const int cl1 = 4 * col_tile[col + 1];
+            for (int j0 = max(c + 1, 4 * col_tile[col]); j0 < cl1; j0 += 32) {
+                const int jc = j0 + lane;
+                bool hit = false;
+                uint32_t code = 0;
+                if (jc < cl1) {
+                    const float4 bl = B.clo[(size_t)r * ncl + jc], bh = B.chi[(size_t)r * ncl + jc];
+                    if (bl.x <= bh.x) {  // the cluster holds atoms
+                        const float dx = 0.5f * (bl.x + bh.x) - cx, dy = 0.5f * (bl.y + bh.y) - cy,
+                                    dz = 0.5f * (bl.z + bh.z) - cz;
+                        const float sx = -rintf(dx * B.invL), sy = -rintf(dy * B.invL),
+                                    sz = -rintf(dz * B.invL);
+                        const float ex = fabsf(fmaf(sx, B.L, dx)), ey = fabsf(fmaf(sy, B.L, dy)),
+                                    ez = fabsf(fmaf(sz, B.L, dz));
+                        const float wx = hx + 0.5f * (bh.x - bl.x), wy = hy + 0.5f * (bh.y - bl.y),
+                                    wz = hz + 0.5f * (bh.z - bl.z);
+                        // lower bound of any periodic-image distance between the two boxes
+                        const float gx = fmaxf(0.f, ex - wx), gy = fmaxf(0.f, ey - wy),
+                                    gz = fmaxf(0.f, ez - wz);
+                        hit = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < B.rlist2;
+                        code = ((uint32_t)(sx + 1.f) << 24) | ((uint32_t)(sy + 1.f) << 26) |
+                               ((uint32_t)(sz + 1.f) << 28) | (bl.w != 0.f ? 1u << 30 : 0u);
                     }
                 }
-                const unsigned kb = __ballot_sync(kFullB, keep);
-                if (keep) {
-                    const int pos = count + __popc(kb & ((1u << lane) - 1u));
-                    if (pos < B.max_ent) out[pos] = e;
+                unsigned m = __ballot_sync(kFullB, hit);
+                while (m) {  // four hit clusters at a time: lane 8 k + a takes atom a of the k-th
+                    const int nh = min(__popc(m), 4);
+                    unsigned mm = m;
+                    for (int k = 0; k < q; ++k) mm &= mm - 1u;
+                    const int src = __ffs(mm) - 1;  // lane of this quarter's hit cluster (-1: none)
+                    const uint32_t hcode = __shfl_sync(kFullB, code, src & 31);
+                    for (int k = 0; k < nh; ++k) m &= m - 1u;
+                    bool keep = false;
+                    uint32_t e = 0;
+                    if (q < nh) {
+                        const int sj = 8 * (j0 + src) + l8;
+                        if (B.id[base + sj] >= 0) {
+                            const float4 xj = B.pos[base + sj];
+                            // the atom under its cluster's shift, first against c's box
+                            const float px = xj.x + (float)((int)((hcode >> 24) & 3u) - 1) * B.L,
+                                        py = xj.y + (float)((int)((hcode >> 26) & 3u) - 1) * B.L,
+                                        pz = xj.z + (float)((int)((hcode >> 28) & 3u) - 1) * B.L;
+                            const float bx = fmaxf(0.f, fabsf(px - cx) - hx),
+                                        by = fmaxf(0.f, fabsf(py - cy) - hy),
+                                        bz = fmaxf(0.f, fabsf(pz - cz) - hz);
+                            if (fmaf(bx, bx, fmaf(by, by, bz * bz)) < B.rlist2) {
+                                float d2 = 3.0e38f, dm = 0.f;
+#pragma unroll
+                                for (int t = 0; t < 8; ++t) {
+                                    if (!((ivalid >> t) & 1u)) continue;
+                                    const float4 a = sxi[w][t];
+                                    const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
+                                    d2 = fminf(d2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                                    dm = fmaxf(dm, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
+                                }
+                                if (!(dm < 0.5f * B.L)) {  // the shift may not be the minimum image
+                                    d2 = 3.0e38f;
+                                    for (int t = 0; t < 8; ++t) {
+                                        if (!((ivalid >> t) & 1u)) continue;
+                                        const float4 a = sxi[w][t];
+                                        const float mx = min_img(xj.x - a.x, B.L, B.invL),
+                                                    my = min_img(xj.y - a.y, B.L, B.invL),
+                                                    mz = min_img(xj.z - a.z, B.L, B.invL);
+                                        d2 = fminf(d2, fmaf(mx, mx, fmaf(my, my, mz * mz)));
+                                    }
+                                }
+                                keep = d2 < B.rlist2;
+                                inexact = inexact || (keep && !(dm < room));
+                                e = (uint32_t)sj | (hcode & 0x7f000000u);
+                            }
+                        }
+                    }
+                    const unsigned kb = __ballot_sync(kFullB, keep);
+                    if (keep) {
+                        const int pos = count + __popc(kb & ((1u << lane) - 1u));
+                        if (pos < B.max_ent) out[pos] = e;
+                    }
+                    count += __popc(kb);
                 }
-                count += __popc(kb);
             }
         }
     }

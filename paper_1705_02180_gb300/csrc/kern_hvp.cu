@@ -1,8 +1,9 @@
 // Hessian-vector products H(X_t) V_t of the physical potential, one cluster of CL
-// CTAs per frame (CL = 2 splits the tile pairs, bonds and angles between the two
-// CTAs; each then writes half of the atoms, summing its and the peer's partials). Used by the double backward of the energy (the gradient of
-// sum_t |grad U(X_t)|^2 is sum_t 2 H(X_t) grad U(X_t); the Onsager-Machlup
-// action of Eq. (SOM) contains (grad U)^2).
+// CTAs per frame (CL = 2 splits the block rows, bonds and angles between the two
+// CTAs; each then writes half of the atoms, summing its and the peer's partials). Used by
+// the double backward of the energy (the gradient of sum_t |grad U(X_t)|^2 is
+// sum_t 2 H(X_t) grad U(X_t); the Onsager-Machlup action of Eq. (SOM) contains (grad U)^2).
+// Pairs come in items of two 8-atom blocks whose boxes lie within r_c, on quarter warps.
 //
 // For a pair term phi(r) with d = x_j - x_i and w = v_j - v_i:
 //   (Hv)_j = phi'' (d.w) d / r^2 + (phi'/r) (w - (d.w) d / r^2),  (Hv)_i = -(Hv)_j,
@@ -10,7 +11,9 @@
 // For an angle term k/2 (theta - theta0)^2:
 //   H v = k (grad theta . v) grad theta + k (theta - theta0) D_v(grad theta),
 // D_v being the directional derivative along v, written out by hand below.
-// Sums are int64 fixed point (order-free, so results are bit-reproducible).
+// Each item sums its j terms in FP32 in a fixed order (the i terms run on over the items of
+// a row of blocks); those sums go to 2^-20 fixed-point partials held as three 32-bit words
+// per component (32-bit shared atomics), so results are bit-reproducible.
 #include <cooperative_groups.h>
 
 #include "scps_internal.h"
@@ -27,17 +30,30 @@ struct HvpShared {
     float4* xq;      // (x, y, z, qs)
     float4* vq;      // direction v
     float2* lj;
-    long long* H;    // 3 x nta fixed point
-    float4* blo;
+    unsigned long long* ex;  // exclusion mask per atom slot
+    int* H2;         // 3 x nta: bits 40 and up of the 2^-20 fixed-point partials (signed)
+    unsigned* H1;    // 3 x nta: bits 20..39
+    unsigned* H0;    // 3 x nta: bits 0..19
+    float4* blo;     // boxes of the 8-atom blocks
     float4* bhi;
-    uint32_t* tp;    // active tile pairs
     int nta;
 };
 
+// Adds x in 2^-20 fixed point as three 32-bit words (two 20-bit unsigned parts and the
+// signed rest), so that the sums cover the range of Hessian-vector products of stiff bonds
+// (|Hv| beyond 1e10) with 32-bit shared atomics; each unsigned word takes up to 4095
+// additions.
+__device__ __forceinline__ void hred(const HvpShared& sm, int k, float x) {
+    const long long v = f2fix(x);
+    atomicAdd(&sm.H0[k], (unsigned)(v & 0xfffffll));
+    atomicAdd(&sm.H1[k], (unsigned)((v >> 20) & 0xfffffll));
+    atomicAdd(&sm.H2[k], (int)(v >> 40));
+}
+
 __device__ __forceinline__ void hadd(const HvpShared& sm, int i, float x, float y, float z) {
-    atomicAdd((unsigned long long*)&sm.H[i], (unsigned long long)f2fix(x));
-    atomicAdd((unsigned long long*)&sm.H[sm.nta + i], (unsigned long long)f2fix(y));
-    atomicAdd((unsigned long long*)&sm.H[2 * sm.nta + i], (unsigned long long)f2fix(z));
+    hred(sm, i, x);
+    hred(sm, sm.nta + i, y);
+    hred(sm, 2 * sm.nta + i, z);
 }
 
 // phi'(r)/r of the shifted-force pair potential and phi''(r).
@@ -73,52 +89,63 @@ __device__ __forceinline__ void pair_derivs(float r2, float sig, float eps24, fl
 }
 
 template <int ELEC>
-__device__ void hvp_tile(const HvpShared& sm, const TopoDev& tp, const PairConst& pc, int I,
-                         int J, int lane) {
-    const int i = I * kTile + lane;
+__device__ __forceinline__ void pair_hvp_term(const HvpShared& sm, const PairConst& pc, int i, int j,
+                                              const float4& xj, const float4& vj, const float2& lj,
+                                              bool ok, float& ax, float& ay, float& az) {
     const float4 xi = sm.xq[i];
     const float4 vi = sm.vq[i];
     const float2 li = sm.lj[i];
-    const bool near = (J - I) <= 1;
-    const unsigned long long em = (near && i < tp.n_atoms) ? tp.excl[i] : 0ull;
-    float hix = 0.f, hiy = 0.f, hiz = 0.f, hjx = 0.f, hjy = 0.f, hjz = 0.f;
-    const int jb = J * kTile;
-    for (int t = 0; t < kTile; ++t) {
-        const int sl = (lane + t) & (kTile - 1);
-        const int j = jb + sl;
-        const float4 xj = sm.xq[j];
-        const float4 vj = sm.vq[j];
-        const float2 lj = sm.lj[j];
-        const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        bool ok = r2 < pc.rc2;
-        if (I == J) ok = ok && (j > i);
+    const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    ok = ok && r2 < pc.rc2;
+    float p1, pp;
+    pair_derivs<ELEC>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, p1, pp);
+    const float wx = vj.x - vi.x, wy = vj.y - vi.y, wz = vj.z - vi.z;
+    const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+    const float c1 = (pp - p1) * dw / r2;
+    ax = ok ? fmaf(c1, dx, p1 * wx) : 0.f;
+    ay = ok ? fmaf(c1, dy, p1 * wy) : 0.f;
+    az = ok ? fmaf(c1, dz, p1 * wz) : 0.f;
+}
+
+// The 64 pairs of block I (8 atoms) with block J >= I on a quarter warp: lane l holds atom
+// j = 8 J + l; at iteration t it takes atom i = 8 I + ((l + t) & 7), so the i sums rotate one
+// lane per iteration (after 8 lane l again holds atom 8 I + l's) while the j sum stays in the
+// lane and goes to the fixed-point partials after the item. The i sums (hi*) run on over the
+// items of the row. Within a block (I == J) a pair counts once (j > i). Near blocks test the
+// exclusion masks. An idle quarter (live false) runs along with no terms.
+template <int ELEC>
+__device__ __forceinline__ void hvp_item(const HvpShared& sm, const PairConst& pc, int I, int J,
+                                         int lane, bool live, float& hix, float& hiy, float& hiz) {
+    const int l8 = lane & 7;
+    const int src = (lane & 24) | ((l8 + 1) & 7);
+    const int j = 8 * J + l8;
+    const float4 xj = sm.xq[j];
+    const float4 vj = sm.vq[j];
+    const float2 lj = sm.lj[j];
+    const bool near = 8 * (J - I) < kExclWindow + 8;
+    float hjx = 0.f, hjy = 0.f, hjz = 0.f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int i = 8 * I + ((l8 + t) & 7);
+        bool ok = live && (I != J || j > i);
         if (near) {
             const int dj = j - i + kExclWindow;
-            if (dj >= 0 && dj < 2 * kExclWindow) ok = ok && !((em >> dj) & 1ull);
+            if (dj >= 0 && dj < 2 * kExclWindow) ok = ok && !((sm.ex[i] >> dj) & 1ull);
         }
-        float p1, pp;
-        pair_derivs<ELEC>(r2, li.x + lj.x, li.y * lj.y, xi.w * xj.w, pc, p1, pp);
-        const float wx = vj.x - vi.x, wy = vj.y - vi.y, wz = vj.z - vi.z;
-        const float dw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
-        const float c1 = (pp - p1) * dw / r2;
-        float ax = fmaf(c1, dx, p1 * wx), ay = fmaf(c1, dy, p1 * wy), az = fmaf(c1, dz, p1 * wz);
-        ax = ok ? ax : 0.f;
-        ay = ok ? ay : 0.f;
-        az = ok ? az : 0.f;
+        float ax, ay, az;
+        pair_hvp_term<ELEC>(sm, pc, i, j, xj, vj, lj, ok, ax, ay, az);
         hix -= ax;
         hiy -= ay;
         hiz -= az;
         hjx += ax;
         hjy += ay;
         hjz += az;
-        const int src = (lane + 1) & (kTile - 1);
-        hjx = __shfl_sync(kFullMask, hjx, src);
-        hjy = __shfl_sync(kFullMask, hjy, src);
-        hjz = __shfl_sync(kFullMask, hjz, src);
+        hix = __shfl_sync(kFullMask, hix, src);
+        hiy = __shfl_sync(kFullMask, hiy, src);
+        hiz = __shfl_sync(kFullMask, hiz, src);
     }
-    hadd(sm, i, hix, hiy, hiz);
-    hadd(sm, jb + lane, hjx, hjy, hjz);
+    if (live) hadd(sm, j, hjx, hjy, hjz);
 }
 
 __device__ void hvp_bond(const HvpShared& sm, const TopoDev& tp, int b) {
@@ -204,19 +231,21 @@ __global__ void __launch_bounds__(1024)
 k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
              const float* __restrict__ V, float* __restrict__ HV, int nta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int tp_count;
+    __shared__ int next_row;
     const TopoDev tp = *topo_ptr;
-    const int n = tp.n_atoms, nt = tp.n_tiles, ntp = nt * (nt + 1) / 2;
+    const int n = tp.n_atoms, nbs = nta / 8;
     HvpShared sm;
     char* p = (char*)smem_raw;
     sm.nta = nta;
     sm.xq = (float4*)p; p += sizeof(float4) * nta;
     sm.vq = (float4*)p; p += sizeof(float4) * nta;
-    sm.blo = (float4*)p; p += sizeof(float4) * (nta / kTile);
-    sm.bhi = (float4*)p; p += sizeof(float4) * (nta / kTile);
-    sm.H = (long long*)p; p += sizeof(long long) * 3 * nta;
-    sm.lj = (float2*)p; p += sizeof(float2) * nta;
-    sm.tp = (uint32_t*)p;
+    sm.blo = (float4*)p; p += sizeof(float4) * nbs;
+    sm.bhi = (float4*)p; p += sizeof(float4) * nbs;
+    sm.ex = (unsigned long long*)p; p += sizeof(unsigned long long) * nta;
+    sm.H2 = (int*)p; p += sizeof(int) * 3 * nta;
+    sm.H1 = (unsigned*)p; p += sizeof(unsigned) * 3 * nta;
+    sm.H0 = (unsigned*)p; p += sizeof(unsigned) * 3 * nta;
+    sm.lj = (float2*)p;
     const long long f = blockIdx.x / CL;
     const int rank = CL == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const float* xf = X + f * n * 3;
@@ -226,22 +255,32 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
             sm.xq[i] = make_float4(xf[3 * i], xf[3 * i + 1], xf[3 * i + 2], tp.qs[i]);
             sm.vq[i] = make_float4(vf[3 * i], vf[3 * i + 1], vf[3 * i + 2], 0.f);
             sm.lj[i] = tp.lj[i];
+            sm.ex[i] = tp.excl[i];
         } else {
             sm.xq[i] = make_float4(1.0e5f * (float)(i + 1), 0.f, 0.f, 0.f);
             sm.vq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             sm.lj[i] = make_float2(0.f, 0.f);
+            sm.ex[i] = 0ull;
         }
     }
-    for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) sm.H[i] = 0;
-    if (threadIdx.x == 0) tp_count = 0;
+    for (int i = threadIdx.x; i < 3 * nta; i += blockDim.x) {
+        sm.H2[i] = 0;
+        sm.H1[i] = 0u;
+        sm.H0[i] = 0u;
+    }
+    if (threadIdx.x == 0) next_row = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int t = warp; t < nt; t += nw) {  // tile boxes (valid atoms only)
-        const int a = t * kTile + lane;
-        const float4 q = sm.xq[a < n ? a : t * kTile];
-        float lx = q.x, ly = q.y, lz = q.z, hx = q.x, hy = q.y, hz = q.z;
+    const int l8 = lane & 7, q = lane >> 3;
+    for (int b0 = 4 * warp; b0 < nbs; b0 += 4 * nw) {  // block boxes (valid atoms only)
+        const int b = b0 + q;
+        const int a = 8 * b + l8;
+        const bool valid = b < nbs && a < n;
+        const float4 x = valid ? sm.xq[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float lx = valid ? x.x : 3.0e38f, ly = valid ? x.y : 3.0e38f, lz = valid ? x.z : 3.0e38f;
+        float hx = valid ? x.x : -3.0e38f, hy = valid ? x.y : -3.0e38f, hz = valid ? x.z : -3.0e38f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 1; o < 8; o <<= 1) {
             lx = fminf(lx, __shfl_xor_sync(kFullMask, lx, o));
             ly = fminf(ly, __shfl_xor_sync(kFullMask, ly, o));
             lz = fminf(lz, __shfl_xor_sync(kFullMask, lz, o));
@@ -249,56 +288,79 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
             hy = fmaxf(hy, __shfl_xor_sync(kFullMask, hy, o));
             hz = fmaxf(hz, __shfl_xor_sync(kFullMask, hz, o));
         }
-        if (lane == 0) {
-            sm.blo[t] = make_float4(lx, ly, lz, 0.f);
-            sm.bhi[t] = make_float4(hx, hy, hz, 0.f);
+        if (l8 == 0 && b < nbs) {
+            sm.blo[b] = make_float4(lx, ly, lz, 0.f);
+            sm.bhi[b] = make_float4(hx, hy, hz, 0.f);
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x * CL + rank; q < ntp; q += blockDim.x * CL) {  // this CTA's share
-        int I = 0, row = nt, r = q;
-        while (r >= row) {
-            r -= row;
-            ++I;
-            --row;
+    // rows of blocks I (I % CL == rank) pulled by the warps; in a row the blocks J >= I whose
+    // box comes within r_c of I's (I itself when it holds atoms), four items at a time
+    for (;;) {
+        int row = 0;
+        if (lane == 0) row = atomicAdd(&next_row, 1);
+        const int I = __shfl_sync(kFullMask, row, 0) * CL + rank;
+        if (I >= nbs) break;
+        const float4 al = sm.blo[I], ah = sm.bhi[I];
+        if (!(al.x <= ah.x)) continue;  // no atoms in block I (warp-uniform)
+        float hix = 0.f, hiy = 0.f, hiz = 0.f;  // this quarter's share of atom 8 I + l8
+        for (int j0 = I; j0 < nbs; j0 += 32) {
+            const int J = j0 + lane;
+            bool hit = false;
+            if (J < nbs) {
+                const float4 bl = sm.blo[J], bh = sm.bhi[J];
+                const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
+                const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
+                const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
+                hit = bl.x <= bh.x && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2;
+            }
+            unsigned m = __ballot_sync(kFullMask, hit);
+            while (m) {
+                const int nh = min(__popc(m), 4);
+                unsigned mm = m;
+                for (int k = 0; k < q; ++k) mm &= mm - 1u;
+                const int src = __ffs(mm) - 1;
+                for (int k = 0; k < nh; ++k) m &= m - 1u;
+                const bool live = q < nh;
+                hvp_item<ELEC>(sm, P.pc, I, live ? j0 + src : I, lane, live, hix, hiy, hiz);
+            }
         }
-        const int J = I + r;
-        const float4 al = sm.blo[I], ah = sm.bhi[I], bl = sm.blo[J], bh = sm.bhi[J];
-        const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
-        const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
-        const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
-        if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2)
-            sm.tp[atomicAdd(&tp_count, 1)] = ((uint32_t)I << 16) | (uint32_t)J;
-    }
-    __syncthreads();
-    for (int k = warp; k < tp_count; k += nw) {
-        const uint32_t w = sm.tp[k];
-        hvp_tile<ELEC>(sm, tp, P.pc, (int)(w >> 16), (int)(w & 0xffff), lane);
+        // the four quarters' shares of the row's atoms (FP32, a fixed order)
+        hix += __shfl_xor_sync(kFullMask, hix, 8);
+        hiy += __shfl_xor_sync(kFullMask, hiy, 8);
+        hiz += __shfl_xor_sync(kFullMask, hiz, 8);
+        hix += __shfl_xor_sync(kFullMask, hix, 16);
+        hiy += __shfl_xor_sync(kFullMask, hiy, 16);
+        hiz += __shfl_xor_sync(kFullMask, hiz, 16);
+        if (lane < 8) hadd(sm, 8 * I + lane, hix, hiy, hiz);
     }
     const int t0 = threadIdx.x * CL + rank, tstep = blockDim.x * CL;
     for (int b = t0; b < tp.n_bonds; b += tstep) hvp_bond(sm, tp, b);
-    for (int q = t0; q < tp.n_angles; q += tstep) hvp_angle(sm, tp, q);
+    for (int a = t0; a < tp.n_angles; a += tstep) hvp_angle(sm, tp, a);
     hvp_cluster_sync<CL>();  // every partial of the cluster is complete
     float* out = HV + f * n * 3;
-    const long long* Ho = CL == 1 ? sm.H : cg::this_cluster().map_shared_rank(sm.H, (unsigned)(rank ^ 1));
+    const int* o2 = CL == 1 ? sm.H2 : cg::this_cluster().map_shared_rank(sm.H2, (unsigned)(rank ^ 1));
+    const unsigned* o1 = CL == 1 ? sm.H1 : cg::this_cluster().map_shared_rank(sm.H1, (unsigned)(rank ^ 1));
+    const unsigned* o0 = CL == 1 ? sm.H0 : cg::this_cluster().map_shared_rank(sm.H0, (unsigned)(rank ^ 1));
     for (int i = threadIdx.x + rank * blockDim.x; i < n; i += CL * blockDim.x) {
-        long long hx = sm.H[i], hy = sm.H[nta + i], hz = sm.H[2 * nta + i];
-        if (CL == 2) {
-            hx += Ho[i];
-            hy += Ho[nta + i];
-            hz += Ho[2 * nta + i];
+        long long h[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int k = c * nta + i;
+            h[c] = ((long long)sm.H2[k] << 40) + ((long long)sm.H1[k] << 20) + (long long)sm.H0[k];
+            if (CL == 2) h[c] += ((long long)o2[k] << 40) + ((long long)o1[k] << 20) + (long long)o0[k];
         }
-        out[3 * i] = fix2f(hx);
-        out[3 * i + 1] = fix2f(hy);
-        out[3 * i + 2] = fix2f(hz);
+        out[3 * i] = fix2f(h[0]);
+        out[3 * i + 1] = fix2f(h[1]);
+        out[3 * i + 2] = fix2f(h[2]);
     }
     hvp_cluster_sync<CL>();  // no CTA leaves while its shared memory may still be read
 }
 
 size_t hvp_smem_bytes(int nta) {
-    const int nt = nta / kTile;
-    return sizeof(float4) * 2 * nta + sizeof(float4) * 2 * nt + sizeof(long long) * 3 * nta +
-           sizeof(float2) * nta + sizeof(uint32_t) * (size_t)(nt * (nt + 1) / 2 + 4);
+    const int nbs = nta / 8;
+    return sizeof(float4) * 2 * nta + sizeof(float4) * 2 * nbs + sizeof(unsigned long long) * nta +
+           (sizeof(int) + 2 * sizeof(unsigned)) * 3 * (size_t)nta + sizeof(float2) * nta;
 }
 
 // Few frames (a checkpoint segment): a 2-CTA cluster of 1024 threads per frame, so that

@@ -1082,6 +1082,8 @@ int scps_hvp(scps_system* s, int32_t topo, int64_t n_frames, const float* X, con
     TraceRange trace_("scps_hvp");
     if (!s) return fail(SCPS_ERR_INVALID_ARG, "NULL system");
     if (s->model != SCPS_MODEL_CHAIN) return fail(SCPS_ERR_UNSUPPORTED, "chain model only");
+    if (s->is_box)  // these kernels take every pair once, with no periodic images
+        return fail(SCPS_ERR_UNSUPPORTED, "Hessian-vector products cover open-boundary chains");
     if (topo < 0 || topo >= (int)s->topos.size()) return fail(SCPS_ERR_INVALID_ARG, "bad topology %d", topo);
     if (n_frames < 0 || n_frames > 2147483647ll) return fail(SCPS_ERR_INVALID_ARG, "bad n_frames");
     if (n_frames == 0) return SCPS_OK;
