@@ -86,11 +86,38 @@ class ForceNormSquared(torch.autograd.Function):
         return HV * g.to(HV.dtype), None, None
 
 
+class ForceNormAction(torch.autograd.Function):
+    """sum_t |grad U(X_t)|^2 over all frames X (float64 scalar) with activation
+    checkpointing over segments of frames: the forward evaluates every frame in one launch
+    and keeps only the positions; the backward recomputes the forces of each segment and
+    applies 2 H(X_t) grad U(X_t) to it (one force launch and one HVP launch per segment, so
+    at most one segment's forces are live). First order only, like ForceNormSquared."""
+
+    @staticmethod
+    def forward(ctx, X, system, topo, segment):
+        X = X.contiguous()
+        U = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        F = torch.empty_like(X)
+        system.energy_forces(topo, X, U, F)
+        ctx.save_for_backward(X)
+        ctx.system, ctx.topo, ctx.segment = system, topo, segment
+        return (F.double() ** 2).sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        (X,) = ctx.saved_tensors
+        seg = min(ctx.segment, X.shape[0])
+        U = torch.empty(seg, dtype=torch.float64, device=X.device)
+        F = torch.empty((seg,) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
+        HV = torch.empty_like(X)
+        for s in range(0, X.shape[0], seg):
+            n = min(seg, X.shape[0] - s)
+            ctx.system.energy_forces(ctx.topo, X[s:s + n], U[:n], F[:n])
+            ctx.system.hvp(ctx.topo, X[s:s + n], F[:n].mul_(-2.0), HV[s:s + n])  # v = 2 grad U
+        return HV * g.to(HV.dtype), None, None, None
+
+
 def force_norm_action(system, X, topo=0, segment=50):
-    """sum_t |grad U(X_t)|^2 over the frames, evaluated per segment of `segment`
-    frames; each segment keeps only its positions and recomputes its forces in the
-    backward pass (activation checkpointing over path frames)."""
-    total = X.new_zeros((), dtype=torch.float64)
-    for s in range(0, X.shape[0], segment):
-        total = total + ForceNormSquared.apply(X[s:s + segment], system, topo)
-    return total
+    """sum_t |grad U(X_t)|^2 over the frames; the backward recomputes the forces segment by
+    segment of `segment` frames (activation checkpointing over path frames)."""
+    return ForceNormAction.apply(X, system, topo, segment)
