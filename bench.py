@@ -372,10 +372,13 @@ def extra_config(torch, pkg, name, args, K, W):
                        "peak_GBps": hbm_peak,
                        "frac": gbs / hbm_peak if hbm_peak else None,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm_peak else None},
-               # per call: one re-evaluation (8 list kernels, which return at once unless a
-               # rebuild is due, pairs, chain) + its A half step, the same 11 kernels per
-               # step, and the step counter
-               "gpu_launches": K * (11 * (spc + 1) + 1), "clocks": clk}
+               # per call: one re-evaluation (decide, 7 list kernels that return at once
+               # unless a rebuild is forced, pairs, chain) + its A half step; per step one
+               # graph of 5 kernels (step counter, decide, pairs, chain, integrate) and, on the
+               # steps that rebuild (at most every rebuild_every steps here), 8 more inside
+               # its conditional node
+               "gpu_launches": K * (11 + 5 * spc + 8 * -(-spc // tune["rebuild_every"])),
+               "clocks": clk}
         rc, st = s.status()
         out["status"] = int(rc)
         s.close()

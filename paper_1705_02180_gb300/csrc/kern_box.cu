@@ -77,6 +77,33 @@ __global__ void k_box_decide(BoxDev B, StateDev st, int r0, int auto_ok) {
     }
 }
 
+// Graph form of step 1a (one CTA for all R replicas): the same decision per replica, and
+// the graph's conditional value: 1 when some replica rebuilds, so that the rebuild kernels
+// run at all only then. The key counts are cleared by k_box_clear_hist inside the rebuild.
+__global__ void k_box_decide_graph(BoxDev B, StateDev st, int R, cudaGraphConditionalHandle h) {
+    int any = 0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const float d2 = __uint_as_float(B.maxd2[r]);
+        const int decide = st.status[r] == 0 &&
+                           (B.need[r] || B.since[r] >= B.rebuild_every || d2 >= B.skin2_quarter);
+        B.need[r] = decide;
+        if (decide) {
+            B.since[r] = 0;
+            B.maxd2[r] = 0u;
+        }
+        any |= decide;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+__global__ void k_box_clear_hist(BoxDev B, int r0) {
+    const int r = blockIdx.y + r0;
+    if (!B.need[r]) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < kNumKeys) B.hist[(size_t)r * kNumKeys + k] = 0;
+}
+
 // Rebuild, step 1b (slots): wrap into the box, key = (column, z bin), count keys.
 __global__ void k_box_key(BoxDev B, int r0) {
     const int r = blockIdx.y + r0;
@@ -848,8 +875,9 @@ __global__ void __launch_bounds__(512) k_box_chain(BoxDev B, const TopoDev* __re
 // BAOAB half steps per slot: B closes the evaluated step, A starts the next one.
 __global__ void k_box_integrate(BoxDev B, const TopoDev* __restrict__ topo, StateDev st,
                                 RunParams P, const uint32_t* __restrict__ rep_ids, long long step,
-                                int do_b, int do_a) {
+                                int do_b, int do_a, int step_from_state) {
     const int r = blockIdx.y;
+    if (step_from_state) step = st.step[r];  // graph form: the counter the step graph advanced
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B.np) return;
     const size_t base = (size_t)r * B.np;
@@ -941,13 +969,10 @@ size_t box_chain_smem(int n_chain, int n_contacts) {
     return sizeof(float4) * n_chain + sizeof(long long) * 3 * n_chain + sizeof(float) * n_contacts;
 }
 
-// One force evaluation of replicas [r0, r0 + nr): rebuild when forced (or, when
-// `auto_ok`, when due), pair forces, chain terms and the ratchet.
-static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev& st,
-                            const RunParams& P, int r0, int nr, int elec, int ncon_max,
-                            bool energy, int do_ratchet, int count_step, int auto_ok,
-                            cudaStream_t s) {
-    k_box_decide<<<nr, 256, 0, s>>>(B, st, r0, auto_ok);
+// The rebuild kernels after the decision (each returns at once for a replica that does not
+// rebuild), for replicas [r0, r0 + nr).
+static void box_rebuild(const BoxDev& B, const TopoDev* topo, const StateDev& st, int r0, int nr,
+                        cudaStream_t s) {
     k_box_key<<<dim3((B.np + 255) / 256, nr), 256, 0, s>>>(B, r0);
     k_box_scan<<<nr, kSortThreads, 0, s>>>(B, r0);
     k_box_scatter<<<dim3((B.n_atoms + 255) / 256, nr), 256, 0, s>>>(B, r0);
@@ -957,6 +982,13 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
     k_box_subsort<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_tiles<<<gt, 128, 0, s>>>(B, topo, r0);
     k_box_list<<<gg, 128, 0, s>>>(B, st, r0);
+}
+
+// Pair forces, then the chain terms and the ratchet, of replicas [r0, r0 + nr).
+static void box_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
+                       int r0, int nr, int elec, int ncon_max, bool energy, int do_ratchet,
+                       int count_step, cudaStream_t s) {
+    const dim3 gg((4 * B.nt + 3) / 4, nr);
 #define PAIRS(E)                                                                                \
     switch (elec) {                                                                             \
         case ELEC_DDIEL: k_box_pairs<ELEC_DDIEL, E><<<gg, 128, 0, s>>>(B, topo, P, r0); break;  \
@@ -975,6 +1007,17 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
         k_box_chain<true><<<nr, 512, smem, s>>>(B, topo, st, P, r0, do_ratchet, count_step);
     else
         k_box_chain<false><<<nr, 512, smem, s>>>(B, topo, st, P, r0, do_ratchet, count_step);
+}
+
+// One force evaluation of replicas [r0, r0 + nr): rebuild when forced (or, when
+// `auto_ok`, when due), pair forces, chain terms and the ratchet.
+static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev& st,
+                            const RunParams& P, int r0, int nr, int elec, int ncon_max,
+                            bool energy, int do_ratchet, int count_step, int auto_ok,
+                            cudaStream_t s) {
+    k_box_decide<<<nr, 256, 0, s>>>(B, st, r0, auto_ok);
+    box_rebuild(B, topo, st, r0, nr, s);
+    box_forces(B, topo, st, P, r0, nr, elec, ncon_max, energy, do_ratchet, count_step, s);
     return cudaGetLastError();
 }
 
@@ -1002,26 +1045,116 @@ cudaError_t box_prepare(const BoxDev& B, int n_contacts_max) {
     return e;
 }
 
-// n_steps steps of replicas [0, R) (kernel launches on stream s).
+// One MD step of replicas [0, R) as a graph: the step counters, the rebuild decision (which
+// sets the graph's conditional value), the rebuild kernels inside a conditional node (run
+// only when some replica rebuilds), the forces, [the frame], the B half step and, unless
+// `last`, the A half step of the next one (noise counter read from the step counters),
+// [the frame scalars].
+static cudaError_t box_step_graph(const BoxDev& B, const TopoDev* topo, const StateDev& st,
+                                  const RunParams& P, const uint32_t* rep_ids, int R, int elec,
+                                  int ncon_max, bool save, bool last, long long frame_atoms,
+                                  cudaStream_t cs, cudaStream_t cs2, cudaGraph_t* def,
+                                  cudaGraphExec_t* exec) {
+    const dim3 ga((B.np + 255) / 256, R);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    k_box_step_count<<<(R + 127) / 128, 128, 0, cs>>>(st, R, 1);
+    k_box_decide_graph<<<1, 256, 0, cs>>>(B, st, R, h);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNode_t cond = nullptr;
+    cudaGraphNodeParams cp = {};
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cond, g, deps, nullptr, nd, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            k_box_clear_hist<<<dim3((kNumKeys + 255) / 256, R), 256, 0, cs2>>>(B, 0);
+            box_rebuild(B, topo, st, 0, R, cs2);
+            const cudaError_t le = cudaGetLastError();
+            e = cudaStreamEndCapture(cs2, &body);
+            if (e == cudaSuccess) e = le;
+        }
+    }
+    if (e == cudaSuccess) {
+        box_forces(B, topo, st, P, 0, R, elec, ncon_max, save, 1, 1, cs);
+        if (save) k_box_frame<<<ga, 256, 0, cs>>>(B, st, P, frame_atoms);
+        k_box_integrate<<<ga, 256, 0, cs>>>(B, topo, st, P, rep_ids, 0, 1, last ? 0 : 1, 1);
+        if (save) k_box_frame_scalars<<<(R + 127) / 128, 128, 0, cs>>>(B, st, P, R);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &out);
+    if (e == cudaSuccess) e = ce;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    *def = g;
+    return cudaSuccess;
+}
+
+void BoxGraphs::reset() {
+    for (int v = 0; v < 4; ++v) {
+        if (exec[v]) cudaGraphExecDestroy(exec[v]);
+        if (def[v]) cudaGraphDestroy(def[v]);
+        exec[v] = nullptr;
+        def[v] = nullptr;
+    }
+}
+
+// n_steps steps of replicas [0, R) on stream s: the current configuration is evaluated
+// again (no scheduled rebuild here, so the result does not depend on how steps are split into
+// calls) and its A half step taken; then every step is one launch of a step graph from G
+// (regular, last, save, save and last; captured on first use), or, without G, the same
+// kernels launched one by one.
 cudaError_t box_run(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
                     const uint32_t* rep_ids, int R, int elec, int ncon_max, long long step0,
-                    long long n_steps, long long frame_atoms, cudaStream_t s) {
+                    long long n_steps, long long frame_atoms, BoxGraphs* G, cudaStream_t s) {
     const dim3 ga((B.np + 255) / 256, R);
-    // re-evaluate the current configuration (no scheduled rebuild here, so the
-    // result does not depend on how steps are split into calls)
     cudaError_t e = box_eval(B, topo, st, P, 0, R, elec, ncon_max, false, 1, 0, 0, s);
     if (e != cudaSuccess) return e;
-    k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step0, 0, 1);
+    k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step0, 0, 1, 0);
     for (long long k = 1; k <= n_steps; ++k) {
         const long long step = step0 + k;
         const bool save = P.save_interval > 0 && step % P.save_interval == 0;
+        const bool last = k == n_steps;
+        if (G) {
+            const int v = (save ? 2 : 0) + (last ? 1 : 0);
+            if (!G->exec[v]) {
+                e = box_step_graph(B, topo, st, P, rep_ids, R, elec, ncon_max, save, last,
+                                   frame_atoms, G->cap, G->cap2, &G->def[v], &G->exec[v]);
+                if (e != cudaSuccess) return e;
+            }
+            e = cudaGraphLaunch(G->exec[v], s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        k_box_step_count<<<(R + 127) / 128, 128, 0, s>>>(st, R, 1);
         e = box_eval(B, topo, st, P, 0, R, elec, ncon_max, save, 1, 1, 1, s);
         if (e != cudaSuccess) return e;
         if (save) k_box_frame<<<ga, 256, 0, s>>>(B, st, P, frame_atoms);
-        k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step, 1, k < n_steps ? 1 : 0);
+        k_box_integrate<<<ga, 256, 0, s>>>(B, topo, st, P, rep_ids, step, 1, last ? 0 : 1, 0);
         if (save) k_box_frame_scalars<<<(R + 127) / 128, 128, 0, s>>>(B, st, P, R);
     }
-    k_box_step_count<<<(R + 127) / 128, 128, 0, s>>>(st, R, n_steps);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ cudaError_t box_load(const BoxDev& B, const TopoDev* topo, const StateDev& st, c
                      int r, cudaStream_t s);
 cudaError_t box_run(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
                     const uint32_t* rep_ids, int R, int elec, int ncon_max, long long step0,
-                    long long n_steps, long long frame_atoms, cudaStream_t s);
+                    long long n_steps, long long frame_atoms, BoxGraphs* G, cudaStream_t s);
 cudaError_t box_energy_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st,
                               const RunParams& P, int r_eval, int elec, int ncon_max,
                               const float* X, double* U, float* F, double* Z, cudaStream_t s);
@@ -118,6 +118,7 @@ struct scps_system {
     RunParams base{};
     std::vector<void*> allocs;
     cudaStream_t cap_stream = nullptr;
+    BoxGraphs box_graphs;  // periodic box: step graphs and their capture streams
     std::map<long long, cudaGraphExec_t> graphs;
     std::vector<cudaGraph_t> graph_defs;
     float* plain_f = nullptr;
@@ -313,6 +314,7 @@ int sync_topos(scps_system* s) {
 }
 
 void drop_graphs(scps_system* s) {
+    s->box_graphs.reset();
     for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
     s->graphs.clear();
     for (auto g : s->graph_defs) cudaGraphDestroy(g);
@@ -679,6 +681,9 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
     if (rc) return bail(rc);
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(SCPS_ERR_CUDA, "cudaStreamCreate failed"));
+    if (s->is_box && (cudaStreamCreateWithFlags(&s->box_graphs.cap, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaStreamCreateWithFlags(&s->box_graphs.cap2, cudaStreamNonBlocking) != cudaSuccess))
+        return bail(fail(SCPS_ERR_CUDA, "cudaStreamCreate failed"));
     // run parameters shared by every launch
     RunParams& P = s->base;
     P.n_replicas = R;
@@ -722,6 +727,8 @@ int scps_destroy_system(scps_system* s) {
     if (!s) return SCPS_OK;
     drop_graphs(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->box_graphs.cap) cudaStreamDestroy(s->box_graphs.cap);
+    if (s->box_graphs.cap2) cudaStreamDestroy(s->box_graphs.cap2);
     s->drop_bias_tables();
     for (auto st : s->fork_streams) cudaStreamDestroy(st);
     for (auto ev : s->fork_events) cudaEventDestroy(ev);
@@ -965,10 +972,12 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
                 return fail(SCPS_ERR_STATE, "periodic-box replicas must share one step counter");
         const long long frame_atoms = (long long)std::max(s->d.max_frames, 1) * s->box.n_atoms;
         SCPS_CU(box_run(s->box, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max,
-                        s->host_step[0], n_steps, frame_atoms, cs));
-        // per evaluation 8 list kernels (they return at once unless a rebuild is due), pairs
-        // and chain; an integrate per half step pair; the step counter
-        launches = 11 * (n_steps + 1) + 1;
+                        s->host_step[0], n_steps, frame_atoms, &s->box_graphs, cs));
+        // the evaluation that opens the call (decide, 7 rebuild kernels that return at once
+        // unless a rebuild is forced, pairs, chain) and its A half step; per step one graph
+        // of 5 kernels (step counter, decide, pairs, chain, integrate; 2 more on save steps)
+        // plus 8 inside its conditional node when some replica rebuilds
+        launches = 11 + 5 * n_steps;
     } else if (s->d.exec == SCPS_EXEC_PLAIN) {
         P.n_steps = n_steps;
         std::vector<RepDev> reps(R);
@@ -1413,6 +1422,7 @@ static int box_autotune(scps_system* s, int probe_steps, int use_cache, scps_tun
     const double rc = s->base.pc.rc > 0.f ? (double)s->base.pc.rc : 1.0;
     std::vector<int> ones(R, 1);
     auto apply = [&](double skin, int every) {
+        s->box_graphs.reset();  // the step graphs hold the box parameters by value
         s->list_skin = skin;
         B.rebuild_every = every;
         B.rlist2 = (float)((rc + skin) * (rc + skin));
@@ -1495,13 +1505,13 @@ static int box_autotune(scps_system* s, int probe_steps, int use_cache, scps_tun
         cudaError_t le = apply(skin, every);
         if (le == cudaSuccess)
             le = box_run(B, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max, step0,
-                         std::max(1, probe_steps / 4), frame_atoms, s->cap_stream);
+                         std::max(1, probe_steps / 4), frame_atoms, &s->box_graphs, s->cap_stream);
         if (le == cudaSuccess) le = copy_all(false);
         if (le == cudaSuccess) le = apply(skin, every);
         if (le == cudaSuccess) le = cudaEventRecord(e0, s->cap_stream);
         if (le == cudaSuccess)
             le = box_run(B, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max, step0,
-                         probe_steps, frame_atoms, s->cap_stream);
+                         probe_steps, frame_atoms, &s->box_graphs, s->cap_stream);
         if (le == cudaSuccess) le = cudaEventRecord(e1, s->cap_stream);
         if (le == cudaSuccess) le = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -172,4 +172,14 @@ struct BoxDev {
 
 constexpr uint32_t kBoxNoSlot = 0x7fffffu;  // padding entry of a box pair list
 
+// Step graphs of the periodic box (variants: regular, last step of a call, save step, save
+// and last), captured on first use with the system's capture streams; they hold the box
+// parameters by value, so any change of those drops them.
+struct BoxGraphs {
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t def[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap = nullptr, cap2 = nullptr;  // owned by the system
+    void reset();
+};
+
 }  // namespace scps

@@ -88,3 +88,48 @@ def test_autotune_cache(pkg):
                                                                t2["threads"])
     s1.close()
     s2.close()
+
+
+@pytest.mark.parametrize("kw", [dict(skin=0.04), dict(skin=0.3), dict(skin=0.12, rebuild_every=3)])
+def test_list_skin_and_cadence_keep_trajectories(pkg, kw):
+    # every pair term is an integer whatever list holds it, and every pair inside the cutoff
+    # is in the list (the displacement bound triggers the builds): the skin and the rebuild
+    # cadence change the work, not the bits
+    ref = mixed(pkg)
+    ref.step(150)
+    a = ref.get_state()
+    n_ref = ref.info()["steps_per_list_build"]
+    ref.close()
+    s = mixed(pkg, **kw)
+    s.step(150)
+    b = s.get_state()
+    for k in ("x", "v", "zm", "T", "step"):
+        assert np.array_equal(a[k], b[k]), k
+    info = s.info()
+    assert info["list_skin"] == pytest.approx(kw["skin"])
+    if kw["skin"] < 0.12:
+        assert info["steps_per_list_build"] < n_ref
+    if kw.get("rebuild_every"):
+        assert info["steps_per_list_build"] <= kw["rebuild_every"]
+    s.close()
+
+
+def test_chain_list_is_complete_and_tight(pkg):
+    # evaluated pair slots per replica-step against the non-excluded pairs inside r_c of the
+    # current configuration (the thermally unfolded 560-atom chain, skin 0.12 nm)
+    c = synth.make_chain(35, seed=1)
+    R = 2
+    x0 = np.concatenate([f32(c.x_unfolded)] * R)
+    s = pkg.System(topologies=[pkg.chain_topology(c)], replica_topology=[0] * R, x0=x0,
+                   dt=0.002, gamma=1.0, kT=KT, seed=5, skin=0.12)
+    s.step(1)
+    slots = s.info()["pair_checks_per_step"] / R
+    x = s.get_state()["x"].reshape(R, -1, 3)[0]
+    d2 = ((x[:, None] - x[None]) ** 2).sum(-1)
+    ex = np.zeros(d2.shape, bool)
+    ex[c.exclusions[:, 0], c.exclusions[:, 1]] = True
+    ex |= ex.T
+    iu = np.triu_indices(len(x), 1)
+    n_in = int(((d2[iu] < 1.0) & ~ex[iu]).sum())
+    assert n_in < slots < 2.2 * n_in
+    s.close()
