@@ -25,6 +25,8 @@ namespace scps {
 namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kHvpSeg = 16;          // candidate blocks J per work unit
+constexpr int kHvpMaxBlocks = 512;   // 8-atom blocks per frame (4096 atoms)
 
 struct HvpShared {
     float4* xq;      // (x, y, z, qs)
@@ -231,7 +233,8 @@ __global__ void __launch_bounds__(1024)
 k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __restrict__ X,
              const float* __restrict__ V, float* __restrict__ HV, int nta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int next_row;
+    __shared__ int next_row, n_units;
+    __shared__ int upre[kHvpMaxBlocks];  // first work unit of each row of blocks
     const TopoDev tp = *topo_ptr;
     const int n = tp.n_atoms, nbs = nta / 8;
     HvpShared sm;
@@ -294,38 +297,66 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
         }
     }
     __syncthreads();
-    // rows of blocks I (I % CL == rank) pulled by the warps; in a row the blocks J >= I whose
-    // box comes within r_c of I's (I itself when it holds atoms), four items at a time
+    const int t0 = threadIdx.x * CL + rank, tstep = blockDim.x * CL;
+    for (int b = t0; b < tp.n_bonds; b += tstep) hvp_bond(sm, tp, b);
+    for (int a = t0; a < tp.n_angles; a += tstep) hvp_angle(sm, tp, a);
+    // work units: the rows of blocks I with I % CL == rank, each cut into segments of 16
+    // candidate blocks J >= I (long rows first); a warp pulls a unit, tests its 16 blocks
+    // against I's box and takes the hits four items at a time
+    if (warp == 0) {
+        int run = 0;
+        for (int r0 = 0; r0 < nbs; r0 += 32) {
+            const int I = r0 + lane;
+            const int ns = (I < nbs && I % CL == rank) ? (nbs - I + kHvpSeg - 1) / kHvpSeg : 0;
+            int x = ns;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFullMask, x, o);
+                if (lane >= o) x += y;
+            }
+            if (I < nbs) upre[I] = run + x - ns;  // first unit of row I
+            run += __shfl_sync(kFullMask, x, 31);
+        }
+        if (lane == 0) n_units = run;
+    }
+    __syncthreads();
     for (;;) {
-        int row = 0;
-        if (lane == 0) row = atomicAdd(&next_row, 1);
-        const int I = __shfl_sync(kFullMask, row, 0) * CL + rank;
-        if (I >= nbs) break;
+        int u = 0;
+        if (lane == 0) u = atomicAdd(&next_row, 1);
+        u = __shfl_sync(kFullMask, u, 0);
+        if (u >= n_units) break;
+        int lo = 0, hi = nbs;  // the last row whose first unit is <= u
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (upre[mid] <= u) lo = mid; else hi = mid;
+        }
+        int I = lo;
+        while (I % CL != rank) --I;  // rows of the other CTA own no units here
+        const int j0 = I + kHvpSeg * (u - upre[I]);
         const float4 al = sm.blo[I], ah = sm.bhi[I];
         if (!(al.x <= ah.x)) continue;  // no atoms in block I (warp-uniform)
-        float hix = 0.f, hiy = 0.f, hiz = 0.f;  // this quarter's share of atom 8 I + l8
-        for (int j0 = I; j0 < nbs; j0 += 32) {
-            const int J = j0 + lane;
-            bool hit = false;
-            if (J < nbs) {
-                const float4 bl = sm.blo[J], bh = sm.bhi[J];
-                const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
-                const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
-                const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
-                hit = bl.x <= bh.x && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2;
-            }
-            unsigned m = __ballot_sync(kFullMask, hit);
-            while (m) {
-                const int nh = min(__popc(m), 4);
-                unsigned mm = m;
-                for (int k = 0; k < q; ++k) mm &= mm - 1u;
-                const int src = __ffs(mm) - 1;
-                for (int k = 0; k < nh; ++k) m &= m - 1u;
-                const bool live = q < nh;
-                hvp_item<ELEC>(sm, P.pc, I, live ? j0 + src : I, lane, live, hix, hiy, hiz);
-            }
+        const int J = j0 + lane;
+        bool hit = false;
+        if (lane < kHvpSeg && J < nbs) {
+            const float4 bl = sm.blo[J], bh = sm.bhi[J];
+            const float gx = fmaxf(0.f, fmaxf(al.x - bh.x, bl.x - ah.x));
+            const float gy = fmaxf(0.f, fmaxf(al.y - bh.y, bl.y - ah.y));
+            const float gz = fmaxf(0.f, fmaxf(al.z - bh.z, bl.z - ah.z));
+            hit = bl.x <= bh.x && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < P.pc.rc2;
         }
-        // the four quarters' shares of the row's atoms (FP32, a fixed order)
+        unsigned m = __ballot_sync(kFullMask, hit);
+        if (!m) continue;
+        float hix = 0.f, hiy = 0.f, hiz = 0.f;  // this quarter's share of atom 8 I + l8
+        while (m) {
+            const int nh = min(__popc(m), 4);
+            unsigned mm = m;
+            for (int k = 0; k < q; ++k) mm &= mm - 1u;
+            const int src = __ffs(mm) - 1;
+            for (int k = 0; k < nh; ++k) m &= m - 1u;
+            const bool live = q < nh;
+            hvp_item<ELEC>(sm, P.pc, I, live ? j0 + src : I, lane, live, hix, hiy, hiz);
+        }
+        // the four quarters' shares of the unit's i atoms (FP32, a fixed order)
         hix += __shfl_xor_sync(kFullMask, hix, 8);
         hiy += __shfl_xor_sync(kFullMask, hiy, 8);
         hiz += __shfl_xor_sync(kFullMask, hiz, 8);
@@ -334,9 +365,6 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
         hiz += __shfl_xor_sync(kFullMask, hiz, 16);
         if (lane < 8) hadd(sm, 8 * I + lane, hix, hiy, hiz);
     }
-    const int t0 = threadIdx.x * CL + rank, tstep = blockDim.x * CL;
-    for (int b = t0; b < tp.n_bonds; b += tstep) hvp_bond(sm, tp, b);
-    for (int a = t0; a < tp.n_angles; a += tstep) hvp_angle(sm, tp, a);
     hvp_cluster_sync<CL>();  // every partial of the cluster is complete
     float* out = HV + f * n * 3;
     const int* o2 = CL == 1 ? sm.H2 : cg::this_cluster().map_shared_rank(sm.H2, (unsigned)(rank ^ 1));
