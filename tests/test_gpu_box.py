@@ -170,3 +170,18 @@ def test_box_list_is_tight_and_complete(torch_cuda, box):
     n_in = len(cKDTree(x, boxsize=b.box).query_pairs(1.0)) - len(b.chain.exclusions)
     assert n_in < slots < 3.5 * n_in
     s.close()
+
+
+def test_box_hvp_is_refused(torch_cuda, box):
+    # the Hessian-vector kernels take no periodic images: a periodic system is refused
+    torch = torch_cuda
+    import paper_1705_02180_gb300 as pkg
+    b = box
+    s = make(pkg, b, 1)
+    X = torch.from_numpy(np.asarray(b.x, np.float32)[None]).cuda()
+    V = torch.zeros_like(X)
+    HV = torch.zeros_like(X)
+    with pytest.raises(pkg.ScpsError) as e:
+        s.hvp(0, X, V, HV)
+    assert e.value.code == -7  # UNSUPPORTED
+    s.close()
