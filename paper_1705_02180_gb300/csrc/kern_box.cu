@@ -611,11 +611,11 @@ __device__ __forceinline__ void box_cluster_forces(const BoxDev& B, const TopoDe
                 xj.y = fmaf((float)((int)((e >> 26) & 3u) - 1), B.L, xj.y);
                 xj.z = fmaf((float)((int)((e >> 28) & 3u) - 1), B.L, xj.z);
             }
-            lj = B.par[base + sj];
-            idj = B.id[base + sj];
+            if (EXCL || MINIMG) idj = B.id[base + sj];  // ids serve exclusions and the image test
         }
         bool fast = false;
         if constexpr (!EXCL && !MINIMG) fast = __all_sync(kFullB, ipure && ((e >> 30) & 1u));
+        if (real && !fast) lj = B.par[base + sj];  // the fast path takes the reference constants
         int fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
         bool good;
         if (k0 == 0) {
@@ -643,6 +643,7 @@ __device__ __forceinline__ void box_cluster_forces(const BoxDev& B, const TopoDe
                 atomicAdd(&acc[2 * (size_t)B.np + sj], (unsigned long long)((long long)fjz * 128));
             }
         } else {
+            if (real && fast) lj = B.par[base + sj];  // the slow path uses the general form
             box_chunk_slow<ELEC, ENERGY, EXCL, MINIMG>(B, P.pc, sx, sp, sid, sem, xj, lj, idj, sj,
                                                       8 * c, k0 == 0, lane, acc, e18);
         }
