@@ -185,3 +185,29 @@ def test_box_hvp_is_refused(torch_cuda, box):
         s.hvp(0, X, V, HV)
     assert e.value.code == -7  # UNSUPPORTED
     s.close()
+
+
+def test_box_call_split_does_not_change_results(torch_cuda, box):
+    # every call opens with a direct re-evaluation of the current configuration (no scheduled
+    # rebuild) and then runs its steps as graphs with the rebuild in a conditional node: the
+    # split of the steps into calls does not change the bits, frames included
+    import paper_1705_02180_gb300 as pkg
+    b = box
+    c = b.chain
+    pairs = c.contacts if len(c.contacts) else np.array([[0, c.n_atoms - 1]])
+    R = 2
+    v0 = f32(b.velocities(R, KT, 6))
+    out = []
+    for split in ((30,), (7, 23), (1, 1, 28)):
+        s = make(pkg, b, R, v0=v0, save_interval=5, max_frames=8, rebuild_every=6)
+        s.set_contact_bias([pairs], [c.x_native], k_R=1e-4)
+        for n in split:
+            s.step(n)
+        assert not s.status()[1].any()
+        out.append((s.get_state(), s.collect_paths()))
+        s.close()
+    for st, paths in out[1:]:
+        for k in ("x", "v", "zm", "T", "step"):
+            assert np.array_equal(out[0][0][k], st[k]), k
+        for p, q in zip(out[0][1], paths):
+            assert np.array_equal(p["frames"], q["frames"]) and np.array_equal(p["epot"], q["epot"])
