@@ -610,7 +610,8 @@ def main():
                                    f"{FLOPS_ANGLE} x {len(c.angles)} angles + {FLOPS_CONTACT} x "
                                    f"{len(c.contacts)} contacts + {FLOPS_ATOM_UPDATE} x {n} atoms",
                            "in_cutoff_pairs": p_in,
-                           "pair_slots_evaluated": info["pair_checks_per_step"] / R},
+                           "pair_slots_evaluated": info["pair_checks_per_step"] / R,
+                           "pair_interactions_per_s": p_in * R * spc * args.steps * world / t_dev},
               "force_err": ferr,
               "gpu_launches": int(info["graph_nodes_last_call"]) * args.steps,
               "clocks": clk, "wall_s": t_wall}
