@@ -6,7 +6,8 @@ residues; stand-in for the ~550-atom Fip35 domain), thermally unfolded start
 (X_N run 2 ns at 600 K by the FP64 oracle, stored), T = 300 K, gamma = 1/ps,
 dt = 2 fs, ratchet bias on the native-contact coordinate z with k_R = 1e-4
 kJ/mol, FP32 force terms with fixed-point sums, 10^5 steps in total. The CTA
-shape and the pair-list skin are picked by the autotuner before the warm-up. One bench step = one scps_step_replicas call of 1000 MD steps for every
+shape and the pair-list skin are picked by the autotuner before the warm-up.
+One bench step = one scps_step_replicas call of 1000 MD steps for every
 replica; K bench steps are timed with CUDA events on the launching stream,
 with an L2 flush (a 512 MB write) between calls outside the events.
 
