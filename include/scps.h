@@ -231,7 +231,14 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b);
 
 /* Advances every replica by n_steps steps (rMD: forces, z, ratchet, update,
  * frame output). Stream-ordered on `stream`; returns after enqueueing. Device
- * errors of the enqueued work are reported by scps_get_status. */
+ * errors of the enqueued work are reported by scps_get_status.
+ * Chains (RESIDENT form): one launch per group and chunk of steps_per_graph steps, each a
+ * CUDA graph captured on first use; the pair lists are built inside the kernel.
+ * Periodic box: the call first evaluates the current configuration again (no scheduled
+ * rebuild, so the split of steps into calls does not change results), then runs every step
+ * as one CUDA graph whose pair-list rebuild sits in a conditional node that runs only when
+ * some replica's rebuild is due; the step counters advance one step at a time (a replica
+ * frozen by an error keeps the count it had). */
 int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream);
 
 /* Potential energy, forces and z for n_frames configurations of topology
