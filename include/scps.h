@@ -245,7 +245,11 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream);
  * `topo` (no bias force, no state change). X: device float, n_frames x
  * n_atoms x 3. U: device double, n_frames (total physical energy). F: device
  * float, n_frames x n_atoms x 3, may be NULL. z: device double, n_frames, may
- * be NULL (needs the contact list of a contact or tube bias). Stream-ordered. */
+ * be NULL (needs the contact list of a contact or tube bias). Stream-ordered. Each frame's
+ * pair list is built in a scratch owned by the system (grown, with a device synchronisation,
+ * when a call needs more frames per launch than any before): calls of one system on
+ * different streams must not overlap in time (order them with events, or use one stream);
+ * scps_hvp uses no such scratch. */
 int scps_energy_forces(scps_system* s, int32_t topo, int64_t n_frames, const float* X,
                        double* U, float* F, double* z, void* stream);
 

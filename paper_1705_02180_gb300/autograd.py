@@ -90,8 +90,10 @@ class ForceNormAction(torch.autograd.Function):
     """sum_t |grad U(X_t)|^2 over all frames X (float64 scalar) with activation
     checkpointing over segments of frames: the forward evaluates every frame in one launch
     and keeps only the positions; the backward recomputes the forces of each segment and
-    applies 2 H(X_t) grad U(X_t) to it (one force launch and one HVP launch per segment, so
-    at most one segment's forces are live). First order only, like ForceNormSquared."""
+    applies 2 H(X_t) grad U(X_t) to it (one force launch and one HVP launch per segment).
+    The force launches run in order on one side stream (they share the system's list
+    scratch), the HVP launches on another, so that segment k's HVP overlaps segment k+1's
+    forces; two segments' forces are live at most. First order only, like ForceNormSquared."""
 
     @staticmethod
     def forward(ctx, X, system, topo, segment):
@@ -107,13 +109,30 @@ class ForceNormAction(torch.autograd.Function):
     def backward(ctx, g):
         (X,) = ctx.saved_tensors
         seg = min(ctx.segment, X.shape[0])
-        U = torch.empty(seg, dtype=torch.float64, device=X.device)
-        F = torch.empty((seg,) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
+        cur = torch.cuda.current_stream()
+        fs, hs = torch.cuda.Stream(), torch.cuda.Stream()  # forces, HVPs
+        fs.wait_stream(cur)
+        hs.wait_stream(cur)
+        U = [torch.empty(seg, dtype=torch.float64, device=X.device) for _ in range(2)]
+        F = [torch.empty((seg,) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
+             for _ in range(2)]
         HV = torch.empty_like(X)
-        for s in range(0, X.shape[0], seg):
+        done_f, done_h = [], []
+        for k, s in enumerate(range(0, X.shape[0], seg)):
             n = min(seg, X.shape[0] - s)
-            ctx.system.energy_forces(ctx.topo, X[s:s + n], U[:n], F[:n])
-            ctx.system.hvp(ctx.topo, X[s:s + n], F[:n].mul_(-2.0), HV[s:s + n])  # v = 2 grad U
+            b = k & 1
+            if k >= 2:
+                fs.wait_event(done_h[k - 2])  # the HVP that read this buffer has finished
+            with torch.cuda.stream(fs):
+                ctx.system.energy_forces(ctx.topo, X[s:s + n], U[b][:n], F[b][:n])
+                F[b][:n].mul_(-2.0)  # v = 2 grad U
+                done_f.append(fs.record_event())
+            hs.wait_event(done_f[k])
+            with torch.cuda.stream(hs):
+                ctx.system.hvp(ctx.topo, X[s:s + n], F[b][:n], HV[s:s + n])
+                done_h.append(hs.record_event())
+        cur.wait_stream(fs)
+        cur.wait_stream(hs)
         return HV * g.to(HV.dtype), None, None, None
 
 
