@@ -9,7 +9,7 @@ import oracle
 import synth
 
 
-@pytest.mark.parametrize("n_res", [19, 35])
+@pytest.mark.parametrize("n_res", [19, 35, 75])
 def test_stored_unfolded_chain(n_res):
     if synth.chain.thermal_unfolded(n_res) is None:
         pytest.skip("no stored unfolded chain of this size")
