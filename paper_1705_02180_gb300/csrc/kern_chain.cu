@@ -1106,11 +1106,12 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     if (tube) {  // second work phase: the bias force per contact, then G is complete
         int* counter2 = &sc.work_next2[b];
         const int n2 = (ncon + kTubeItem - 1) / kTubeItem;
+        int m2 = 0;  // the next item index is pulled while the current item runs
+        if (lane == 0) m2 = atomicAdd(counter2, 1);
         for (;;) {
-            int m = 0;
-            if (lane == 0) m = atomicAdd(counter2, 1);
-            const int k = __shfl_sync(kFull, m, 0) * CL + rank;
+            const int k = __shfl_sync(kFull, m2, 0) * CL + rank;
             if (k >= n2) break;
+            if (lane == 0) m2 = atomicAdd(counter2, 1);
             tube_pass2(sm, sc, tp, P, GH, GL, k * kTubeItem, lane);
         }
         cluster_barrier<CL>();  // the peer reads this CTA's G next
