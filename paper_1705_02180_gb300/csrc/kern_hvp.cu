@@ -25,7 +25,7 @@ namespace scps {
 namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kHvpSeg = 16;          // candidate blocks J per work unit
+constexpr int kHvpSeg = 8;           // candidate blocks J per work unit
 constexpr int kHvpMaxBlocks = 512;   // 8-atom blocks per frame (4096 atoms)
 
 struct HvpShared {
@@ -300,8 +300,8 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
     const int t0 = threadIdx.x * CL + rank, tstep = blockDim.x * CL;
     for (int b = t0; b < tp.n_bonds; b += tstep) hvp_bond(sm, tp, b);
     for (int a = t0; a < tp.n_angles; a += tstep) hvp_angle(sm, tp, a);
-    // work units: the rows of blocks I with I % CL == rank, each cut into segments of 16
-    // candidate blocks J >= I (long rows first); a warp pulls a unit, tests its 16 blocks
+    // work units: the rows of blocks I with I % CL == rank, each cut into segments of kHvpSeg
+    // candidate blocks J >= I (long rows first); a warp pulls a unit, tests its blocks
     // against I's box and takes the hits four items at a time
     if (warp == 0) {
         int run = 0;
