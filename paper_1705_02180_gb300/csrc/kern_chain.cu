@@ -47,7 +47,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kChunk = 32;    // contacts / bonds / angles per work item (one per lane)
-constexpr int kTubeItem = 8;  // contacts per work item of the contact-map tube passes
 
 // Shared-memory arrays of one CTA. Atom slots: nta real or padding slots plus 8 sentinel
 // slots (a block far from everything) that absorb the padding of list chunks.
@@ -530,9 +529,9 @@ __device__ __forceinline__ float contact_C_f32(float u) {
 // reference slice k, added in fixed point (2^-40) to the lane's running sums dacc
 // (exact integer sums: independent of which warp takes which item). Lanes 0..7
 // compute C of the item's contacts; then lane l takes slices l, l + 32, ... The
-// item's rows of the reference maps are contiguous (contact-major, K per row), so
-// each load instruction reads consecutive slices, and the eight rows of one slice
-// block are loaded before any is used.
+// reference maps are stored by item, slice-major inside an item (the eight contacts'
+// values of one slice side by side, zero past the last contact), so a lane reads the
+// eight values of its slice with two 16-byte loads and a warp reads 1 KB in one piece.
 __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, const RunParams& P,
                                            int c0, int lane, long long* dacc) {
     const int nq = min(kTubeItem, tp.n_contacts - c0);
@@ -544,14 +543,14 @@ __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, 
         C = contact_C_f32(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq);
     }
     const int K = P.tube_k;
-    const float* rows = tp.tube_A + (size_t)c0 * K;
+    const float4* slab = reinterpret_cast<const float4*>(tp.tube_A) + (size_t)(c0 / kTubeItem) * K * 2;
 #pragma unroll
     for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
         if (blk * 32 >= K) break;
         const int k = blk * 32 + lane;
-        float a[kTubeItem];
-#pragma unroll
-        for (int q = 0; q < kTubeItem; ++q) a[q] = (q < nq && k < K) ? __ldg(rows + q * K + k) : 0.f;
+        const float4 lo = k < K ? __ldg(slab + 2 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = k < K ? __ldg(slab + 2 * k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float a[kTubeItem] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
         float acc = 0.f;
 #pragma unroll
         for (int q = 0; q < kTubeItem; ++q) {
@@ -567,7 +566,8 @@ __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, 
 // the atoms of contact p is beta_p grad C_p with beta_p = (2/N0) sum_k gamma_k
 // (C_p - <C_p(t'_k)>); h = beta_p C'(u) goes to G like the z gradient (F = -2/r0^2 G).
 // The dots sum_k gamma_k <C_p(t'_k)> are formed with lane l on slices l, l + 32, ...
-// (coalesced rows) and reduced over the warp for the eight contacts at once: three
+// (two 16-byte loads per slice, as in the first pass) and reduced over the warp for
+// the eight contacts at once: three
 // exchange steps halve the values each lane holds, two more finish the sums, so lane
 // L ends with the dot of contact (L >> 2) & 7. The order of every sum is fixed.
 __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, const TopoDev& tp,
@@ -578,7 +578,7 @@ __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, 
     // latency overlaps the slice loads
     const int2 ij = tp.con_ij[c0 + min(lane, nq - 1)];
     const int K = P.tube_k;
-    const float* rows = tp.tube_A + (size_t)c0 * K;
+    const float4* slab = reinterpret_cast<const float4*>(tp.tube_A) + (size_t)(c0 / kTubeItem) * K * 2;
     float v[kTubeItem];
 #pragma unroll
     for (int q = 0; q < kTubeItem; ++q) v[q] = 0.f;
@@ -587,11 +587,11 @@ __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, 
         if (blk * 32 >= K) break;
         const int k = blk * 32 + lane;
         const float g = k < K ? sc.gam[k] : 0.f;
+        const float4 lo = k < K ? __ldg(slab + 2 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = k < K ? __ldg(slab + 2 * k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float a[kTubeItem] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int q = 0; q < kTubeItem; ++q) {
-            const float a = (q < nq && k < K) ? __ldg(rows + q * K + k) : 0.f;
-            v[q] = fmaf(g, a, v[q]);
-        }
+        for (int q = 0; q < kTubeItem; ++q) v[q] = fmaf(g, a[q], v[q]);
     }
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
     float w4[4], w2[2];

@@ -857,11 +857,13 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
             if (em == cudaSuccess) em = cudaDeviceSynchronize();
             cudaFree(d_xn);  // only C0 = C(X_N) is kept
             SCPS_CU(em);
-            if (tube) {  // reference maps, stored [contact][slice]; N0 = sum C0^2 (Eq. sX)
+            if (tube) {  // reference maps, stored [item of kTubeItem contacts][slice][contact
+                         // of the item], zero past the last contact; N0 = sum C0^2 (Eq. sX)
                 if (nc > 0 && !b->ref_maps[t])
                     return fail(SCPS_ERR_INVALID_ARG, "topology %zu: NULL reference maps", t);
                 const int K = b->n_ref;
-                std::vector<float> A((size_t)std::max(nc, 1) * K, 0.f);
+                const size_t n_it = (size_t)std::max((nc + kTubeItem - 1) / kTubeItem, 1);
+                std::vector<float> A(n_it * K * kTubeItem, 0.f);
                 double n0 = 0.0;
                 for (int c = 0; c < nc; ++c) {
                     double d2 = 0.0;
@@ -876,7 +878,7 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b) {
                         const double a = b->ref_maps[t][(size_t)k * nc + c];
                         if (!std::isfinite(a))
                             return fail(SCPS_ERR_NONFINITE, "topology %zu: non-finite reference map", t);
-                        A[(size_t)c * K + k] = (float)a;
+                        A[((size_t)(c / kTubeItem) * K + k) * kTubeItem + c % kTubeItem] = (float)a;
                     }
                 }
                 float* d_A;

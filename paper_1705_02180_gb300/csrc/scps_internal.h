@@ -36,11 +36,14 @@ struct TopoDev {
     const float2* con_C0;      // C0 as float-float (hi, lo)
     const int* con_off;        // n_atoms + 1 offsets into con_nbr
     const int2* con_nbr;       // per atom: (contact index, partner atom)
-    const float* tube_A;       // tube bias: [n_contacts][K] average contact maps <C(t'_k)>
+    const float* tube_A;       // tube bias: average contact maps <C(t'_k)>, stored [item of
+                               // kTubeItem contacts][K][contact of the item], zero-padded
     float tube_inv_n0;         // tube bias: 1 / sum_p C0_p^2 (the norm of Eq. sX)
 };
 
 constexpr int kMaxTubeK = 128;  // reference slices of the contact-map tube bias
+constexpr int kTubeItem = 8;    // contacts per work item of the tube passes (and of the
+                                // blocks in which the reference maps are stored)
 constexpr int kMaxThreadsPair = 768;  // threads per CTA of a 2-CTA cluster (80 registers each)
 
 // Per-replica addressing.
