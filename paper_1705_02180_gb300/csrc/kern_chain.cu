@@ -561,53 +561,56 @@ __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, 
     }
 }
 
-// Contact-map tube bias, second pass over one item of kTubeItem contacts: with
-// gamma_k the weights of the ratchet forces on the slices (dF/dD_k), the force on
+// Contact-map tube bias, second pass over two items of kTubeItem contacts, one per
+// half warp (c0: the first contact of this half's item; has: the half has an item):
+// with gamma_k the weights of the ratchet forces on the slices (dF/dD_k), the force on
 // the atoms of contact p is beta_p grad C_p with beta_p = (2/N0) sum_k gamma_k
 // (C_p - <C_p(t'_k)>); h = beta_p C'(u) goes to G like the z gradient (F = -2/r0^2 G).
-// The dots sum_k gamma_k <C_p(t'_k)> are formed with lane l on slices l, l + 32, ...
-// (two 16-byte loads per slice, as in the first pass) and reduced over the warp for
-// the eight contacts at once: three
-// exchange steps halve the values each lane holds, two more finish the sums, so lane
-// L ends with the dot of contact (L >> 2) & 7. The order of every sum is fixed.
+// The dots sum_k gamma_k <C_p(t'_k)> are formed with lane l of a half on slices l,
+// l + 16, ... (two 16-byte loads per slice, the eight contacts' values side by side)
+// and reduced over the half for the eight contacts at once: three exchange steps
+// halve the values each lane holds, one more finishes the sums, so half lane L ends
+// with the dot of contact L >> 1. The order of every sum is fixed. Two items per warp
+// keep twice the loads in flight per L2 round trip.
 __device__ __forceinline__ void tube_pass2(const Shared& sm, const Scalars& sc, const TopoDev& tp,
                                            const RunParams& P, int* GH, unsigned* GL, int c0,
-                                           int lane) {
-    const int nq = min(kTubeItem, tp.n_contacts - c0);
-    // the contact of lane l (l < nq; clamped elsewhere) is read first, so that its
+                                           bool has, int lane) {
+    const int hl = lane & 15;
+    const int nq = has ? min(kTubeItem, tp.n_contacts - c0) : 0;
+    // the contact of half lane l (l < nq; clamped elsewhere) is read first, so that its
     // latency overlaps the slice loads
-    const int2 ij = tp.con_ij[c0 + min(lane, nq - 1)];
-    const int K = P.tube_k;
+    const int2 ij = has ? tp.con_ij[c0 + min(hl, nq - 1)] : make_int2(0, 0);
+    const int K = has ? P.tube_k : 0;
     const float4* slab = reinterpret_cast<const float4*>(tp.tube_A) + (size_t)(c0 / kTubeItem) * K * 2;
     float v[kTubeItem];
 #pragma unroll
     for (int q = 0; q < kTubeItem; ++q) v[q] = 0.f;
 #pragma unroll
-    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
-        if (blk * 32 >= K) break;
-        const int k = blk * 32 + lane;
-        const float g = k < K ? sc.gam[k] : 0.f;
-        const float4 lo = k < K ? __ldg(slab + 2 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 hi = k < K ? __ldg(slab + 2 * k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int blk = 0; blk < kMaxTubeK / 16; ++blk) {
+        if (blk * 16 >= P.tube_k) break;
+        const int k = blk * 16 + hl;
+        const bool in = k < K;
+        const float g = in ? sc.gam[k] : 0.f;
+        const float4 lo = in ? __ldg(slab + 2 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = in ? __ldg(slab + 2 * k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float a[kTubeItem] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
         for (int q = 0; q < kTubeItem; ++q) v[q] = fmaf(g, a[q], v[q]);
     }
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    const bool b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
     float w4[4], w2[2];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        w4[q] = (b4 ? v[q + 4] : v[q]) + __shfl_xor_sync(kFull, b4 ? v[q] : v[q + 4], 16);
+        w4[q] = (b3 ? v[q + 4] : v[q]) + __shfl_xor_sync(kFull, b3 ? v[q] : v[q + 4], 8);
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-        w2[q] = (b3 ? w4[q + 2] : w4[q]) + __shfl_xor_sync(kFull, b3 ? w4[q] : w4[q + 2], 8);
-    float w1 = (b2 ? w2[1] : w2[0]) + __shfl_xor_sync(kFull, b2 ? w2[0] : w2[1], 4);
-    w1 += __shfl_xor_sync(kFull, w1, 2);
+        w2[q] = (b2 ? w4[q + 2] : w4[q]) + __shfl_xor_sync(kFull, b2 ? w4[q] : w4[q + 2], 4);
+    float w1 = (b1 ? w2[1] : w2[0]) + __shfl_xor_sync(kFull, b1 ? w2[0] : w2[1], 2);
     w1 += __shfl_xor_sync(kFull, w1, 1);
-    const float dot = __shfl_sync(kFull, w1, (lane & 7) * 4);
+    const float dot = __shfl_sync(kFull, w1, (lane & 16) | ((hl & 7) * 2));
     // every lane stays to the end (all exchanges above are full-warp); lanes >= nq
-    // hold a copy of the last contact and add nothing
-    const bool live = lane < nq;
+    // of a half hold a copy of its last contact and add nothing
+    const bool live = hl < nq;
     const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
     const float dx = q.x - a.x, dy = q.y - a.y, dz = q.z - a.z;
     const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq;
@@ -1108,11 +1111,12 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
         const int n2 = (ncon + kTubeItem - 1) / kTubeItem;
         int m2 = 0;  // the next item index is pulled while the current item runs
         if (lane == 0) m2 = atomicAdd(counter2, 1);
-        for (;;) {
-            const int k = __shfl_sync(kFull, m2, 0) * CL + rank;
-            if (k >= n2) break;
+        for (;;) {  // units of two items of this CTA, one per half warp
+            const int u = __shfl_sync(kFull, m2, 0);
+            if (2 * u * CL + rank >= n2) break;
             if (lane == 0) m2 = atomicAdd(counter2, 1);
-            tube_pass2(sm, sc, tp, P, GH, GL, k * kTubeItem, lane);
+            const int k = (2 * u + (lane >> 4)) * CL + rank;
+            tube_pass2(sm, sc, tp, P, GH, GL, k * kTubeItem, k < n2, lane);
         }
         cluster_barrier<CL>();  // the peer reads this CTA's G next
         if (tid == 0) sc.work_next2[b] = 0;
