@@ -524,40 +524,55 @@ __device__ __forceinline__ float contact_C_f32(float u) {
     return num / (num + u2 * u + u2 * u2);
 }
 
-// Contact-map tube bias, first pass over one item of kTubeItem native contacts
-// (c0 .. c0 + 7): the item's share of sum_p (C_p(X) - <C_p(t'_k)>)^2 for every
-// reference slice k, added in fixed point (2^-40) to the lane's running sums dacc
-// (exact integer sums: independent of which warp takes which item). Lanes 0..7
-// compute C of the item's contacts; then lane l takes slices l, l + 32, ... The
+// Contact-map tube bias, first pass over two items of kTubeItem native contacts, one per
+// half warp (c0: the first contact of this half's item; has: the half has an item): the
+// items' shares of sum_p (C_p(X) - <C_p(t'_k)>)^2 for every reference slice k, each
+// item's share rounded to fixed point (2^-40) and added to the lanes' running sums dacc
+// (exact integer sums: independent of which warp takes which item). Half lanes 0..7
+// compute C of their item's contacts; then half lane l takes slices l, l + 16, ... The
 // reference maps are stored by item, slice-major inside an item (the eight contacts'
 // values of one slice side by side, zero past the last contact), so a lane reads the
-// eight values of its slice with two 16-byte loads and a warp reads 1 KB in one piece.
+// eight values of its slice with two 16-byte loads. Lane l keeps the sums of slices l,
+// l + 32, ...: of each pair of 16-slice blocks the half keeps one block's values and
+// swaps the other with the opposite half.
 __device__ __forceinline__ void tube_pass1(const Shared& sm, const TopoDev& tp, const RunParams& P,
-                                           int c0, int lane, long long* dacc) {
-    const int nq = min(kTubeItem, tp.n_contacts - c0);
+                                           int c0, bool has, int lane, long long* dacc) {
+    const int hl = lane & 15;
+    const bool h1 = lane & 16;
+    const int nq = has ? min(kTubeItem, tp.n_contacts - c0) : 0;
     float C = 0.f;
-    if (lane < nq) {
-        const int2 ij = tp.con_ij[c0 + lane];
+    if (hl < nq) {
+        const int2 ij = tp.con_ij[c0 + hl];
         const float4 a = sm.xq[ij.x], q = sm.xq[ij.y];
         const float dx = q.x - a.x, dy = q.y - a.y, dz = q.z - a.z;
         C = contact_C_f32(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * P.inv_r0sq);
     }
     const int K = P.tube_k;
     const float4* slab = reinterpret_cast<const float4*>(tp.tube_A) + (size_t)(c0 / kTubeItem) * K * 2;
+    float even = 0.f;  // this lane's sum of the even block of the current pair of blocks
 #pragma unroll
-    for (int blk = 0; blk < kMaxTubeK / 32; ++blk) {
-        if (blk * 32 >= K) break;
-        const int k = blk * 32 + lane;
-        const float4 lo = k < K ? __ldg(slab + 2 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 hi = k < K ? __ldg(slab + 2 * k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int blk = 0; blk < kMaxTubeK / 16; ++blk) {
+        if (blk * 16 >= K) break;
+        const int k = blk * 16 + hl;
+        const bool in = has && k < K;
+        const float4 lo = in ? __ldg(slab + 2 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = in ? __ldg(slab + 2 * k + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float a[kTubeItem] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
         float acc = 0.f;
 #pragma unroll
         for (int q = 0; q < kTubeItem; ++q) {
-            const float d = __shfl_sync(kFull, C, q) - a[q];
+            const float d = __shfl_sync(kFull, C, (lane & 16) | q) - a[q];
             acc = q < nq ? fmaf(d, d, acc) : acc;
         }
-        dacc[blk] += __float2ll_rn(acc * 1099511627776.0f);  // 2^40
+        const bool last = (blk + 1) * 16 >= K;
+        if ((blk & 1) == 0 && !last) {
+            even = acc;
+            continue;
+        }
+        const float e0 = (blk & 1) ? even : acc, o1 = (blk & 1) ? acc : 0.f;
+        const float other = __shfl_xor_sync(kFull, h1 ? e0 : o1, 16);
+        dacc[blk >> 1] += __float2ll_rn((h1 ? o1 : e0) * 1099511627776.0f) +  // 2^40
+                          __float2ll_rn(other * 1099511627776.0f);
     }
 }
 
@@ -976,14 +991,15 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
     // Work list of this CTA: pair batches (four items from its item table each), blocks
     // with themselves (four per batch), then its shares of the contact, bond and angle
     // chunks (global chunk g belongs to CTA g % CL). Under the contact-map tube bias the
-    // contact items are first-pass items of kTubeItem contacts (loads from the reference
-    // maps in L2), interleaved one to one with the pair batches so that their memory
-    // latency overlaps arithmetic.
+    // contact items are first-pass units of two items of kTubeItem contacts (loads from
+    // the reference maps in L2), interleaved one to one with the pair batches so that
+    // their memory latency overlaps arithmetic.
     const int n_pb = (sc.n_items + 3) >> 2;
     const int n_db = (sc.n_diag + 3) >> 2;
     const bool tube = TUBE && do_ratchet;  // contact-map tube bias: two work phases
     const int ncon = (P.bias == 1 || P.bias == 5) ? tp.n_contacts : 0;  // frames: z too
-    const int g_con = tube ? (ncon + kTubeItem - 1) / kTubeItem : (ncon + kChunk - 1) / kChunk;
+    const int g_con = tube ? ((ncon + kTubeItem - 1) / kTubeItem + 1) / 2  // two items a unit
+                           : (ncon + kChunk - 1) / kChunk;
     const int g_bond = (tp.n_bonds + kChunk - 1) / kChunk;
     const int g_ang = (tp.n_angles + kChunk - 1) / kChunk;
     const int n_con = (g_con - rank + CL - 1) / CL;
@@ -1018,7 +1034,10 @@ __device__ void evaluate(Shared& sm, Scalars& sc, const TopoDev& tp, const RunPa
             } else {
                 const int g = kc * CL + rank;
                 if (tube) {
-                    if constexpr (TUBE) tube_pass1(sm, tp, P, g * kTubeItem, lane, dacc);
+                    if constexpr (TUBE) {
+                        const int c0 = (2 * g + (lane >> 4)) * kTubeItem;
+                        tube_pass1(sm, tp, P, c0, c0 < ncon, lane, dacc);
+                    }
                 } else {
                     const int c = g * kChunk + lane;
                     if (c < ncon) zacc += contact_term(sm, GH, GL, tp, P, c);
