@@ -18,9 +18,9 @@
 // block I the list holds, in ascending order, every atom j of a later block that
 // lies within r_list = r_c + skin of some atom of I, in chunks of 8 (the last one
 // padded with a far-away sentinel slot). A work item is one block against one
-// chunk (64 pairs) on a quarter warp: lane l keeps atom j_l of the chunk and the
-// block's atoms rotate through the lanes, so the i-force accumulators rotate one
-// lane per pair while the j-force stays in place. Pairs inside a block form 28-pair
+// chunk (64 pairs) on a quarter warp: lane l keeps atom j_l of the chunk and takes
+// block atom l ^ t at its pair t, so the i-force accumulators move by one xor exchange
+// per pair while the j-force stays in place. Pairs inside a block form 28-pair
 // items of their own. The list is rebuilt when a bound on the largest displacement
 // since the last build reaches skin/2, or after rebuild_every steps, so no pair
 // inside r_c is ever missing.
@@ -232,9 +232,8 @@ __device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsign
                                                const TopoDev& tp, const PairConst& pc, int I, int j,
                                                unsigned long long xm, int lane, long long& e18) {
     const int l8 = lane & 7, q = lane >> 3;
-    // bit t of xr: the pair this lane takes at iteration t (block atom (l8 + t) & 7) is excluded
+    // bit t of xr: the pair this lane takes at iteration t (block atom l8 ^ t) is excluded
     const unsigned xr = NEARX ? (unsigned)(xm >> (8 * l8)) & 0xffu : 0u;
-    const int src = (lane & 24) | ((l8 + 1) & 7);
     const float4 xj = sm.xq[j];
     const float2 lj = sm.lj[j];
     const int i0 = 8 * I;
@@ -243,7 +242,7 @@ __device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsign
     bool bad = false;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        const int i = i0 + ((l8 + t) & 7);
+        const int i = (i0 | l8) ^ t;  // block atom l8 ^ t
         const float4 xi = sm.xq[i];
         const float2 li = sm.lj[i];
         const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
@@ -265,12 +264,14 @@ __device__ __forceinline__ bool pair_item_fast(const Shared& sm, int* FH, unsign
         fjy -= ty;
         fjz -= tz;
         if (ENERGY) ei += ok ? __float2int_rn(e * kPairEScale) : 0;
-        fix = __shfl_sync(kFull, fix, src);
-        fiy = __shfl_sync(kFull, fiy, src);
-        fiz = __shfl_sync(kFull, fiz, src);
+        if (t < 7) {  // the sums of block atom l8 ^ t go to the lane that takes it next
+            fix = __shfl_xor_sync(kFull, fix, t ^ (t + 1));
+            fiy = __shfl_xor_sync(kFull, fiy, t ^ (t + 1));
+            fiz = __shfl_xor_sync(kFull, fiz, t ^ (t + 1));
+        }
     }
     if ((__ballot_sync(kFull, bad) >> (8 * q)) & 0xffu) return false;
-    const int s3 = sm.na8, i = i0 + l8;  // after 8 rotations lane l holds block atom l
+    const int s3 = sm.na8, i = (i0 | l8) ^ 7;  // after the last exchange lane l holds atom l ^ 7
     red_fix13(FH, FL, i, fix);
     red_fix13(FH, FL, s3 + i, fiy);
     red_fix13(FH, FL, 2 * s3 + i, fiz);
@@ -931,7 +932,7 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
         }
         __syncwarp();  // (the records above are complete before their masks are written)
         // excluded pairs of the near items, in the order the lanes meet them (byte s, bit t:
-        // entry s with block atom (s + t) & 7); four chunks per pass, eight lanes each, the
+        // entry s with block atom s ^ t); four chunks per pass, eight lanes each, the
         // block atoms' exclusion words held by lanes 0..7
         const unsigned long long exa = (lane < 8 && 8 * I + lane < n) ? tp.excl[8 * I + lane] : 0ull;
         const uint16_t* e = L.jl + list_jl_off(L.nbs, I);
@@ -941,7 +942,7 @@ __device__ void build_list(const Shared& sm, Scalars& sc, const TopoDev& tp, flo
             unsigned byte = 0u;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int a = (sl + t) & 7, i = 8 * I + a;
+                const int a = sl ^ t, i = 8 * I + a;
                 const unsigned long long ex = __shfl_sync(kFull, exa, a);
                 const int dj = jj - i + kExclWindow;  // entries lie after the block
                 if (c < cn && dj < 2 * kExclWindow && ((ex >> dj) & 1ull)) byte |= 1u << t;
