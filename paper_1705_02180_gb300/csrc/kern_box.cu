@@ -461,9 +461,9 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
 }
 
 // The 64 pairs of one chunk (8 list entries) with the 8 atoms of the i cluster, on a quarter
-// warp: lane l holds entry j_l; at iteration t it takes cluster atom (l + t) & 7, so the
-// i-force sums rotate one lane per iteration (after 8 lane l holds atom l's) while the j
-// force stays in the lane. Each pair term s (x_j - x_i) is rounded to 2^-13 units and summed
+// warp: lane l holds entry j_l; at iteration t it takes cluster atom l ^ t, so the i-force
+// sums move by one xor exchange per iteration (after the eighth, xor 7, lane l holds atom
+// l's again) while the j force stays in the lane. Each pair term s (x_j - x_i) is rounded to 2^-13 units and summed
 // in 32-bit registers. FIRST: quarter 0 holds the cluster's own slots, whose pairs count
 // once (j slot after i slot). EXCL: exclusion masks (clusters holding chain atoms); MINIMG:
 // per-pair minimum image; FAST: every atom has the reference LJ parameters, whose pair
@@ -476,12 +476,11 @@ __device__ __forceinline__ bool box_chunk(const BoxDev& B, const PairConst& pc, 
                                           int idj, int lane, int& fix, int& fiy, int& fiz,
                                           int& fjx, int& fjy, int& fjz, long long& e18) {
     const int l8 = lane & 7, q = lane >> 3;
-    const int src = (lane & 24) | ((l8 + 1) & 7);
     long long ech = 0;
     bool bad = false;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        const int ii = (l8 + t) & 7;
+        const int ii = l8 ^ t;
         const float4 xi = sx[ii];
         float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         if (MINIMG) {
@@ -520,9 +519,10 @@ __device__ __forceinline__ bool box_chunk(const BoxDev& B, const PairConst& pc, 
         fjy -= ty;
         fjz -= tz;
         if (ENERGY) ech += ok ? __float2int_rn(ep * kPairEScale) : 0;
-        fix = __shfl_sync(kFullB, fix, src);
-        fiy = __shfl_sync(kFullB, fiy, src);
-        fiz = __shfl_sync(kFullB, fiz, src);
+        const int m = t < 7 ? t ^ (t + 1) : 7;  // to the lane that takes atom l8 ^ t next
+        fix = __shfl_xor_sync(kFullB, fix, m);
+        fiy = __shfl_xor_sync(kFullB, fiy, m);
+        fiz = __shfl_xor_sync(kFullB, fiz, m);
     }
     const bool good = !((__ballot_sync(kFullB, bad) >> (8 * q)) & 0xffu);
     if (ENERGY && good) e18 += ech;
