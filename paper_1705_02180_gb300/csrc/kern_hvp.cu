@@ -111,16 +111,15 @@ __device__ __forceinline__ void pair_hvp_term(const HvpShared& sm, const PairCon
 }
 
 // The 64 pairs of block I (8 atoms) with block J >= I on a quarter warp: lane l holds atom
-// j = 8 J + l; at iteration t it takes atom i = 8 I + ((l + t) & 7), so the i sums rotate one
-// lane per iteration (after 8 lane l again holds atom 8 I + l's) while the j sum stays in the
-// lane and goes to the fixed-point partials after the item. The i sums (hi*) run on over the
+// j = 8 J + l; at iteration t it takes atom i = 8 I + (l ^ t), so the i sums move by one xor
+// exchange per iteration (after the eighth, xor 7, lane l again holds atom 8 I + l's) while
+// the j sum stays in the lane and goes to the fixed-point partials after the item. The i sums (hi*) run on over the
 // items of the row. Within a block (I == J) a pair counts once (j > i). Near blocks test the
 // exclusion masks. An idle quarter (live false) runs along with no terms.
 template <int ELEC>
 __device__ __forceinline__ void hvp_item(const HvpShared& sm, const PairConst& pc, int I, int J,
                                          int lane, bool live, float& hix, float& hiy, float& hiz) {
     const int l8 = lane & 7;
-    const int src = (lane & 24) | ((l8 + 1) & 7);
     const int j = 8 * J + l8;
     const float4 xj = sm.xq[j];
     const float4 vj = sm.vq[j];
@@ -129,7 +128,7 @@ __device__ __forceinline__ void hvp_item(const HvpShared& sm, const PairConst& p
     float hjx = 0.f, hjy = 0.f, hjz = 0.f;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        const int i = 8 * I + ((l8 + t) & 7);
+        const int i = (8 * I + l8) ^ t;
         bool ok = live && (I != J || j > i);
         if (near) {
             const int dj = j - i + kExclWindow;
@@ -143,9 +142,10 @@ __device__ __forceinline__ void hvp_item(const HvpShared& sm, const PairConst& p
         hjx += ax;
         hjy += ay;
         hjz += az;
-        hix = __shfl_sync(kFullMask, hix, src);
-        hiy = __shfl_sync(kFullMask, hiy, src);
-        hiz = __shfl_sync(kFullMask, hiz, src);
+        const int m = t < 7 ? t ^ (t + 1) : 7;  // to the lane that takes atom i next
+        hix = __shfl_xor_sync(kFullMask, hix, m);
+        hiy = __shfl_xor_sync(kFullMask, hiy, m);
+        hiz = __shfl_xor_sync(kFullMask, hiz, m);
     }
     if (live) hadd(sm, j, hjx, hjy, hjz);
 }
