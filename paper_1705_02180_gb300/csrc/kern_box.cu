@@ -873,61 +873,69 @@ __global__ void __launch_bounds__(512) k_box_chain(BoxDev B, const TopoDev* __re
     }
 }
 
-// BAOAB half steps per slot: B closes the evaluated step, A starts the next one.
+// BAOAB half steps per slot: B closes the evaluated step, A starts the next one. The largest
+// squared displacement since the list build goes to the replica's bound with one atomic per
+// warp (every lane reaches the warp reduction; the slots of a warp share their replica).
 __global__ void k_box_integrate(BoxDev B, const TopoDev* __restrict__ topo, StateDev st,
                                 RunParams P, const uint32_t* __restrict__ rep_ids, long long step,
                                 int do_b, int do_a, int step_from_state) {
     const int r = blockIdx.y;
     if (step_from_state) step = st.step[r];  // graph form: the counter the step graph advanced
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B.np) return;
     const size_t base = (size_t)r * B.np;
-    float4 f = take_nb_force(B, r, s);  // also clears the j part (frozen replicas too)
-    const int a = B.id[base + s];
-    if (a < 0 || st.status[r] != 0) return;
-    const TopoDev& tp = *topo;
-    if (a < B.n_chain) {
-        const float4 c = B.fch[(size_t)r * B.n_chain + a];
-        f.x += c.x;
-        f.y += c.y;
-        f.z += c.z;
+    float d2 = 0.f;
+    if (s < B.np) {
+        float4 f = take_nb_force(B, r, s);  // also clears the j part (frozen replicas too)
+        const int a = B.id[base + s];
+        if (a >= 0 && st.status[r] == 0) {
+            const TopoDev& tp = *topo;
+            if (a < B.n_chain) {
+                const float4 c = B.fch[(size_t)r * B.n_chain + a];
+                f.x += c.x;
+                f.y += c.y;
+                f.z += c.z;
+            }
+            const float im = tp.inv_m[a];
+            const float hdt = P.half_dt;
+            float4 v = B.vel[base + s];
+            float4 x = B.pos[base + s];
+            if (do_b) {
+                v.x = fmaf(hdt * im, f.x, v.x);
+                v.y = fmaf(hdt * im, f.y, v.y);
+                v.z = fmaf(hdt * im, f.z, v.z);
+            }
+            if (do_a) {
+                v.x = fmaf(hdt * im, f.x, v.x);
+                v.y = fmaf(hdt * im, f.y, v.y);
+                v.z = fmaf(hdt * im, f.z, v.z);
+                x.x = fmaf(hdt, v.x, x.x);
+                x.y = fmaf(hdt, v.y, x.y);
+                x.z = fmaf(hdt, v.z, x.z);
+                const uint4 rb = philox4x32_10(make_uint4((uint32_t)a, rep_ids[r], (uint32_t)step, 0u),
+                                               P.key0, P.key1);
+                const float4 xi = normals4_f32(rb);
+                const float sd = tp.noise_sd[a];
+                v.x = fmaf(P.c1, v.x, sd * xi.x);
+                v.y = fmaf(P.c1, v.y, sd * xi.y);
+                v.z = fmaf(P.c1, v.z, sd * xi.z);
+                x.x = fmaf(hdt, v.x, x.x);
+                x.y = fmaf(hdt, v.y, x.y);
+                x.z = fmaf(hdt, v.z, x.z);
+                if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
+                      isfinite(v.y) && isfinite(v.z)))
+                    atomicOr(&st.status[r], SCPS_FLAG_NONFINITE);
+                B.pos[base + s] = x;
+                const float4 p0 = B.pos_ref[base + s];
+                const float ddx = x.x - p0.x, ddy = x.y - p0.y, ddz = x.z - p0.z;
+                d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            }
+            B.vel[base + s] = v;
+        }
     }
-    const float im = tp.inv_m[a];
-    const float hdt = P.half_dt;
-    float4 v = B.vel[base + s];
-    float4 x = B.pos[base + s];
-    if (do_b) {
-        v.x = fmaf(hdt * im, f.x, v.x);
-        v.y = fmaf(hdt * im, f.y, v.y);
-        v.z = fmaf(hdt * im, f.z, v.z);
+    if (do_a) {  // non-negative floats order as unsigned
+        const unsigned m = __reduce_max_sync(kFullB, __float_as_uint(d2));
+        if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(&B.maxd2[r], m);
     }
-    if (do_a) {
-        v.x = fmaf(hdt * im, f.x, v.x);
-        v.y = fmaf(hdt * im, f.y, v.y);
-        v.z = fmaf(hdt * im, f.z, v.z);
-        x.x = fmaf(hdt, v.x, x.x);
-        x.y = fmaf(hdt, v.y, x.y);
-        x.z = fmaf(hdt, v.z, x.z);
-        const uint4 rb = philox4x32_10(make_uint4((uint32_t)a, rep_ids[r], (uint32_t)step, 0u),
-                                       P.key0, P.key1);
-        const float4 xi = normals4_f32(rb);
-        const float sd = tp.noise_sd[a];
-        v.x = fmaf(P.c1, v.x, sd * xi.x);
-        v.y = fmaf(P.c1, v.y, sd * xi.y);
-        v.z = fmaf(P.c1, v.z, sd * xi.z);
-        x.x = fmaf(hdt, v.x, x.x);
-        x.y = fmaf(hdt, v.y, x.y);
-        x.z = fmaf(hdt, v.z, x.z);
-        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
-              isfinite(v.z)))
-            atomicOr(&st.status[r], SCPS_FLAG_NONFINITE);
-        B.pos[base + s] = x;
-        const float4 p0 = B.pos_ref[base + s];
-        const float ddx = x.x - p0.x, ddy = x.y - p0.y, ddz = x.z - p0.z;
-        const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-        atomicMax(&B.maxd2[r], __float_as_uint(d2));  // non-negative floats order as unsigned
-    }
-    B.vel[base + s] = v;
 }
 
 // Frame output of the evaluated configuration (positions in atom-id order).
@@ -985,10 +993,9 @@ static void box_rebuild(const BoxDev& B, const TopoDev* topo, const StateDev& st
     k_box_list<<<gg, 128, 0, s>>>(B, st, r0);
 }
 
-// Pair forces, then the chain terms and the ratchet, of replicas [r0, r0 + nr).
-static void box_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
-                       int r0, int nr, int elec, int ncon_max, bool energy, int do_ratchet,
-                       int count_step, cudaStream_t s) {
+// Pair forces of replicas [r0, r0 + nr).
+static void box_pairs_launch(const BoxDev& B, const TopoDev* topo, const RunParams& P, int r0, int nr,
+                             int elec, bool energy, cudaStream_t s) {
     const dim3 gg((4 * B.nt + 3) / 4, nr);
 #define PAIRS(E)                                                                                \
     switch (elec) {                                                                             \
@@ -1003,11 +1010,26 @@ static void box_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st,
         PAIRS(false)
     }
 #undef PAIRS
+}
+
+// Chain terms and the ratchet of replicas [r0, r0 + nr) (independent of the pair forces: the
+// integrator adds the two).
+static void box_chain_launch(const BoxDev& B, const TopoDev* topo, const StateDev& st,
+                             const RunParams& P, int r0, int nr, int ncon_max, bool energy,
+                             int do_ratchet, int count_step, cudaStream_t s) {
     const size_t smem = box_chain_smem(B.n_chain, ncon_max);
     if (energy)
         k_box_chain<true><<<nr, 512, smem, s>>>(B, topo, st, P, r0, do_ratchet, count_step);
     else
         k_box_chain<false><<<nr, 512, smem, s>>>(B, topo, st, P, r0, do_ratchet, count_step);
+}
+
+// Pair forces, then the chain terms and the ratchet, of replicas [r0, r0 + nr).
+static void box_forces(const BoxDev& B, const TopoDev* topo, const StateDev& st, const RunParams& P,
+                       int r0, int nr, int elec, int ncon_max, bool energy, int do_ratchet,
+                       int count_step, cudaStream_t s) {
+    box_pairs_launch(B, topo, P, r0, nr, elec, energy, s);
+    box_chain_launch(B, topo, st, P, r0, nr, ncon_max, energy, do_ratchet, count_step, s);
 }
 
 // One force evaluation of replicas [r0, r0 + nr): rebuild when forced (or, when
@@ -1094,8 +1116,22 @@ static cudaError_t box_step_graph(const BoxDev& B, const TopoDev* topo, const St
             if (e == cudaSuccess) e = le;
         }
     }
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e == cudaSuccess) {  // the chain terms run beside the pair forces (second branch)
+        e = cudaEventRecord(fork, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, fork, 0);
+        if (e == cudaSuccess) {
+            box_chain_launch(B, topo, st, P, 0, R, ncon_max, save, 1, 1, cs2);
+            e = cudaEventRecord(join, cs2);
+        }
+        if (e == cudaSuccess) {
+            box_pairs_launch(B, topo, P, 0, R, elec, save, cs);
+            e = cudaStreamWaitEvent(cs, join, 0);
+        }
+    }
     if (e == cudaSuccess) {
-        box_forces(B, topo, st, P, 0, R, elec, ncon_max, save, 1, 1, cs);
         if (save) k_box_frame<<<ga, 256, 0, cs>>>(B, st, P, frame_atoms);
         k_box_integrate<<<ga, 256, 0, cs>>>(B, topo, st, P, rep_ids, 0, 1, last ? 0 : 1, 1);
         if (save) k_box_frame_scalars<<<(R + 127) / 128, 128, 0, cs>>>(B, st, P, R);
@@ -1104,6 +1140,8 @@ static cudaError_t box_step_graph(const BoxDev& B, const TopoDev* topo, const St
     cudaGraph_t out = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &out);
     if (e == cudaSuccess) e = ce;
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
