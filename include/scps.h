@@ -134,11 +134,13 @@ typedef struct {
     double skin;            /* list buffer r_list - r_c (nm); 0 = default (0.15 for the periodic
                                box, 0.12 for chains). A list is rebuilt before any pair inside
                                r_c can be missing: periodic box, once an atom has moved skin/2
-                               since the last build; chains, once a bound on every atom's
+                               since the last build (the lists of all live replicas are then
+                               rebuilt together); chains, once a bound on every atom's
                                displacement since then (dt/2 times the largest |v| + |v'| of
                                each step, summed) reaches skin/2. Forces do not depend on the
                                skin or the rebuild cadence (chains: bit for bit). */
-    int32_t rebuild_every;  /* periodic box: scheduled rebuild interval (steps), 0 = 20; chains:
+    int32_t rebuild_every;  /* periodic box: scheduled rebuild interval (steps), 0 = 20, all
+                               live replicas together as soon as one is due; chains:
                                also rebuild at least every this many steps, 0 = only by the
                                displacement bound */
 } scps_system_desc;
@@ -237,7 +239,8 @@ int scps_set_bias(scps_system* s, const scps_bias_desc* b);
  * Periodic box: the call first evaluates the current configuration again (no scheduled
  * rebuild, so the split of steps into calls does not change results), then runs every step
  * as one CUDA graph whose pair-list rebuild sits in a conditional node that runs only when
- * some replica's rebuild is due; the step counters advance one step at a time (a replica
+ * some replica's rebuild is due (it then rebuilds the lists of all live replicas); the step
+ * counters advance one step at a time (a replica
  * frozen by an error keeps the count it had). */
 int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream);
 
@@ -317,7 +320,7 @@ int scps_path_average(scps_system* s, int32_t n_sel, const int32_t* replicas, in
  * 40} steps (a rebuild also comes earlier once an atom has moved skin/2), probed the
  * same way from a device snapshot of the box state; the probes and the final choice
  * force a list rebuild at the next step, so the trajectory equals that of a run with one
- * more rebuild there (the box's FP32 per-atom sums follow the list order: equal to
+ * more rebuild there (positions are wrapped into the box at each rebuild: equal to
  * rounding, not bit for bit). Cached under (SM count, electrostatics, atoms, replicas).
  * Synchronous; out may be NULL. */
 int scps_autotune(scps_system* s, int32_t probe_steps, int32_t use_cache, scps_tune_result* out);

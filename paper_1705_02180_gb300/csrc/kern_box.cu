@@ -20,7 +20,8 @@
 //   integrate            BAOAB half steps with Philox noise keyed by atom id
 // A rebuild is due every `rebuild_every` steps, or earlier when an atom has
 // moved more than skin/2 since the last one, so every pair inside the cutoff
-// is always in the list. Forces are integer sums of per-pair terms (order-free);
+// is always in the list; once one live replica is due, all live replicas of the
+// batch rebuild together. Forces are integer sums of per-pair terms (order-free);
 // positions are wrapped into the box at each rebuild, so runs that rebuild at
 // other steps agree to rounding.
 #include "scps_internal.h"
@@ -56,44 +57,45 @@ __device__ __forceinline__ int warp_rank(float key, int lane, bool member, unsig
 
 }  // namespace
 
-// Rebuild, step 1a (one CTA per replica): decide; on a rebuild clear the key
-// counts and the bookkeeping of the displacement test.
-__global__ void k_box_decide(BoxDev B, StateDev st, int r0, int auto_ok) {
-    __shared__ int decide;
-    const int r = blockIdx.x + r0;
-    if (threadIdx.x == 0) {
-        const float d2 = __uint_as_float(B.maxd2[r]);
-        decide = st.status[r] == 0 &&
-                 (B.need[r] || (auto_ok && (B.since[r] >= B.rebuild_every || d2 >= B.skin2_quarter)));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) B.need[r] = decide;  // the later rebuild kernels run iff set
-    if (!decide) return;
-    int* hist = B.hist + (size_t)r * kNumKeys;
-    for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) hist[k] = 0;
-    if (threadIdx.x == 0) {
-        B.since[r] = 0;
-        B.maxd2[r] = 0u;
-    }
-}
-
-// Graph form of step 1a (one CTA for all R replicas): the same decision per replica, and
-// the graph's conditional value: 1 when some replica rebuilds, so that the rebuild kernels
-// run at all only then. The key counts are cleared by k_box_clear_hist inside the rebuild.
-__global__ void k_box_decide_graph(BoxDev B, StateDev st, int R, cudaGraphConditionalHandle h) {
+// Rebuild decision of replicas [r0, r0 + nr) by one CTA: a replica rebuilds when forced
+// (need set), or, when `auto_ok`, as soon as one live replica of the batch is due (its
+// rebuild_every steps are up or its largest displacement reaches skin/2). Lists of all live
+// replicas are then rebuilt together: one rebuild of the whole batch keeps the GPU full,
+// where replicas due at different steps would each rebuild alone. Values are read before
+// any is written, so the decision is the same whatever the thread order. Returns 1 to all
+// threads when some replica rebuilds.
+__device__ int box_decide_batch(const BoxDev& B, const StateDev& st, int r0, int nr, int auto_ok) {
+    int due = 0;
+    if (auto_ok)
+        for (int r = r0 + threadIdx.x; r < r0 + nr; r += blockDim.x) {
+            const float d2 = __uint_as_float(B.maxd2[r]);
+            due |= st.status[r] == 0 && (B.since[r] >= B.rebuild_every || d2 >= B.skin2_quarter);
+        }
+    due = __syncthreads_or(due);
     int any = 0;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        const float d2 = __uint_as_float(B.maxd2[r]);
-        const int decide = st.status[r] == 0 &&
-                           (B.need[r] || B.since[r] >= B.rebuild_every || d2 >= B.skin2_quarter);
-        B.need[r] = decide;
+    for (int r = r0 + threadIdx.x; r < r0 + nr; r += blockDim.x) {
+        const int decide = st.status[r] == 0 && (B.need[r] || due);
+        B.need[r] = decide;  // the later rebuild kernels run iff set
         if (decide) {
             B.since[r] = 0;
             B.maxd2[r] = 0u;
         }
         any |= decide;
     }
-    any = __syncthreads_or(any);
+    return __syncthreads_or(any);
+}
+
+// Rebuild, step 1a: the decision (one CTA for the batch); the key counts of the replicas
+// that rebuild are cleared by k_box_clear_hist.
+__global__ void k_box_decide(BoxDev B, StateDev st, int r0, int nr, int auto_ok) {
+    box_decide_batch(B, st, r0, nr, auto_ok);
+}
+
+// Graph form of step 1a (one CTA for all R replicas): the same decision, and the graph's
+// conditional value: 1 when some replica rebuilds, so that the rebuild kernels run at all
+// only then.
+__global__ void k_box_decide_graph(BoxDev B, StateDev st, int R, cudaGraphConditionalHandle h) {
+    const int any = box_decide_batch(B, st, 0, R, 1);
     if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
@@ -1038,7 +1040,8 @@ static cudaError_t box_eval(const BoxDev& B, const TopoDev* topo, const StateDev
                             const RunParams& P, int r0, int nr, int elec, int ncon_max,
                             bool energy, int do_ratchet, int count_step, int auto_ok,
                             cudaStream_t s) {
-    k_box_decide<<<nr, 256, 0, s>>>(B, st, r0, auto_ok);
+    k_box_decide<<<1, 256, 0, s>>>(B, st, r0, nr, auto_ok);
+    k_box_clear_hist<<<dim3((kNumKeys + 255) / 256, nr), 256, 0, s>>>(B, r0);
     box_rebuild(B, topo, st, r0, nr, s);
     box_forces(B, topo, st, P, r0, nr, elec, ncon_max, energy, do_ratchet, count_step, s);
     return cudaGetLastError();
