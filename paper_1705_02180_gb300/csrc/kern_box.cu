@@ -326,9 +326,14 @@ __global__ void k_box_tiles(BoxDev B, const TopoDev* __restrict__ topo, int r0) 
 // minimum image.
 __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0) {
     __shared__ float4 sxi[4][8];
+    __shared__ int col_tile[kMaxCols + 1];  // first tile of each column (and the end)
     const int r = blockIdx.y + r0;
     if (!B.need[r]) return;
     const int ncl = 4 * B.nt;
+    const int ncols = B.ncol * B.ncol;
+    for (int k = threadIdx.x; k <= ncols; k += blockDim.x)
+        col_tile[k] = B.colinfo[(size_t)r * 2 * (kMaxCols + 1) + kMaxCols + 1 + k];
+    __syncthreads();
     const int w = threadIdx.x >> 5;
     const int c = blockIdx.x * 4 + w;
     if (c >= ncl) return;
@@ -353,10 +358,8 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
         const float hx = 0.5f * (ah.x - al.x), hy = 0.5f * (ah.y - al.y), hz = 0.5f * (ah.z - al.z);
         // candidate columns: an atom within r_list of c lies at most `reach` columns away in x
         // and in y (periodically); columns in ascending order keep the entries ascending
-        const int* col_tile = B.colinfo + (size_t)r * 2 * (kMaxCols + 1) + kMaxCols + 1;
         const float colw = B.L / (float)B.ncol;
         const int reach = (int)ceilf(sqrtf(B.rlist2) / colw);
-        const int ncols = B.ncol * B.ncol;
         int lo = 0, hi = ncols;  // c's column: the last one whose first tile is <= c's tile
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -364,10 +367,16 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
         }
         const int qx = lo / B.ncol, qy = lo % B.ncol;
         for (int col = 0; col < ncols; ++col) {
-            int ddx = abs(col / B.ncol - qx), ddy = abs(col % B.ncol - qy);
+            const int ix = col / B.ncol;
+            int ddx = abs(ix - qx);
             ddx = min(ddx, B.ncol - ddx);
+            if (ddx > reach) {  // the whole row of columns is out of reach
+                col = ix * B.ncol + B.ncol - 1;
+                continue;
+            }
+            int ddy = abs(col - ix * B.ncol - qy);
             ddy = min(ddy, B.ncol - ddy);
-            if (ddx > reach || ddy > reach) continue;
+            if (ddy > reach) continue;
             const int cl1 = 4 * col_tile[col + 1];
             for (int j0 = max(c + 1, 4 * col_tile[col]); j0 < cl1; j0 += 32) {
                 const int jc = j0 + lane;
@@ -404,8 +413,9 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
                     uint32_t e = 0;
                     if (q < nh) {
                         const int sj = 8 * (j0 + src) + l8;
-                        if (B.id[base + sj] >= 0) {
-                            const float4 xj = B.pos[base + sj];
+                        const int idj = B.id[base + sj];
+                        const float4 xj = B.pos[base + sj];  // (loaded with the id: one round trip)
+                        if (idj >= 0) {
                             // the atom under its cluster's shift, first against c's box
                             const float px = xj.x + (float)((int)((hcode >> 24) & 3u) - 1) * B.L,
                                         py = xj.y + (float)((int)((hcode >> 26) & 3u) - 1) * B.L,
@@ -465,8 +475,8 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
 // The 64 pairs of one chunk (8 list entries) with the 8 atoms of the i cluster, on a quarter
 // warp: lane l holds entry j_l; at iteration t it takes cluster atom l ^ t, so the i-force
 // sums move by one xor exchange per iteration (after the eighth, xor 7, lane l holds atom
-// l's again) while the j force stays in the lane. Each pair term s (x_j - x_i) is rounded to 2^-13 units and summed
-// in 32-bit registers. FIRST: quarter 0 holds the cluster's own slots, whose pairs count
+// l's again) while the j force stays in the lane. Each pair term s (x_j - x_i) is rounded to
+// 2^-13 units and summed in 32-bit registers. FIRST: quarter 0 holds the cluster's own slots, whose pairs count
 // once (j slot after i slot). EXCL: exclusion masks (clusters holding chain atoms); MINIMG:
 // per-pair minimum image; FAST: every atom has the reference LJ parameters, whose pair
 // constants U are computed once. Returns false for the quarters where some |s| exceeds
