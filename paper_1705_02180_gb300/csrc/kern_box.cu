@@ -424,15 +424,17 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
                                         by = fmaxf(0.f, fabsf(py - cy) - hy),
                                         bz = fmaxf(0.f, fabsf(pz - cz) - hz);
                             if (fmaf(bx, bx, fmaf(by, by, bz * bz)) < B.rlist2) {
-                                float d2 = 3.0e38f, dm = 0.f;
+                                // empty slots of c sit far away (x beyond 1e5 nm), so all 8
+                                // are tested; dm bounds every per-axis separation from c's atoms
+                                float d2 = 3.0e38f;
 #pragma unroll
                                 for (int t = 0; t < 8; ++t) {
-                                    if (!((ivalid >> t) & 1u)) continue;
                                     const float4 a = sxi[w][t];
                                     const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
                                     d2 = fminf(d2, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                                    dm = fmaxf(dm, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
                                 }
+                                const float dm = fmaxf(fabsf(px - cx) + hx,
+                                                       fmaxf(fabsf(py - cy) + hy, fabsf(pz - cz) + hz));
                                 if (!(dm < 0.5f * B.L)) {  // the shift may not be the minimum image
                                     d2 = 3.0e38f;
                                     for (int t = 0; t < 8; ++t) {
