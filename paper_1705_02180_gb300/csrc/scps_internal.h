@@ -62,8 +62,8 @@ struct RepDev {
 //     of some atom of the block, ascending, padded to a multiple of 8 with the sentinel
 //     slot nta; block I owns 8 (nbs - 1 - I) entries from offset list_jl_off(nbs, I);
 //   item tables (uint32), one per CTA of a cluster: (I << 17 | near << 16 | chunk);
-//   exclusion masks (uint64), one per item of those tables: bit 8 a + s set when block atom a
-//     and chunk entry s form an excluded pair (items near their block only).
+//   exclusion masks (uint64), one per item of those tables: bit 8 s + t set when chunk entry s
+//     and block atom s ^ t form an excluded pair (items near their block only).
 __host__ __device__ __forceinline__ long long list_jl_off(int nbs, int I) {
     return 8ll * ((long long)I * (nbs - 1) - (long long)I * (I - 1) / 2);
 }
