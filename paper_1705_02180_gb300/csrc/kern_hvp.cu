@@ -367,24 +367,16 @@ k_hvp_frames(const TopoDev* __restrict__ topo_ptr, RunParams P, const float* __r
     }
     hvp_cluster_sync<CL>();  // every partial of the cluster is complete
     float* out = HV + f * n * 3;
-    const int* o2[CL];  // every CTA's partials (its own included), summed in integers
-    const unsigned* o1[CL];
-    const unsigned* o0[CL];
-#pragma unroll
-    for (int q = 0; q < CL; ++q) {
-        o2[q] = CL == 1 ? sm.H2 : cg::this_cluster().map_shared_rank(sm.H2, (unsigned)q);
-        o1[q] = CL == 1 ? sm.H1 : cg::this_cluster().map_shared_rank(sm.H1, (unsigned)q);
-        o0[q] = CL == 1 ? sm.H0 : cg::this_cluster().map_shared_rank(sm.H0, (unsigned)q);
-    }
+    const int* o2 = CL == 1 ? sm.H2 : cg::this_cluster().map_shared_rank(sm.H2, (unsigned)(rank ^ 1));
+    const unsigned* o1 = CL == 1 ? sm.H1 : cg::this_cluster().map_shared_rank(sm.H1, (unsigned)(rank ^ 1));
+    const unsigned* o0 = CL == 1 ? sm.H0 : cg::this_cluster().map_shared_rank(sm.H0, (unsigned)(rank ^ 1));
     for (int i = threadIdx.x + rank * blockDim.x; i < n; i += CL * blockDim.x) {
         long long h[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int k = c * nta + i;
-            h[c] = 0;
-#pragma unroll
-            for (int q = 0; q < CL; ++q)
-                h[c] += ((long long)o2[q][k] << 40) + ((long long)o1[q][k] << 20) + (long long)o0[q][k];
+            h[c] = ((long long)sm.H2[k] << 40) + ((long long)sm.H1[k] << 20) + (long long)sm.H0[k];
+            if (CL == 2) h[c] += ((long long)o2[k] << 40) + ((long long)o1[k] << 20) + (long long)o0[k];
         }
         out[3 * i] = fix2f(h[0]);
         out[3 * i + 1] = fix2f(h[1]);
@@ -399,9 +391,8 @@ size_t hvp_smem_bytes(int nta) {
            (sizeof(int) + 2 * sizeof(unsigned)) * 3 * (size_t)nta + sizeof(float2) * nta;
 }
 
-// Few frames (a checkpoint segment): a cluster of 3 (or 2) CTAs of 1024 threads per frame,
-// as many as the SMs hold in one wave, so that the frames spread over the SMs; many frames:
-// one 512-thread CTA each. The result does not depend on the cluster size (integer sums).
+// Few frames (a checkpoint segment): a 2-CTA cluster of 1024 threads per frame, so that
+// the frames spread over the SMs; many frames: one 512-thread CTA each.
 template <int ELEC>
 static cudaError_t launch_hvp_t(const TopoDev* topo, const RunParams& P, const float* X,
                                 const float* V, float* HV, long long n_frames, int nta,
@@ -410,10 +401,10 @@ static cudaError_t launch_hvp_t(const TopoDev* topo, const RunParams& P, const f
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int cl = 3 * n_frames <= n_sm ? 3 : 2 * n_frames <= n_sm ? 2 : 1;
+    const int cl = 2 * n_frames <= n_sm ? 2 : 1;
     const int threads = n_frames * cl <= n_sm ? 1024 : 512;
     const size_t smem = hvp_smem_bytes(nta);
-    auto kern = cl == 3 ? k_hvp_frames<ELEC, 3> : cl == 2 ? k_hvp_frames<ELEC, 2> : k_hvp_frames<ELEC, 1>;
+    auto kern = cl == 2 ? k_hvp_frames<ELEC, 2> : k_hvp_frames<ELEC, 1>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
