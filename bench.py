@@ -347,7 +347,8 @@ def extra_config(torch, pkg, name, args, K, W):
         durs, clk = timed_calls(torch, lambda st: s.step(spc, stream=st), K, W)
         atoms = b.n_atoms * R
         rate = atoms * spc * K / durs.sum()
-        slots = s.info()["pair_checks_per_step"] / R
+        info = s.info()  # (the last timed call: rebuild steps, builds per replica)
+        slots = info["pair_checks_per_step"] / R
         xs = s.get_state()["x"].reshape(R, b.n_atoms, 3)[0] % b.box
         p_in = len(cKDTree(xs, boxsize=b.box).query_pairs(1.0)) - len(c.exclusions)
         t = b.topology()
@@ -364,7 +365,8 @@ def extra_config(torch, pkg, name, args, K, W):
                                       f"sites), L {b.box:.3f} nm, RF, rc 1.0, skin "
                                       f"{tune['skin']:.2f}, rebuild <= {tune['rebuild_every']} "
                                       "steps (autotuned), dt 2 fs, 300 K",
-                          "atoms": atoms, "md_steps_per_call": spc, "autotune": tune},
+                          "atoms": atoms, "md_steps_per_call": spc, "autotune": tune,
+                          "steps_per_list_build": info["steps_per_list_build"]},
                "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                             "frac": ach / peak, "traffic": None,
                             "in_cutoff_pairs_per_replica": p_in,
@@ -373,12 +375,12 @@ def extra_config(torch, pkg, name, args, K, W):
                        "peak_GBps": hbm_peak,
                        "frac": gbs / hbm_peak if hbm_peak else None,
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm_peak else None},
-               # per call: one re-evaluation (decide, 7 list kernels that return at once
-               # unless a rebuild is forced, pairs, chain) + its A half step; per step one
-               # graph of 5 kernels (step counter, decide, pairs, chain, integrate) and, on the
-               # steps that rebuild (at most every rebuild_every steps here), 8 more inside
-               # its conditional node
-               "gpu_launches": K * (11 + 5 * spc + 8 * -(-spc // tune["rebuild_every"])),
+               # per call: one re-evaluation (decide, hist clear, 7 list kernels that return
+               # at once unless a rebuild is forced, pairs, chain) + its A half step; per step
+               # one graph of 5 kernels (step counter, decide, pairs, chain, integrate) and, on
+               # the steps that rebuild, 8 more inside its conditional node (counted on the
+               # device; the last timed call's count times K)
+               "gpu_launches": K * int(info["graph_nodes_last_call"]),
                "clocks": clk}
         rc, st = s.status()
         out["status"] = int(rc)

@@ -180,7 +180,9 @@ typedef struct {
     int32_t cluster_size, threads, steps_per_graph;
     int32_t kernels_per_step_call;      /* kernel launches one scps_step_replicas call enqueues
                                            per graph node (resident form) */
-    int64_t graph_nodes_last_call;      /* kernel launches enqueued by the last step call */
+    int64_t graph_nodes_last_call;      /* kernel launches enqueued by the last step call
+                                           (periodic box: including the 8 rebuild kernels of
+                                           each step that rebuilt; synchronises) */
     int64_t pair_checks_per_step;       /* resident chains: non-bonded pair slots one step
                                            evaluates, summed over replicas, with the pair list
                                            each replica built last (64 per list item of 8 x 8
@@ -193,7 +195,8 @@ typedef struct {
     double list_skin;                   /* pair-list skin r_list - r_c (nm) */
     double steps_per_list_build;        /* resident chains: mean steps per pair-list build in
                                            the latest launch (the build that opens a launch
-                                           counts) */
+                                           counts); periodic box: mean steps per list build
+                                           of a replica in the latest step call */
 } scps_info;
 
 /* launch plans of the resident form */

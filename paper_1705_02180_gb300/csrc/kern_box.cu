@@ -79,6 +79,7 @@ __device__ int box_decide_batch(const BoxDev& B, const StateDev& st, int r0, int
         if (decide) {
             B.since[r] = 0;
             B.maxd2[r] = 0u;
+            B.nbuild[r] += 1;
         }
         any |= decide;
     }
@@ -96,7 +97,10 @@ __global__ void k_box_decide(BoxDev B, StateDev st, int r0, int nr, int auto_ok)
 // only then.
 __global__ void k_box_decide_graph(BoxDev B, StateDev st, int R, cudaGraphConditionalHandle h) {
     const int any = box_decide_batch(B, st, 0, R, 1);
-    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        cudaGraphSetConditional(h, any ? 1u : 0u);
+        if (any) B.nevent[0] += 1;
+    }
 }
 
 __global__ void k_box_clear_hist(BoxDev B, int r0) {

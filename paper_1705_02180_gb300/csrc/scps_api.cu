@@ -668,6 +668,8 @@ int scps_create_system(const scps_system_desc* d, scps_system** out) {
         BALLOC(B.cflag, (size_t)Rs * 4 * B.nt);
         BALLOC(B.need, Rs);
         BALLOC(B.since, Rs);
+        BALLOC(B.nbuild, Rs);
+        BALLOC(B.nevent, 1);
         BALLOC(B.maxd2, Rs);
         BALLOC(B.fch, (size_t)Rs * B.n_chain);
         BALLOC(B.eb, Rs);
@@ -973,13 +975,17 @@ int scps_step_replicas(scps_system* s, int64_t n_steps, void* stream) {
             if (s->host_step[r] != s->host_step[0])
                 return fail(SCPS_ERR_STATE, "periodic-box replicas must share one step counter");
         const long long frame_atoms = (long long)std::max(s->d.max_frames, 1) * s->box.n_atoms;
+        SCPS_CU(cudaMemsetAsync(s->box.nbuild, 0, sizeof(int) * (size_t)(R + 1), cs));
+        SCPS_CU(cudaMemsetAsync(s->box.nevent, 0, sizeof(int), cs));
         SCPS_CU(box_run(s->box, s->d_topos, s->st, P, s->d_rep_ids, R, s->d.elec, s->ncon_max,
                         s->host_step[0], n_steps, frame_atoms, &s->box_graphs, cs));
-        // the evaluation that opens the call (decide, 7 rebuild kernels that return at once
-        // unless a rebuild is forced, pairs, chain) and its A half step; per step one graph
-        // of 5 kernels (step counter, decide, pairs, chain, integrate; 2 more on save steps)
-        // plus 8 inside its conditional node when some replica rebuilds
-        launches = 11 + 5 * n_steps;
+        // the evaluation that opens the call (decide, hist clear, 7 rebuild kernels that
+        // return at once unless a rebuild is forced, pairs, chain) and its A half step; per
+        // step one graph of 5 kernels (step counter, decide, pairs, chain, integrate; 2 more
+        // on save steps) plus 8 inside its conditional node on the steps that rebuild (added
+        // by scps_get_info, which reads their count)
+        launches = 12 + 5 * n_steps;
+        s->last_launch_steps = n_steps;
     } else if (s->d.exec == SCPS_EXEC_PLAIN) {
         P.n_steps = n_steps;
         std::vector<RepDev> reps(R);
@@ -1348,6 +1354,17 @@ int scps_get_info(const scps_system* s, scps_info* info) {
         long long slots = 0;
         for (int v : ne) slots += 8ll * v;
         info->pair_checks_per_step = slots;
+        // list builds and rebuild steps of the latest step call
+        const int R = s->d.n_replicas;
+        std::vector<int> nb(R);
+        int nev = 0;
+        SCPS_CU(cudaMemcpy(nb.data(), s->box.nbuild, sizeof(int) * (size_t)R, cudaMemcpyDeviceToHost));
+        SCPS_CU(cudaMemcpy(&nev, s->box.nevent, sizeof(int), cudaMemcpyDeviceToHost));
+        double builds = 0.0;
+        for (int v : nb) builds += v;
+        if (builds > 0.0 && s->last_launch_steps > 0)
+            info->steps_per_list_build = (double)s->last_launch_steps * (double)R / builds;
+        info->graph_nodes_last_call += 8ll * nev;
     }
     return SCPS_OK;
 }

@@ -168,6 +168,8 @@ struct BoxDev {
                       // reference LJ parameters (the last atom's)
     int* need;        // [replica] rebuild flag
     int* since;       // [replica] evaluations since the last rebuild
+    int* nbuild;      // [replica] list builds since the start of the latest step call
+    int* nevent;      // [1] steps of the latest step call whose graph ran the rebuild kernels
     unsigned* maxd2;  // [replica] largest squared displacement since then (float bits)
     float4* fch;      // [replica][n_chain] bonded + bias force on chain atoms
     double* eb;       // [replica] bonded energy (save steps)

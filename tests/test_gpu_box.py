@@ -211,3 +211,24 @@ def test_box_call_split_does_not_change_results(torch_cuda, box):
             assert np.array_equal(out[0][0][k], st[k]), k
         for p, q in zip(out[0][1], paths):
             assert np.array_equal(p["frames"], q["frames"]) and np.array_equal(p["epot"], q["epot"])
+
+
+def test_box_replicas_rebuild_together(torch_cuda, box):
+    # once one live replica is due, every live replica rebuilds its list at the same step: the
+    # builds per replica of a call equal the steps whose graph ran the rebuild kernels, and the
+    # launch count adds the 8 rebuild kernels for each of those steps
+    import paper_1705_02180_gb300 as pkg
+    b = box
+    R = 3
+    v0 = f32(b.velocities(R, KT, 8))
+    s = make(pkg, b, R, v0=v0, skin=0.1, rebuild_every=7)
+    s.step(5)  # (the first call opens with the initial build of every list)
+    n = 40
+    s.step(n)
+    info = s.info()
+    events = (info["graph_nodes_last_call"] - (12 + 5 * n)) / 8
+    assert events == int(events) and events >= n // 8
+    builds_per_replica = n / info["steps_per_list_build"]
+    assert abs(builds_per_replica - events) < 1e-9
+    assert s.status()[0] == 0
+    s.close()
