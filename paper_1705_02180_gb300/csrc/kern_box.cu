@@ -482,8 +482,8 @@ __global__ void __launch_bounds__(128) k_box_list(BoxDev B, StateDev st, int r0)
 // warp: lane l holds entry j_l; at iteration t it takes cluster atom l ^ t, so the i-force
 // sums move by one xor exchange per iteration (after the eighth, xor 7, lane l holds atom
 // l's again) while the j force stays in the lane. Each pair term s (x_j - x_i) is rounded to
-// 2^-13 units and summed in 32-bit registers. FIRST: quarter 0 holds the cluster's own slots, whose pairs count
-// once (j slot after i slot). EXCL: exclusion masks (clusters holding chain atoms); MINIMG:
+// 2^-13 units and summed in 32-bit registers. FIRST: quarter 0 holds the cluster's own
+// slots, whose pairs count once (j slot after i slot). EXCL: exclusion masks (clusters holding chain atoms); MINIMG:
 // per-pair minimum image; FAST: every atom has the reference LJ parameters, whose pair
 // constants U are computed once. Returns false for the quarters where some |s| exceeds
 // pc.s_lim (their 32-bit sums could overflow; the caller redoes those chunks pair by pair).
